@@ -1,0 +1,190 @@
+"""FP64 single-threaded CPU oracle of the TPC Time-Frame tracker.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  The oracle is a
+plain C program (``o2tpc_oracle.c``) that shares no code with the CUDA path;
+this module builds it with gcc and exposes it through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "o2tpc_oracle.c")
+LIBDIR = os.path.join(HERE, "_lib")
+SO = os.path.join(LIBDIR, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(LIBDIR, exist_ok=True)
+    deps = [SRC, os.path.join(HERE, "o2tpc_oracle.h")]
+    if force or not os.path.exists(SO) or any(os.path.getmtime(d) > os.path.getmtime(SO) for d in deps):
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", SO + ".tmp", SRC, "-lm"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + r.stdout + r.stderr)
+        os.replace(SO + ".tmp", SO)
+    return SO
+
+
+class _Input(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("format", ctypes.c_int32),
+        ("sector", ctypes.c_void_p),
+        ("row", ctypes.c_void_p),
+        ("y", ctypes.c_void_p),
+        ("z", ctypes.c_void_p),
+        ("packed", ctypes.c_void_p),
+        ("bz", ctypes.c_double),
+        ("vdrift", ctypes.c_double),
+        ("sector_mask", ctypes.c_uint64),
+        ("reverse_tracklet_order", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.oracle_run.restype = ctypes.c_void_p
+        lib.oracle_run.argtypes = [ctypes.POINTER(_Input), ctypes.POINTER(ctypes.c_int32)]
+        lib.oracle_free.restype = None
+        lib.oracle_free.argtypes = [ctypes.c_void_p]
+        lib.oracle_get.restype = ctypes.c_int64
+        lib.oracle_get.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p),
+                                   ctypes.POINTER(ctypes.c_int32)]
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.oracle_propagate.restype = ctypes.c_int32
+        lib.oracle_propagate.argtypes = [dp, dp, dp, ctypes.c_double, ctypes.c_double]
+        lib.oracle_update.restype = ctypes.c_int32
+        lib.oracle_update.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
+        lib.oracle_rotate.restype = ctypes.c_int32
+        lib.oracle_rotate.argtypes = [dp, dp, dp, ctypes.c_double]
+        lib.oracle_fit_points.restype = ctypes.c_int32
+        lib.oracle_fit_points.argtypes = [ctypes.c_int32, dp, dp, dp, ctypes.c_double, dp, dp]
+        _lib = lib
+    return _lib
+
+
+_DT = {0: np.int32, 1: np.int64, 2: np.float64}
+
+FIELDS = [
+    "yu", "zu", "rid", "sorted_orig", "sorted_rid", "sorted_y", "sorted_z", "sorted_cell",
+    "row_count", "row_zmin", "row_zmax", "row_ny", "row_nz", "row_cz", "row_start", "row_cellbase",
+    "cell_start", "up_raw", "dn_raw", "up", "dn", "starts", "tl_nhits", "tl_kept", "tl_zref", "tl_off",
+    "tl_hits", "tl_state", "st_sector", "st_tracklet", "st_zref", "st_off", "st_hits", "st_in", "st_out",
+    "st_next", "st_prev", "pair_ab", "pair_chi2", "trk_off", "trk_cl", "trk_x", "trk_alpha", "trk_par",
+    "trk_cov", "trk_chi2", "trk_ndf", "trk_sector", "trk_flags", "trk_zref", "trk_head", "trk_nseg",
+]
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _vp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=None) -> dict:
+    """Runs the oracle on a ``synth.TimeFrame``-like object (attributes n,
+    fmt, sector, row, y, z, packed, bz, vdrift).  Returns a dict of numpy
+    arrays (copies) named as in ``FIELDS``."""
+    lib = _load()
+    inp = _Input()
+    inp.n = tf.n
+    inp.format = tf.fmt
+    keep = []
+    if tf.fmt == 0:
+        for nm in ("sector", "row", "y", "z"):
+            a = np.ascontiguousarray(getattr(tf, nm))
+            keep.append(a)
+            setattr(inp, nm, _vp(a))
+    else:
+        a = np.ascontiguousarray(tf.packed)
+        keep.append(a)
+        inp.packed = _vp(a)
+    inp.bz = tf.bz
+    inp.vdrift = tf.vdrift
+    inp.sector_mask = sector_mask
+    inp.reverse_tracklet_order = int(reverse_tracklet_order)
+    st = ctypes.c_int32()
+    h = lib.oracle_run(ctypes.byref(inp), ctypes.byref(st))
+    if st.value != 0 or not h:
+        raise OracleError(f"oracle rejected the input (status {st.value})")
+    out = {}
+    try:
+        for nm in (fields or FIELDS):
+            p = ctypes.c_void_p()
+            t = ctypes.c_int32()
+            n = lib.oracle_get(h, nm.encode(), ctypes.byref(p), ctypes.byref(t))
+            if n < 0:
+                raise KeyError(nm)
+            dt = _DT[t.value]
+            if n == 0:
+                out[nm] = np.zeros(0, dt)
+            else:
+                buf = (ctypes.c_char * (n * np.dtype(dt).itemsize)).from_address(p.value)
+                out[nm] = np.frombuffer(buf, dtype=dt).copy()
+    finally:
+        lib.oracle_free(h)
+    for nm in ("tl_state", "st_in", "st_out"):
+        if nm in out:
+            out[nm] = out[nm].reshape(-1, 21)
+    if "trk_par" in out:
+        out["trk_par"] = out["trk_par"].reshape(-1, 5)
+    if "trk_cov" in out:
+        out["trk_cov"] = out["trk_cov"].reshape(-1, 15)
+    if "pair_ab" in out:
+        out["pair_ab"] = out["pair_ab"].reshape(-1, 2)
+    return out
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def propagate(x: float, p5, c15, x2: float, bz: float):
+    lib = _load()
+    xx = np.array([x], np.float64)
+    p = np.array(p5, np.float64)
+    c = np.array(c15, np.float64)
+    rc = lib.oracle_propagate(_dptr(xx), _dptr(p), _dptr(c), x2, bz)
+    return rc, xx[0], p, c
+
+
+def update(p5, c15, ym: float, zm: float):
+    lib = _load()
+    p = np.array(p5, np.float64)
+    c = np.array(c15, np.float64)
+    chi = np.zeros(1, np.float64)
+    rc = lib.oracle_update(_dptr(p), _dptr(c), ym, zm, _dptr(chi))
+    return rc, p, c, chi[0]
+
+
+def rotate(x: float, p5, c15, dalpha: float):
+    lib = _load()
+    xx = np.array([x], np.float64)
+    p = np.array(p5, np.float64)
+    c = np.array(c15, np.float64)
+    rc = lib.oracle_rotate(_dptr(xx), _dptr(p), _dptr(c), dalpha)
+    return rc, xx[0], p, c
+
+
+def fit_points(x, y, z, bz: float, seed_p5, c15_init=None):
+    lib = _load()
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    z = np.ascontiguousarray(z, np.float64)
+    p = np.array(seed_p5, np.float64)
+    c = np.zeros(15, np.float64) if c15_init is None else np.array(c15_init, np.float64)
+    rc = lib.oracle_fit_points(len(x), _dptr(x), _dptr(y), _dptr(z), bz, _dptr(p), _dptr(c))
+    return rc, p, c

@@ -1,0 +1,54 @@
+/*
+ * o2tpc_oracle.h - interface of the FP64 single-threaded CPU oracle tracker.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this; only the tests, the package entry's smoke check and the CPU
+ * baseline leg of the benchmark do.  It shares no code with the CUDA path.
+ */
+#ifndef O2TPC_ORACLE_H
+#define O2TPC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int64_t n;               /* clusters */
+  int32_t format;          /* 0: float (sector,row,y,z); 1: fixed 12-byte records */
+  const uint8_t* sector;   /* float format */
+  const uint8_t* row;      /* float format */
+  const float* y;          /* cm, local */
+  const float* z;          /* cm, apparent z for a collision at t = 0 */
+  const uint8_t* packed;   /* fixed format, n * 12 bytes */
+  double bz;               /* T */
+  double vdrift;           /* cm/us */
+  uint64_t sector_mask;    /* bit s set: sector s is tracked (0 = all) */
+  int32_t reverse_tracklet_order; /* 1: build tracklets in reverse order (selection order-independence test) */
+} oracle_input;
+
+typedef struct oracle_result oracle_result;
+
+/* Runs the whole tracker.  *status: 0 ok, -1 invalid input. */
+oracle_result* oracle_run(const oracle_input* in, int32_t* status);
+void oracle_free(oracle_result* r);
+/* Named outputs (see o2tpc_oracle.c, oracle_get).  Returns the element count
+ * (-1 if unknown name); *ptr points into the result (owned by it);
+ * *type: 0 int32, 1 int64, 2 double. */
+int64_t oracle_get(oracle_result* r, const char* name, const void** ptr, int32_t* type);
+
+/* Building blocks, exposed so that the tests can pin them one by one. */
+int32_t oracle_propagate(double* x, double* p5, double* c15, double x2, double bz);
+int32_t oracle_update(double* p5, double* c15, double ym, double zm, double* chi2);
+int32_t oracle_rotate(double* x, double* p5, double* c15, double dalpha);
+/* Fits measurements (x_i, y_i, zeta_i) in the order given: the first point
+ * seeds y and zeta, (sin phi, t, q/pT) come from p5; the initial covariance is
+ * c15 if c15[0] > 0, else the tracker's initial diagonal.  Returns the state
+ * and covariance at the last point in p5, c15. */
+int32_t oracle_fit_points(int32_t n, const double* x, const double* y, const double* z, double bz,
+                          double* p5_inout, double* c15_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,178 @@
+"""Pins of the oracle's whole tracking chain against the generator's truth
+(closed-form helices), not against the oracle's own formulas:
+
+* noise-free helices are found with exactly their cluster sets and fitted
+  to the truth within the quantisation of the cluster format,
+* fit pulls of all five parameters have zero mean and unit width,
+* efficiency / fake sanity bounds on the single-sector workload,
+* a particle crossing two sectors comes out as one merged track,
+* the selection does not depend on the order tracklets are processed in,
+* float and fixed-point inputs of the same clusters give the same tracks.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import Helix, VDRIFT
+from paper_2106_03636_gb300 import synth
+
+ZUNIT = 0.003125 * VDRIFT
+
+
+def match_tracks(tf, o):
+    """Per output track: (truth id or -1, purity)."""
+    tt = tf.truth_track
+    off, cl = o["trk_off"], o["trk_cl"]
+    out = []
+    for i in range(len(off) - 1):
+        ids = tt[cl[off[i]:off[i + 1]]]
+        v, c = np.unique(ids, return_counts=True)
+        j = int(np.argmax(c))
+        out.append((int(v[j]), c[j] / len(ids)))
+    return out
+
+
+def truth_state(tf, tid, o, i):
+    """Truth (y, zeta, sin phi, tan lambda, q/pT) at the output x and frame."""
+    T = tf.truth
+    hx = Helix(T["pt"][tid], T["eta"][tid], T["phi0"][tid], int(T["q"][tid]), T["zv"][tid], T["t0"][tid], tf.bz)
+    r = hx.at_local_x(o["trk_alpha"][i], o["trk_x"][i])
+    if r is None:
+        return None
+    y, s, arc, z = r
+    side = 1 if o["trk_sector"][i] < 18 else -1
+    zeta = VDRIFT * hx.t0 + 250.0 - side * z
+    return np.array([y, zeta, s, hx.tanl, hx.q / hx.pt])
+
+
+def fitted(o, i):
+    p = o["trk_par"][i].copy()
+    p[1] += o["trk_zref"][i] * ZUNIT
+    return p
+
+
+def test_noise_free_helices_recovered_exactly():
+    tf = synth.single_sector(seed=11, ntracks=60, sigma_y=0.0, sigma_z=0.0, noise_frac=0.0)
+    o = oracle.run(tf)
+    tt = tf.truth_track
+    cnt = np.bincount(tt, minlength=len(tf.truth["pt"]))
+    m = match_tracks(tf, o)
+    found = {}
+    for i, (tid, pur) in enumerate(m):
+        assert pur == 1.0
+        assert tid not in found
+        found[tid] = i
+    # every track with >= 10 clusters (no gaps: one cluster per crossed row) is found with all of them
+    for tid in np.nonzero(cnt >= 10)[0]:
+        rows = np.sort(tf.row[tt == tid])
+        if np.any(np.diff(rows) > 5):
+            continue
+        assert tid in found, tid
+        i = found[tid]
+        assert o["trk_off"][i + 1] - o["trk_off"][i] == cnt[tid]
+    # With exact clusters the only noise left is the quantisation of the
+    # format (uniform, 1/160 cm in y and 0.008 cm in zeta: rms 0.0018 and
+    # 0.0023 cm, i.e. <= 0.02 of the 0.1 / 0.15 cm errors the filter assumes),
+    # so every parameter must sit within 4 such scaled standard deviations.
+    for tid, i in found.items():
+        d = fitted(o, i) - truth_state(tf, tid, o, i)
+        c = o["trk_cov"][i]
+        sig = np.sqrt([c[0], c[2], c[5], c[9], c[14]])
+        assert np.all(np.abs(d) <= 4 * 0.02 * sig), (tid, d / sig)
+        assert abs(d[0]) < 0.004 and abs(d[1]) < 0.008
+
+
+@pytest.mark.slow
+def test_fit_pulls_unit_width():
+    """Pull widths of all five parameters are 1 within 0.06 and means 0
+    within 0.1.  A wrong covariance term moves a width by far more.  The
+    means carry the extended filter's second-order linearisation bias (about
+    +0.07 sigma in tan(lambda), +0.04 in zeta; it vanishes at Bz = 0).  The
+    collision sits at t0 = 20 us so that no cluster meets the start of the
+    readout window, where a cut on the smeared time would bias zeta."""
+    pulls = []
+    ev = 0
+    while len(pulls) < 10000:
+        tf = synth.single_sector(seed=1000 + ev, ntracks=200, t0=20.0)
+        o = oracle.run(tf)
+        for i, (tid, pur) in enumerate(match_tracks(tf, o)):
+            if tid < 0 or pur < 1.0:
+                continue
+            tr = truth_state(tf, tid, o, i)
+            if tr is None:
+                continue
+            d = fitted(o, i) - tr
+            c = o["trk_cov"][i]
+            sig = np.sqrt([c[0], c[2], c[5], c[9], c[14]])
+            pulls.append(d / sig)
+        ev += 1
+    P = np.array(pulls)
+    mean, width = P.mean(axis=0), P.std(axis=0)
+    assert np.all(np.abs(mean) < 0.1), mean
+    assert np.all(np.abs(width - 1.0) < 0.06), width
+
+
+def efficiency(tf, o, min_cl=10):
+    tt = tf.truth_track
+    cnt = np.bincount(tt[tt >= 0], minlength=len(tf.truth["pt"]))
+    findable = set(np.nonzero(cnt >= min_cl)[0].tolist())
+    found, fakes = set(), 0
+    for tid, pur in match_tracks(tf, o):
+        if tid >= 0 and pur >= 0.9:
+            found.add(tid)
+        else:
+            fakes += 1
+    return len(found & findable) / max(1, len(findable)), fakes / max(1, len(o["trk_x"]))
+
+
+def test_single_sector_efficiency_and_fakes():
+    tf = synth.single_sector()
+    o = oracle.run(tf)
+    eff, fake = efficiency(tf, o)
+    assert eff >= 0.95 and fake < 0.01, (eff, fake)
+
+
+def test_two_sector_particles_merge():
+    tf = synth.full_tpc_1ms(seed=21, n_coll=1, ntracks=2900)
+    o = oracle.run(tf)
+    tt = tf.truth_track
+    sig = tt >= 0
+    # particles with >= 12 clusters in each of exactly two adjacent sectors, all on one side
+    ntr = len(tf.truth["pt"])
+    per = np.zeros((ntr, 36), np.int32)
+    np.add.at(per, (tt[sig], tf.sector[sig]), 1)
+    cand = [t for t in range(ntr) if (per[t] > 0).sum() == 2 and np.all(per[t][per[t] > 0] >= 12)]
+    cand = [t for t in cand if abs(np.diff(np.nonzero(per[t])[0])[0]) in (1, 17)]
+    assert len(cand) > 100
+    m = match_tracks(tf, o)
+    one = 0
+    for t in cand:
+        hits = [i for i, (tid, pur) in enumerate(m) if tid == t and pur >= 0.9]
+        if len(hits) == 1 and len(set(tf.sector[o["trk_cl"][o["trk_off"][hits[0]]:o["trk_off"][hits[0] + 1]]])) == 2:
+            one += 1
+    assert one / len(cand) >= 0.95, one / len(cand)
+
+
+def test_selection_independent_of_tracklet_order():
+    tf = synth.full_tpc_1ms(seed=22, n_coll=1, ntracks=1500)
+    a = oracle.run(tf)
+    b = oracle.run(tf, reverse_tracklet_order=True)
+    for k in ("st_hits", "st_off", "trk_cl", "trk_off", "trk_par", "trk_cov"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_float_and_fixed_formats_agree():
+    tf_f = synth.full_tpc_1ms(seed=23, n_coll=1, ntracks=1500)
+    tf_x = synth.full_tpc_1ms(seed=23, n_coll=1, ntracks=1500, fmt=synth.FMT_FIXED)
+    assert tf_f.n == tf_x.n
+    a = oracle.run(tf_f, fields=["trk_off", "trk_cl"])
+    b = oracle.run(tf_x, fields=["trk_off", "trk_cl"])
+
+    def sets(o):
+        off, cl = o["trk_off"], o["trk_cl"]
+        return {tuple(sorted(cl[off[i]:off[i + 1]].tolist())) for i in range(len(off) - 1)}
+
+    sa, sb = sets(a), sets(b)
+    assert len(sa & sb) >= 0.98 * max(len(sa), len(sb))
