@@ -1,0 +1,298 @@
+"""Benchmark: TPC clusters/s of the GB300 tracker on a full 50 kHz Pb-Pb Time Frame.
+
+One step = one pass of the whole hot path (ingest, grid + sort, neighbours,
+cleaner, start hits, tracklets, selection, sector fits, merger, final refit,
+result download) over one synthetic Time Frame of 128 LHC orbits (~250 M
+clusters in 12-byte fixed-point records), through the C-ABI.
+
+* ``value``: clusters/s with the input already resident in HBM (the TF is
+  submitted with device pointers); CUDA events on the library's stream
+  bracket the K timed steps; the 3 GB input is larger than L2, so no flush.
+* ``e2e``: the same metric with the input in pinned host memory: the
+  host-to-device copy and the result download are inside the timed region.
+* ``roofline``: the dominant step, from the library's per-step CUDA events,
+  against the measured HBM copy bandwidth.
+* ``cpu_baseline``: the FP64 single-threaded oracle on one sector of the same
+  Time Frame.
+
+``--impl reference`` times that oracle as the reference arm instead.
+Under torchrun each rank tracks its own Time Frames (replicas; the only
+collective is the max-over-ranks of the timings).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TPC clusters/s and TF/s at 50 kHz Pb-Pb on 1 GB300 (served vs plain); p99 TF latency"
+
+# Algorithmic HBM bytes per cluster of each step: data the step must read or
+# write once per cluster at minimum (16-byte sort records, 8-byte sorted
+# coordinates, 4-byte indices, 8-byte ownership words).  Their sum is the
+# 64 B/cluster of the whole path.
+STAGE_BYTES = {
+    "ingest": 12.0,        # read the 12-byte packed record
+    "sort": 12.0 + 12.0,   # read the record again, write sorted y, zeta + input index
+    "neighbours": 8.0 + 8.0,  # read sorted coordinates, write two links
+    "clean_starts": 8.0,   # read the links
+    "tracklets": 8.0,      # ownership / hit-list words per attached cluster
+    "selection": 4.0,      # output cluster index
+    "sector_fit": 1.0,
+    "merge": 0.5,
+    "refit": 0.5,
+    "download": 0.0,
+}
+PATH_BYTES = 64.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 7:
+                self.rows.append(f)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def make_workload(name: str, seed: int):
+    from paper_2106_03636_gb300 import synth
+
+    if name == "full_tf":
+        return synth.full_tf(seed=seed), {"workload": "full_tf_128orbits_50kHz_PbPb", "orbits": 128,
+                                          "rate_khz": 50.0, "format": "fixed12"}
+    if name == "full_tpc_1ms":
+        return synth.full_tpc_1ms(seed=seed), {"workload": "full_tpc_50coll_1ms", "format": "float"}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def cpu_baseline(tf, sector: int = 0):
+    """The oracle as it stands on one sector of the workload."""
+    from types import SimpleNamespace
+
+    import oracle
+
+    sel = tf.packed[:, 9] == sector
+    sub = SimpleNamespace(n=int(sel.sum()), fmt=tf.fmt, packed=np.ascontiguousarray(tf.packed[sel]), sector=None,
+                          row=None, y=None, z=None, bz=tf.bz, vdrift=tf.vdrift)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.run(sub, fields=["trk_off"])
+    dt = time.perf_counter() - t0
+    return sub.n, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import torch  # noqa: F401  (same process layout as the main arm)
+
+    tf, cfg = make_workload(args.workload, args.seed)
+    cfg["sample"] = "sector 0 of the Time Frame per step"
+    for _ in range(args.warmup):
+        cpu_baseline(tf)
+    n_tot, t_tot = 0, 0.0
+    for _ in range(args.steps):
+        n, dt = cpu_baseline(tf)
+        n_tot += n
+        t_tot += dt
+    v = n_tot / t_tot
+    line = {"metric": METRIC, "value": v, "unit": "clusters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+                             "sample": f"sector 0 of the TF ({n_tot // args.steps} clusters) per step"},
+            "e2e": {"value": v, "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="full_tf", choices=["full_tf", "full_tpc_1ms"])
+    ap.add_argument("--seed", type=int, default=20210609)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("nccl" if args.impl == "gb300" else "gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    torch.cuda.set_device(local)
+    from paper_2106_03636_gb300 import o2tpc
+
+    tf, cfg = make_workload(args.workload, args.seed + 1000 * rank)
+    n = tf.n
+    host_in = torch.from_numpy(tf.packed if tf.fmt == 1 else np.zeros(1, np.uint8))
+    dev = {}
+    if tf.fmt == 1:
+        dev["packed"] = host_in.to(f"cuda:{local}")
+    else:
+        for k in ("sector", "row", "y", "z"):
+            dev[k] = torch.from_numpy(getattr(tf, k)).to(f"cuda:{local}")
+    torch.cuda.synchronize()
+
+    trk = o2tpc.Tracker(device=local, torch_memory=True)
+    st = trk.stream
+
+    def step(location, arrays):
+        r = trk.poll(trk.submit(tf, location=location, arrays=arrays))
+        if r["status"] != 0:
+            raise RuntimeError(o2tpc.o2tpc_strerror(r["status"]))
+        return r
+
+    for _ in range(args.warmup):
+        r = step(o2tpc.O2TPC_LOC_DEVICE, dev)
+
+    def timed(location, arrays):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stage = np.zeros(10)
+        launches = 0
+        lat = []
+        e0.record(st)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            r = step(location, arrays)
+            lat.append(1e3 * (time.perf_counter() - t0))
+            stage += np.asarray(r["stats"]["ms_stage"])
+            launches += int(r["stats"]["n_launches"])
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms, stage / args.steps, launches, lat, r
+
+    with ClockSampler(local) as clk:
+        ms, stage, launches, lat, r = timed(o2tpc.O2TPC_LOC_DEVICE, dev)
+    clocks = clk.summary()
+    ms_step = ms / args.steps
+    value = world * n / (ms_step / 1e3)
+
+    # e2e: pinned host input, H2D and result download inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pin = {"packed": host_in.pin_memory()} if tf.fmt == 1 else {
+            k: torch.from_numpy(getattr(tf, k)).pin_memory() for k in ("sector", "row", "y", "z")}
+        step(o2tpc.O2TPC_LOC_HOST, pin)
+        ms_h, _, _, lat_h, rh = timed(o2tpc.O2TPC_LOC_HOST, pin)
+        h2d = 12 * n if tf.fmt == 1 else 10 * n
+        nt, ncl = rh["n_tracks"], int(rh["offsets"][-1])
+        d2h = 8 * (nt + 1) + 4 * ncl + nt * (4 * 2 + 20 + 60 + 4 + 4 + 1 + 1 + 4)
+        e2e = {"value": world * n / (ms_h / args.steps / 1e3), "unit": "clusters/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": ms_h / args.steps,
+               "p50_ms": float(np.percentile(lat_h, 50)), "p99_ms": float(np.percentile(lat_h, 99))}
+
+    peak, peak_kind = peaks()
+    names = o2tpc.STAGES
+    k = int(np.argmax(stage))
+    dom = names[k]
+    achieved = STAGE_BYTES[dom] * n / (stage[k] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+            "bytes_per_cluster": STAGE_BYTES[dom], "ms_per_launch": float(stage[k])}
+    path_frac = value / world * PATH_BYTES / 1e9 / peak
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and tf.fmt == 1:
+        nc, dt = cpu_baseline(tf)
+        cpu = {"value": nc / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+               "sample": f"sector 0 of the same TF: {nc} clusters, {dt:.1f} s"}
+
+    cfg.update({"clusters": int(n), "tracks": int(r["n_tracks"]), "l2": "inputs larger than L2 (no flush)",
+                "mode": "plain (one TF per step)", "parallelism": f"replicas x{world}"})
+    line = {"metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "tf_per_s": world / (ms_step / 1e3), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)),
+            "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(10)},
+            "path_roofline": {"bytes_per_cluster": PATH_BYTES, "frac": path_frac, "peak": peak},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    trk.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * o2tpc.h - C-ABI of the GB300 (sm_103a) TPC Time-Frame tracker.
+ *
+ * What the library computes.  TPC track reconstruction over one continuous-
+ * readout Time Frame (TF): the paper's dominant synchronous workload
+ * (Sec. 2.1), run on whole TFs of 128 LHC orbits, the processing unit of
+ * Run 3 (Sec. 2), with tracks found before collisions are known, since the
+ * drift time gives no a priori z (Sec. 2, Sec. 2.3).  Clusters go in (sector,
+ * pad row, y, z or drift time); tracks come out as lists of cluster indices
+ * plus helix parameters and covariance.  The steps, each a CUDA kernel:
+ * grid binning and per-row sort, NeighboursFinder, NeighboursCleaner,
+ * StartHitsFinder, TrackletConstructor (FP32 Kalman filter), TrackletSelector,
+ * sector-to-sector merger and final refit (FP32, with an FP64 covariance
+ * fallback that is counted).
+ *
+ * Execution model.  One context drives one GPU from one host thread, as the
+ * paper's GPU code does (Sec. 3.1.1: one CPU core per GPU).  o2tpc_submit_tf
+ * queues a TF and returns at once; a worker thread of the context admits
+ * queued TFs by their device-memory footprint, runs the admitted ones as one
+ * batch (one launch per step over all TFs in the batch) and copies the
+ * results back; o2tpc_poll waits for one TF.  TFs whose footprint can never
+ * fit are refused with O2TPC_ETOOBIG (the paper processes such TFs on the
+ * CPU, Sec. 3.1.3); a full queue answers O2TPC_EAGAIN (back pressure,
+ * Sec. 3.3).  Each TF's result is the same whether it ran alone or in a batch.
+ *
+ * Units and conventions.
+ *   sector s: 0-17 side A (z > 0), 18-35 side C; sector s is centred at
+ *     azimuth ((s mod 18) * 20 + 10) degrees; local x along the sector axis.
+ *   pad row r: 0-151, plane at local x_r = 85 + r * 160/151 cm.
+ *   y: local y in cm (pad direction).
+ *   z (float input): apparent z in cm for a collision at t = 0,
+ *     i.e. side * (250 - v_drift * t), side = +1 (A) / -1 (C).
+ *   drift coordinate zeta = v_drift * t (cm); internally in units of 1/64 of
+ *     a 200 ns time bin (3.125 ns).
+ *   Output parameters, in the frame of the innermost cluster's sector at
+ *   x = that cluster's pad-row x:
+ *     par[0] y (cm)
+ *     par[1] zeta - zeta_ref (cm), zeta_ref = the innermost cluster's drift
+ *            coordinate (reported in time units of 1/64 bin in zeta_ref[])
+ *     par[2] sin(phi) (local)
+ *     par[3] tan(lambda) (dz/ds in the transverse path length)
+ *     par[4] q/pT (1/GeV)
+ *   cov: lower triangle of the 5x5 covariance, order
+ *     (0,0) (1,0) (1,1) (2,0) (2,1) (2,2) (3,0) (3,1) (3,2) (3,3)
+ *     (4,0) (4,1) (4,2) (4,3) (4,4).
+ *
+ * Errors.  Functions return O2TPC_OK (0), O2TPC_PENDING (1) or a negative
+ * o2tpc_status.  No function aborts the process; a CUDA failure is reported
+ * as O2TPC_ECUDA and leaves the context unusable (destroy it).
+ */
+#ifndef O2TPC_H
+#define O2TPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct o2tpc_ctx o2tpc_ctx; /* opaque; owned by the library */
+
+typedef enum {
+  O2TPC_OK = 0,
+  O2TPC_PENDING = 1,   /* poll: the TF is not done within the timeout          */
+  O2TPC_EINVAL = -1,   /* bad argument, or a cluster with sector >= 36, row >= 152,
+                          non-finite y/z or a drift coordinate out of range   */
+  O2TPC_ENOMEM = -2,   /* a device or host allocation failed                   */
+  O2TPC_EAGAIN = -3,   /* queue full: retry after polling/releasing             */
+  O2TPC_ETOOBIG = -4,  /* the TF's footprint exceeds the memory budget          */
+  O2TPC_ECUDA = -5,    /* a CUDA call failed                                    */
+  O2TPC_ETIMEOUT = -6, /* a bounded device wait ran out                         */
+  O2TPC_ENOTFOUND = -7 /* unknown ticket                                        */
+} o2tpc_status;
+
+enum { O2TPC_FMT_FLOAT = 0, O2TPC_FMT_FIXED = 1 };
+enum { O2TPC_LOC_HOST = 0, O2TPC_LOC_DEVICE = 1 };
+
+/* o2tpc_config.flags */
+enum {
+  O2TPC_FLAG_KEEP_STAGES = 1u << 0, /* keep per-step device arrays until release,
+                                       readable with o2tpc_get_stage          */
+  O2TPC_FLAG_NO_BATCHING = 1u << 1, /* run every TF alone (one TF per batch)  */
+  O2TPC_FLAG_FORCE_FP64 = 1u << 2   /* take the FP64 covariance path in the final
+                                       refit for every track (testing aid)     */
+};
+
+typedef struct {
+  int32_t device;          /* CUDA device ordinal                                     */
+  uint64_t mem_budget;     /* device bytes the admitted TFs may use (0: 120 GB)       */
+  int32_t max_inflight;    /* TFs queued or running at once (0: 64)                   */
+  int32_t max_batch;       /* TFs per batch (0: 64)                                   */
+  double bz_tesla;         /* solenoid field (0 allowed: straight lines)              */
+  double vdrift_cm_us;     /* drift velocity (> 0)                                    */
+  uint32_t flags;          /* O2TPC_FLAG_*                                            */
+  /* Device memory: if dev_alloc is set, every device buffer comes from it
+   * (e.g. a framework's caching allocator) and goes back through dev_free;
+   * otherwise cudaMallocAsync/cudaFreeAsync on the context's stream. */
+  void* (*dev_alloc)(size_t bytes, void* user);
+  void (*dev_free)(void* ptr, void* user);
+  void* alloc_user;
+  void* stream;            /* cudaStream_t to run on, or NULL for a library stream    */
+} o2tpc_config;
+
+typedef struct {
+  uint64_t n;              /* clusters (may be 0)                                      */
+  int32_t format;          /* O2TPC_FMT_FLOAT or O2TPC_FMT_FIXED                       */
+  int32_t location;        /* O2TPC_LOC_HOST or O2TPC_LOC_DEVICE (pointers below)      */
+  /* FLOAT: arrays of n */
+  const uint8_t* sector;
+  const uint8_t* row;
+  const float* y;          /* cm                                                       */
+  const float* z;          /* cm, apparent z (see above)                               */
+  /* FIXED: n records of 12 bytes, little endian:
+   *   u32 time64 (drift time in 1/64 of a 200 ns bin, < 2^30), u16 pad64
+   *   (pad position in 1/64 pad, 0 at the sector's pad-plane edge), u16 charge,
+   *   u8 row, u8 sector, u16 spare */
+  const void* packed;
+  uint64_t user_tag;       /* echoed in the result                                     */
+} o2tpc_tf;
+
+typedef struct {
+  uint64_t n_clusters;
+  uint64_t n_tracklets;      /* start hits = tracklets built                          */
+  uint64_t n_sector_tracks;
+  uint64_t n_tracks;
+  uint64_t n_fp64_fallback;  /* tracks whose final refit ran with FP64 covariance     */
+  uint32_t batch_size;       /* TFs in the batch this TF ran in                       */
+  float ms_queue;            /* submit -> batch start (host clock)                    */
+  float ms_batch;            /* batch start -> results on the host (host clock)       */
+  float ms_device;           /* device time of the batch (CUDA events)                */
+  uint64_t n_launches;       /* kernels launched for the batch                        */
+  /* device time of each step of the batch (CUDA events on the context's stream,
+   * gaps for the host reading sizes included): 0 ingest + row statistics +
+   * grid, 1 row/cell sort, 2 NeighboursFinder, 3 NeighboursCleaner +
+   * StartHitsFinder, 4 TrackletConstructor, 5 TrackletSelector, 6 sector-track
+   * fits, 7 merger, 8 final refit, 9 result download */
+  float ms_stage[10];
+} o2tpc_stats;
+
+/* Result of one TF; library-owned memory, valid until o2tpc_result_release. */
+typedef struct {
+  uint64_t n_tracks;
+  const uint64_t* offsets;     /* [n_tracks + 1] into cluster_idx                     */
+  const uint32_t* cluster_idx; /* indices into the submitted cluster order, innermost
+                                  segment first, ascending pad row within a sector   */
+  const float* x;              /* [n_tracks] local x of the reported state (cm)       */
+  const float* alpha;          /* [n_tracks] sector frame angle (rad)                 */
+  const float* par;            /* [n_tracks][5]                                       */
+  const float* cov;            /* [n_tracks][15]                                      */
+  const float* chi2;           /* [n_tracks]                                          */
+  const int32_t* ndf;          /* [n_tracks] 2 * fitted clusters - 5                  */
+  const uint8_t* sector;       /* [n_tracks] sector of the reported frame             */
+  const uint8_t* flags;        /* [n_tracks] bit0 FP64 fallback, bit1 merged from
+                                  several sectors, bit2 refit stopped at a sector
+                                  boundary                                           */
+  const uint32_t* zeta_ref;    /* [n_tracks] drift coordinate origin of par[1]        */
+  o2tpc_stats stats;
+  uint64_t user_tag;
+  int32_t status;              /* O2TPC_OK or the error of this TF                    */
+} o2tpc_result;
+
+/* Creates a context on cfg->device (cfg may be NULL: all defaults).
+ * *out is set on success.  Returns O2TPC_EINVAL, O2TPC_ECUDA or O2TPC_ENOMEM. */
+int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out);
+
+/* Queues one TF.  The input is borrowed, not copied: host input (pinned
+ * memory gives the fastest upload) and device input alike must stay valid and
+ * unchanged until o2tpc_poll has returned the TF's result.  *ticket
+ * identifies the TF.
+ * Returns O2TPC_OK, O2TPC_EINVAL, O2TPC_EAGAIN (queue full), O2TPC_ETOOBIG,
+ * O2TPC_ENOMEM.  Invalid cluster content is detected on the device and
+ * reported by o2tpc_poll as the TF's status O2TPC_EINVAL. */
+int o2tpc_submit_tf(o2tpc_ctx* ctx, const o2tpc_tf* tf, uint64_t* ticket);
+
+/* Waits up to timeout_ms (< 0: forever, 0: just test) for a TF.  On
+ * O2TPC_OK, *out is the result (its own status may still be an error).
+ * Returns O2TPC_PENDING on timeout, O2TPC_ENOTFOUND for an unknown ticket. */
+int o2tpc_poll(o2tpc_ctx* ctx, uint64_t ticket, int32_t timeout_ms, const o2tpc_result** out);
+
+/* Frees a polled result (and the TF's kept stages); the ticket is retired. */
+void o2tpc_result_release(o2tpc_ctx* ctx, const o2tpc_result* res);
+
+/* Waits for all queued work, frees everything.  Returns O2TPC_OK or the first
+ * CUDA error seen. */
+int o2tpc_destroy(o2tpc_ctx* ctx);
+
+/* Human-readable text of a status code (static storage). */
+const char* o2tpc_strerror(int32_t status);
+
+/* Intermediate arrays of one polled TF, kept when the context was created
+ * with O2TPC_FLAG_KEEP_STAGES (for testing and inspection).  Copies the named
+ * array to host memory dst (capacity bytes); *needed receives its size in
+ * bytes.  Indices are local to the TF (hit indices count from its first
+ * sorted hit).  Returns O2TPC_OK, O2TPC_EINVAL (unknown name or dst too
+ * small; *needed still set), O2TPC_ENOTFOUND.  Names:
+ *   "sorted_orig"  int32[n]  input index of each sorted hit
+ *   "sorted_yz"    int32[n][2] y and zeta in integer units, sorted order
+ *   "row_grid"     int32[5472][8] start, count, cellBase, ny, nz, cz, zmin, 0
+ *   "cell_start"   int32[cells + 1]
+ *   "up_raw", "dn_raw", "up", "dn"  int32[n]
+ *   "starts"       int32[n_tracklets]
+ *   "tl_nhits"     int32[n_tracklets]  (0 if dropped)
+ *   "tl_hits"      int32[n_tracklets][152] hit slots, ascending rows, -1 padded
+ *   "tl_state"     float[n_tracklets][21]  x, par[5], cov[15] (zeta rel. start hit)
+ *   "st_tracklet"  int32[n_sector_tracks]
+ *   "st_off"       int32[n_sector_tracks + 1]
+ *   "st_hits"      int32[...] sorted hit indices of the sector tracks
+ *   "st_in", "st_out" float[n_sector_tracks][21]
+ *   "st_next", "st_prev" int32[n_sector_tracks] merge links (-1 none)
+ */
+int o2tpc_get_stage(o2tpc_ctx* ctx, uint64_t ticket, const char* name, void* dst, uint64_t capacity,
+                    uint64_t* needed);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* O2TPC_H */

@@ -69,7 +69,11 @@ static int o_side(int s) { return s < 18 ? 1 : -1; }
 static double o_tan10(void) { return tan(10.0 * O_PI / 180.0); }
 static int64_t o_floordiv(int64_t a, int64_t b) { int64_t q = a / b; if ((a % b != 0) && ((a < 0) != (b < 0))) --q; return q; }
 
-static const double O_CINIT[15] = {O_SY * O_SY, 0, O_SZ * O_SZ, 0, 0, 0.25, 0, 0, 0, 0.25, 0, 0, 0, 0, 400.0};
+/* Initial covariance of every fit: the first hit's (y, zeta) errors, and
+ * loose priors on the seeded sin(phi) (0.2), t (0.5) and q/pT (20, i.e. pT
+ * down to 0.05 GeV).  A sin(phi) prior much wider than 0.2 makes the first
+ * updates nearly singular, which single precision cannot follow. */
+static const double O_CINIT[15] = {O_SY * O_SY, 0, O_SZ * O_SZ, 0, 0, 0.04, 0, 0, 0, 0.25, 0, 0, 0, 0, 400.0};
 static int o_ix(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
 
 /* ------------------------------------------------------------- result */

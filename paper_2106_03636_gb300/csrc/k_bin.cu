@@ -1,0 +1,337 @@
+// k_bin.cu - ingest, per-row statistics, grid and the stable per-row sort.
+//
+// Steps A1-A4 of the hot path: clusters of a batch of Time Frames are
+// decoded to integer (y, zeta), counted per (TF, sector, row), binned into a
+// per-row grid of cells (cell = iz * ny + iy) and sorted by
+// (TF, sector, row, cell, input index).  The sort is a two-level counting
+// sort: tiles of the input scatter into row buckets at offsets from a
+// per-(tile,row) prefix (no global atomics), then one CTA per row scatters
+// its bucket into cells and restores input order inside each cell, so the
+// result is the stable order whatever the atomic interleaving.
+#include "o2tpc_kernels.cuh"
+
+namespace o2tpc {
+
+// Decodes cluster i of TF t.  Returns false (and sets the error word) for
+// invalid content; the cluster is then filed under row 0 so that indices stay
+// in bounds.
+__device__ inline bool decode(const TFDesc& t, int i, const GeomConst* __restrict__ G, int& lr, int& yu,
+                              int& zu) {
+  int s, r;
+  bool ok = true;
+  if (t.format == 1) {
+    const uint32_t* rec = reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(t.in0) + 12ll * i);
+    uint32_t w0 = __ldg(rec), w1 = __ldg(rec + 1), w2 = __ldg(rec + 2);
+    uint32_t pad = w1 & 0xFFFFu;
+    r = (int)(w2 & 0xFFu);
+    s = (int)((w2 >> 8) & 0xFFu);
+    if (s >= kNSec || r >= kNRow || w0 > 0x3FFFFFFFu) { ok = false; s = 0; r = 0; }
+    yu = (int)pad - 32 * G->npads[r];
+    zu = (int)w0;
+  } else {
+    s = __ldg(static_cast<const uint8_t*>(t.in0) + i);
+    r = __ldg(static_cast<const uint8_t*>(t.in1) + i);
+    float yf = __ldg(t.y + i), zf = __ldg(t.z + i);
+    if (s >= kNSec || r >= kNRow) { ok = false; s = 0; r = 0; }
+    if (!isfinite(yf) || !isfinite(zf)) { ok = false; yf = 0.f; zf = 0.f; }
+    float yq = rintf(__fmul_rn(yf, 160.0f));
+    float d = (s < 18) ? __fsub_rn(250.0f, zf) : __fadd_rn(250.0f, zf);
+    float zq = rintf(__fmul_rn(d, G->kz));
+    if (fabsf(yq) > 1048576.0f || fabsf(zq) > 1073741824.0f) { ok = false; yq = 0.f; zq = 0.f; }
+    yu = (int)yq;
+    zu = (int)zq;
+  }
+  lr = s * kNRow + r;
+  return ok;
+}
+
+// K0: per tile, decode and accumulate per-row count / min / max in shared
+// memory; write the tile's 5472-row statistics (SoA: count, zmin, zmax).
+__global__ void __launch_bounds__(512) k_ingest_stats(const TFDesc* __restrict__ tfs, const int2* __restrict__ tiles,
+                                                      int tileSize, const GeomConst* __restrict__ G,
+                                                      int* __restrict__ tileStats, unsigned* __restrict__ err) {
+  extern __shared__ int sm[];
+  int* s_cnt = sm;
+  int* s_min = sm + kRowsPerTF;
+  int* s_max = sm + 2 * kRowsPerTF;
+  const int tile = blockIdx.x;
+  const int2 td = tiles[tile];
+  const TFDesc t = tfs[td.x];
+  for (int i = threadIdx.x; i < kRowsPerTF; i += blockDim.x) { s_cnt[i] = 0; s_min[i] = INT_MAX; s_max[i] = INT_MIN; }
+  __syncthreads();
+  const int b = td.y, e = min(t.n, td.y + tileSize);
+  bool bad = false;
+  for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+    int lr, yu, zu;
+    if (!decode(t, i, G, lr, yu, zu)) bad = true;
+    atomicAdd(&s_cnt[lr], 1);
+    atomicMin(&s_min[lr], zu);
+    atomicMax(&s_max[lr], zu);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrInput);
+  int* out = tileStats + (size_t)tile * 3 * kRowsPerTF;
+  for (int i = threadIdx.x; i < kRowsPerTF; i += blockDim.x) {
+    out[i] = s_cnt[i];
+    out[kRowsPerTF + i] = s_min[i];
+    out[2 * kRowsPerTF + i] = s_max[i];
+  }
+}
+
+// Per (TF, row): reduce the tile statistics, and turn each tile's count into
+// its exclusive offset inside the row's bucket (tile order = input order).
+__global__ void k_row_reduce(const TFDesc* __restrict__ tfs, int nTF, int* __restrict__ tileStats,
+                             int* __restrict__ rowCnt, int* __restrict__ rowMin, int* __restrict__ rowMax) {
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nTF * kRowsPerTF) return;
+  int tf = g / kRowsPerTF, lr = g - tf * kRowsPerTF;
+  const TFDesc t = tfs[tf];
+  int c = 0, mn = INT_MAX, mx = INT_MIN;
+  for (int k = 0; k < t.nTiles; ++k) {
+    int* ts = tileStats + (size_t)(t.tileBase + k) * 3 * kRowsPerTF;
+    int v = ts[lr];
+    ts[lr] = c;
+    c += v;
+    mn = min(mn, ts[kRowsPerTF + lr]);
+    mx = max(mx, ts[2 * kRowsPerTF + lr]);
+  }
+  rowCnt[g] = c;
+  rowMin[g] = mn;
+  rowMax[g] = mx;
+}
+
+// Block-wide exclusive scan of one int per thread (blockDim.x == 1024).
+__device__ inline int block_excl_scan(int v, int* total) {
+  __shared__ int ws[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    ws[lane] = s;
+  }
+  __syncthreads();
+  int incl = x + (w > 0 ? ws[w - 1] : 0);
+  if (total) *total = ws[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+// Grid of every row and the three row-level exclusive scans (hits, cells,
+// NeighboursFinder blocks).  One CTA of 1024 threads; each thread owns a
+// contiguous run of rows.  totals[0..2] = hits, cells, NF blocks.
+__global__ void __launch_bounds__(1024) k_grid(int nRows, const int* __restrict__ rowCnt, const int* __restrict__ rowMin,
+                                               const int* __restrict__ rowMax, const GeomConst* __restrict__ G,
+                                               RowGrid* __restrict__ grid, int* __restrict__ nfBlockStart,
+                                               int nfBlock, int* __restrict__ totals) {
+  int per = (nRows + blockDim.x - 1) / blockDim.x;
+  int b = threadIdx.x * per, e = min(nRows, b + per);
+  int sh = 0, sc = 0, sb = 0;
+  for (int R = b; R < e; ++R) {
+    int r = (R % kRowsPerTF) % kNRow;
+    int n = rowCnt[R];
+    int ny = max(1, (64 * G->npads[r] + kCellY - 1) / kCellY);
+    int nz = 1;
+    if (n > 0) nz = min(max((n + kHitsPerCell * ny - 1) / (kHitsPerCell * ny), 1), kMaxNz);
+    sh += n;
+    sc += ny * nz;
+    sb += (n + nfBlock - 1) / nfBlock;
+  }
+  int th, tc, tb;
+  int oh = block_excl_scan(sh, &th);
+  int oc = block_excl_scan(sc, &tc);
+  int ob = block_excl_scan(sb, &tb);
+  for (int R = b; R < e; ++R) {
+    int r = (R % kRowsPerTF) % kNRow;
+    int n = rowCnt[R];
+    RowGrid g;
+    g.ny = max(1, (64 * G->npads[r] + kCellY - 1) / kCellY);
+    g.nz = 1;
+    g.cz = 1;
+    g.zmin = 0;
+    if (n > 0) {
+      g.nz = min(max((n + kHitsPerCell * g.ny - 1) / (kHitsPerCell * g.ny), 1), kMaxNz);
+      long long range = (long long)rowMax[R] - (long long)rowMin[R] + 1;
+      g.cz = (int)((range + g.nz - 1) / g.nz);
+      g.zmin = rowMin[R];
+    }
+    g.start = oh;
+    g.count = n;
+    g.cellBase = oc;
+    g.pad = 0;
+    grid[R] = g;
+    nfBlockStart[R] = ob;
+    oh += n;
+    oc += g.ny * g.nz;
+    ob += (n + nfBlock - 1) / nfBlock;
+  }
+  if (threadIdx.x == 0) {
+    totals[0] = th;
+    totals[1] = tc;
+    totals[2] = tb;
+    nfBlockStart[nRows] = tb;
+  }
+}
+
+__global__ void k_cell_sentinel(int* __restrict__ cellStart, const int* __restrict__ totals) {
+  cellStart[totals[1]] = totals[0];
+}
+
+// K3a: scatter each tile's clusters into its row bucket at
+// rowStart + (tile offset within the row) + (unordered rank inside the tile).
+// Records: {y_u, zeta_u, batch input index, cell}.
+__global__ void __launch_bounds__(512) k_row_scatter(const TFDesc* __restrict__ tfs, const int2* __restrict__ tiles,
+                                                     int tileSize, const GeomConst* __restrict__ G,
+                                                     const int* __restrict__ tileStats,
+                                                     const RowGrid* __restrict__ grid, int4* __restrict__ bucket) {
+  __shared__ int s_cur[kRowsPerTF];
+  const int tile = blockIdx.x;
+  const int2 td = tiles[tile];
+  const TFDesc t = tfs[td.x];
+  const int Rbase = td.x * kRowsPerTF;
+  const int* ts = tileStats + (size_t)tile * 3 * kRowsPerTF;
+  for (int i = threadIdx.x; i < kRowsPerTF; i += blockDim.x) s_cur[i] = grid[Rbase + i].start + ts[i];
+  __syncthreads();
+  const int b = td.y, e = min(t.n, td.y + tileSize);
+  for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+    int lr, yu, zu;
+    decode(t, i, G, lr, yu, zu);
+    const RowGrid g = grid[Rbase + lr];
+    int iy = cell_iy(g, G->npads[lr % kNRow], yu);
+    int iz = (int)(((long long)zu - g.zmin) / g.cz);
+    int slot = atomicAdd(&s_cur[lr], 1);
+    bucket[slot] = make_int4(yu, zu, t.inBase + i, iz * g.ny + iy);
+  }
+}
+
+// K3b: one CTA per row.  Counting sort of the row's bucket by cell into the
+// final arrays, then input order restored inside every cell (insertion sort
+// by input index).  Cell counters live in shared memory when the row has at
+// most kSmemCells cells, else in the global scratch (cellStart itself).
+constexpr int kSmemCells = 12288;
+
+__global__ void __launch_bounds__(256) k_cell_sort(const RowGrid* __restrict__ grid, const int4* __restrict__ bucket,
+                                                   int* __restrict__ cellStart, int2* __restrict__ syz,
+                                                   int* __restrict__ sorig, int* __restrict__ gscratch) {
+  __shared__ int s_cnt[kSmemCells];
+  __shared__ int s_carry;
+  const RowGrid g = grid[blockIdx.x];
+  if (g.count == 0) {
+    for (int c = threadIdx.x; c < g.ny * g.nz; c += blockDim.x) cellStart[g.cellBase + c] = g.start;
+    return;
+  }
+  const int nc = g.ny * g.nz;
+  int* cnt = (nc <= kSmemCells) ? s_cnt : (gscratch + g.cellBase);
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) cnt[c] = 0;
+  __syncthreads();
+  const int4* bk = bucket + g.start;
+  for (int i = threadIdx.x; i < g.count; i += blockDim.x) atomicAdd(&cnt[bk[i].w], 1);
+  __syncthreads();
+  // exclusive scan of the cell counts, in chunks of blockDim
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < nc; c0 += blockDim.x) {
+    int c = c0 + threadIdx.x;
+    int v = (c < nc) ? cnt[c] : 0;
+    // warp + block scan for 256 threads
+    __shared__ int ws[8];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    int wo = 0;
+    for (int k = 0; k < w; ++k) wo += ws[k];
+    int excl = s_carry + wo + x - v;
+    __syncthreads();
+    if (c < nc) {
+      cnt[c] = excl;
+      cellStart[g.cellBase + c] = g.start + excl;
+    }
+    if (threadIdx.x == blockDim.x - 1) s_carry = excl + v;
+    __syncthreads();
+  }
+  // scatter (unordered inside a cell)
+  for (int i = threadIdx.x; i < g.count; i += blockDim.x) {
+    int4 rec = bk[i];
+    int pos = g.start + atomicAdd(&cnt[rec.w], 1);
+    syz[pos] = make_int2(rec.x, rec.y);
+    sorig[pos] = rec.z;
+  }
+  __syncthreads();
+  // restore input order inside each cell
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    int b = cellStart[g.cellBase + c];
+    int e = (c + 1 < nc) ? cellStart[g.cellBase + c + 1] : g.start + g.count;
+    for (int i = b + 1; i < e; ++i) {
+      int ko = sorig[i];
+      int2 kv = syz[i];
+      int j = i - 1;
+      while (j >= b && sorig[j] > ko) {
+        sorig[j + 1] = sorig[j];
+        syz[j + 1] = syz[j];
+        --j;
+      }
+      sorig[j + 1] = ko;
+      syz[j + 1] = kv;
+    }
+  }
+}
+
+// ------------------------------------------------------------- launchers
+void launch_ingest_stats(const TFDesc* tfs, const int2* tiles, int nTiles, int tileSize, const GeomConst* G,
+                         int* tileStats, unsigned* err, cudaStream_t st) {
+  size_t smem = 3 * kRowsPerTF * sizeof(int);
+  cudaFuncSetAttribute(k_ingest_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (nTiles > 0) {
+    k_ingest_stats<<<nTiles, 512, smem, st>>>(tfs, tiles, tileSize, G, tileStats, err);
+    ++g_launch_count;
+  }
+}
+
+void launch_row_reduce(const TFDesc* tfs, int nTF, int* tileStats, int* rowCnt, int* rowMin, int* rowMax,
+                       cudaStream_t st) {
+  int n = nTF * kRowsPerTF;
+  k_row_reduce<<<(n + 255) / 256, 256, 0, st>>>(tfs, nTF, tileStats, rowCnt, rowMin, rowMax);
+  ++g_launch_count;
+}
+
+void launch_grid(int nRows, const int* rowCnt, const int* rowMin, const int* rowMax, const GeomConst* G,
+                 RowGrid* grid, int* nfBlockStart, int nfBlock, int* totals, cudaStream_t st) {
+  k_grid<<<1, 1024, 0, st>>>(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, nfBlock, totals);
+  ++g_launch_count;
+}
+
+void launch_row_scatter(const TFDesc* tfs, const int2* tiles, int nTiles, int tileSize, const GeomConst* G,
+                        const int* tileStats, const RowGrid* grid, int4* bucket, cudaStream_t st) {
+  if (nTiles > 0) {
+    k_row_scatter<<<nTiles, 512, 0, st>>>(tfs, tiles, tileSize, G, tileStats, grid, bucket);
+    ++g_launch_count;
+  }
+}
+
+void launch_cell_sort(int nRows, const RowGrid* grid, const int4* bucket, int* cellStart, int2* syz, int* sorig,
+                      int* gscratch, const int* totals, cudaStream_t st) {
+  if (nRows > 0) {
+    k_cell_sort<<<nRows, 256, 0, st>>>(grid, bucket, cellStart, syz, sorig, gscratch);
+    ++g_launch_count;
+  }
+  k_cell_sentinel<<<1, 1, 0, st>>>(cellStart, totals);
+  ++g_launch_count;
+}
+
+}  // namespace o2tpc

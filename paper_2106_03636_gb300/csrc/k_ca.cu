@@ -1,0 +1,255 @@
+// k_ca.cu - cellular-automaton seeding: NeighboursFinder, NeighboursCleaner,
+// StartHitsFinder, plus the device-wide scan used for ordered compaction.
+//
+// All decisions here are integer: the straightness metric of a hit h with an
+// upper neighbour u (row r+1) and a lower neighbour d (row r-1) is
+//   D = 2077 (2 y_h - y_u - y_d)^2 + 1536 (2 z_h - z_u - z_d)^2
+// (a 2-dof chi2 scaled by 6 sigma_y^2 * 6 sigma_z^2 in integer units; it fits
+// in 31 bits inside the windows), accepted when D <= 16 * 1536 * 2077, and
+// the winner is the lexicographic minimum of (D, u, d), which no enumeration
+// order can change.
+#include "o2tpc_kernels.cuh"
+
+namespace o2tpc {
+
+// K4: one thread per hit; blocks tile the rows (nfBlockStart maps a block to
+// its row).
+__global__ void __launch_bounds__(kNFBlock) k_neighbours(const RowGrid* __restrict__ grid,
+                                                         const int* __restrict__ nfBlockStart, int nRows,
+                                                         const int* __restrict__ cellStart,
+                                                         const int2* __restrict__ syz, const GeomConst* __restrict__ G,
+                                                         int* __restrict__ upRaw, int* __restrict__ dnRaw) {
+  if ((int)blockIdx.x >= nfBlockStart[nRows]) return;  // launched with an upper bound of blocks
+  const int R = upper_bound_i32(nfBlockStart, nRows + 1, blockIdx.x) - 1;
+  const RowGrid g = grid[R];
+  const int h = g.start + (blockIdx.x - nfBlockStart[R]) * kNFBlock + threadIdx.x;
+  if (h >= g.start + g.count) return;
+  const int r = (R % kRowsPerTF) % kNRow;
+  int bu = -1, bd = -1;
+  if (r >= 1 && r <= kNRow - 2) {
+    const RowGrid gu = grid[R + 1], gd = grid[R - 1];
+    const int npu = G->npads[r + 1], npd = G->npads[r - 1];
+    const int2 hh = syz[h];
+    const long long yh = hh.x, zh = hh.y;
+    int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
+    if (cell_range(gu, npu, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, uy0, uy1, uz0, uz1) &&
+        cell_range(gd, npd, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, dy0, dy1, dz0, dz1)) {
+      int bestD = INT_MAX;
+      const int y2 = 2 * hh.x, z2 = 2 * hh.y;
+      for (int izu = uz0; izu <= uz1; ++izu) {
+        const int ua = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy0);
+        const int ub = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy1 + 1);
+        for (int u = ua; u < ub; ++u) {
+          const int2 pu = __ldg(syz + u);
+          if (abs(pu.x - hh.x) > kWinY || abs(pu.y - hh.y) > kWinZ) continue;
+          for (int izd = dz0; izd <= dz1; ++izd) {
+            const int da = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy0);
+            const int db = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy1 + 1);
+            for (int d = da; d < db; ++d) {
+              const int2 pd = __ldg(syz + d);
+              if (abs(pd.x - hh.x) > kWinY || abs(pd.y - hh.y) > kWinZ) continue;
+              const int ey = y2 - pu.x - pd.x, ez = z2 - pu.y - pd.y;
+              const int D = kWeightY * ey * ey + kWeightZ * ez * ez;
+              if (D > kMaxMetric) continue;
+              if (D < bestD || (D == bestD && (u < bu || (u == bu && d < bd)))) {
+                bestD = D;
+                bu = u;
+                bd = d;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  upRaw[h] = bu;
+  dnRaw[h] = bd;
+}
+
+// K5 + K6a: reciprocity filter on the raw (snapshot) links and the chain-head
+// flag: dn < 0, up >= 0, up[up] >= 0 (chains of at least three hits).
+__global__ void k_clean(int n, const int* __restrict__ upRaw, const int* __restrict__ dnRaw, int* __restrict__ up,
+                        int* __restrict__ dn, int* __restrict__ startFlag) {
+  int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= n) return;
+  int u = upRaw[h], d = dnRaw[h];
+  int uc = (u >= 0 && dnRaw[u] == h) ? u : -1;
+  int dc = (d >= 0 && upRaw[d] == h) ? d : -1;
+  up[h] = uc;
+  dn[h] = dc;
+  int flag = 0;
+  if (dc < 0 && uc >= 0) {
+    int uu = upRaw[uc];
+    int uuc = (uu >= 0 && dnRaw[uu] == uc) ? uu : -1;
+    flag = uuc >= 0;
+  }
+  startFlag[h] = flag;
+}
+
+// --------------------------------------------------------------- scans
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ inline int warp_incl(int x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// inclusive block scan for blockDim == 1024; returns the exclusive prefix
+__device__ inline int block_excl(int v, int* total) {
+  __shared__ int ws[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = warp_incl(v);
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) ws[lane] = warp_incl(ws[lane]);
+  __syncthreads();
+  int incl = x + (w > 0 ? ws[w - 1] : 0);
+  if (total) *total = ws[31];
+  __syncthreads();
+  return incl - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int* __restrict__ in, int n, int* __restrict__ sums) {
+  long long base = (long long)blockIdx.x * kScanTile;
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    long long i = base + (long long)k * kScanThreads + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  int tot;
+  block_excl(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_mid(int* __restrict__ sums, int nb) {
+  int per = (nb + kScanThreads - 1) / kScanThreads;
+  int b = threadIdx.x * per, e = min(nb, b + per);
+  int s = 0;
+  for (int i = b; i < e; ++i) s += sums[i];
+  int off = block_excl(s, nullptr);
+  for (int i = b; i < e; ++i) {
+    int v = sums[i];
+    sums[i] = off;
+    off += v;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restrict__ in, int n,
+                                                             const int* __restrict__ sums, int* __restrict__ out) {
+  long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    long long i = base + k;
+    v[k] = (i < n) ? in[i] : 0;
+    s += v[k];
+  }
+  int tot;
+  int off = block_excl(s, &tot) + sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    long long i = base + k;
+    if (i < n) out[i] = off;
+    off += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = off;
+}
+
+// out[0..n] = exclusive scan of in[0..n-1], out[n] = total; out may alias in.
+// scratch: >= scan_scratch_ints(n) ints.
+int scan_scratch_ints(long long n) { return (int)((n + kScanTile - 1) / kScanTile) + 1; }
+
+void scan_exclusive(const int* in, int* out, int n, int* scratch, cudaStream_t st) {
+  int nb = (n + kScanTile - 1) / kScanTile;
+  if (nb == 0) {
+    cudaMemsetAsync(out, 0, sizeof(int), st);
+    return;
+  }
+  k_scan_sums<<<nb, kScanThreads, 0, st>>>(in, n, scratch);
+  ++g_launch_count;
+  k_scan_mid<<<1, kScanThreads, 0, st>>>(scratch, nb);
+  ++g_launch_count;
+  k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, n, scratch, out);
+  ++g_launch_count;
+}
+
+// ordered compaction: out[pos[i]] = i for flag[i] != 0 (pos = exclusive scan)
+__global__ void k_compact(int n, const int* __restrict__ flag, const int* __restrict__ pos, int* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) out[pos[i]] = i;
+}
+
+// first entry of a sorted list that is >= each TF's first sorted hit
+__global__ void k_tf_ranges(int nTF, const RowGrid* __restrict__ grid, const int* __restrict__ list, int nList,
+                            int* __restrict__ tfBegin) {
+  int tf = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tf > nTF) return;
+  int key = (tf == nTF) ? INT_MAX : grid[tf * kRowsPerTF].start;
+  int lo = 0, hi = nList;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (list[m] < key) lo = m + 1;
+    else hi = m;
+  }
+  tfBegin[tf] = (tf == nTF) ? nList : lo;
+}
+
+// out[i] = first index of the sorted list with list[j] >= keys[i]
+__global__ void k_lower_bounds(const int* __restrict__ list, int nList, const int* __restrict__ keys, int nKeys,
+                               int* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nKeys) return;
+  const int key = keys[i];
+  int lo = 0, hi = nList;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (list[m] < key) lo = m + 1;
+    else hi = m;
+  }
+  out[i] = lo;
+}
+
+// ------------------------------------------------------------- launchers
+void launch_lower_bounds(const int* list, int nList, const int* keys, int nKeys, int* out, cudaStream_t st) {
+  if (nKeys > 0) {
+    k_lower_bounds<<<(nKeys + 127) / 128, 128, 0, st>>>(list, nList, keys, nKeys, out);
+    ++g_launch_count;
+  }
+}
+
+void launch_neighbours(int nfBlocks, const RowGrid* grid, const int* nfBlockStart, int nRows, const int* cellStart,
+                       const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw, cudaStream_t st) {
+  if (nfBlocks > 0)
+    k_neighbours<<<nfBlocks, kNFBlock, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw);
+    ++g_launch_count;
+}
+
+void launch_clean(int n, const int* upRaw, const int* dnRaw, int* up, int* dn, int* startFlag, cudaStream_t st) {
+  if (n > 0) {
+    k_clean<<<(n + 255) / 256, 256, 0, st>>>(n, upRaw, dnRaw, up, dn, startFlag);
+    ++g_launch_count;
+  }
+}
+
+void launch_compact(int n, const int* flag, const int* pos, int* out, cudaStream_t st) {
+  if (n > 0) {
+    k_compact<<<(n + 255) / 256, 256, 0, st>>>(n, flag, pos, out);
+    ++g_launch_count;
+  }
+}
+
+void launch_tf_ranges(int nTF, const RowGrid* grid, const int* list, int nList, int* tfBegin, cudaStream_t st) {
+  k_tf_ranges<<<(nTF + 1 + 63) / 64, 64, 0, st>>>(nTF, grid, list, nList, tfBegin);
+  ++g_launch_count;
+}
+
+}  // namespace o2tpc

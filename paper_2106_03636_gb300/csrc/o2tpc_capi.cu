@@ -1,0 +1,952 @@
+// o2tpc_capi.cu - host runtime behind include/o2tpc.h.
+//
+// One context owns one CUDA stream and one worker thread (the paper drives
+// each GPU from one CPU core, Sec. 3.1.1).  Submitted Time Frames wait in a
+// FIFO; the worker admits as many as fit the memory budget and the batch
+// limits and runs them as one batch: every step is one launch over all TFs
+// of the batch (rows are indexed tf * 5472 + sector * 152 + row, so no step
+// mixes TFs and each TF's result does not depend on its batch mates).  Four
+// host synchronisations per batch read the data-dependent sizes (start hits,
+// sector tracks, merge pairs, tracks) that the following buffers need.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "o2tpc.h"
+#include "o2tpc_kernels.cuh"
+
+using namespace o2tpc;
+
+thread_local long long o2tpc::g_launch_count = 0;
+
+namespace {
+
+constexpr int kTileMin = 65536;           // clusters per ingest tile, at least
+constexpr int kTilesPerTFMax = 4096;
+constexpr uint64_t kMaxBatchHits = 2000000000ull;
+
+struct CudaError {
+  cudaError_t e;
+  int line;
+};
+#define CK(x)                                             \
+  do {                                                    \
+    cudaError_t e_ = (x);                                 \
+    if (e_ != cudaSuccess) throw CudaError{e_, __LINE__}; \
+  } while (0)
+// checks the last launch
+#define CKL() CK(cudaGetLastError())
+
+struct AllocError {};
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ----------------------------------------------------------- allocations
+struct Ctx;
+
+struct DevBlock {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// All device buffers of one batch; freed when the last of its TFs is released
+// (or at once when stages are not kept).
+struct BatchMem {
+  Ctx* ctx = nullptr;
+  std::vector<DevBlock> blocks;
+  int refs = 0;
+  // stage views (valid while kept)
+  int nTF = 0, nRows = 0, N = 0, nTl = 0, nSt = 0, nCells = 0;
+  std::vector<int> tfHitBase, tfHitEnd, tfInBase, tfTlBegin, tfStBegin, tfCellBase, tfCellEnd;
+  RowGrid* grid = nullptr;
+  int *cellStart = nullptr, *sorig = nullptr, *upRaw = nullptr, *dnRaw = nullptr, *up = nullptr, *dn = nullptr;
+  int2* syz = nullptr;
+  int* starts = nullptr;
+  TrackletBufs tb{};
+  SectorTrackBufs sb{};
+  MergeBufs mb{};
+  ~BatchMem();
+  void* alloc(size_t bytes);
+};
+
+struct Job {
+  uint64_t ticket = 0;
+  o2tpc_tf tf{};
+  uint64_t footprint = 0;
+  double t_submit = 0, t_start = 0, t_end = 0;
+  bool done = false;
+  int status = O2TPC_OK;
+  // result storage
+  o2tpc_result res{};
+  std::vector<uint64_t> off;
+  std::vector<uint32_t> cl, zref;
+  std::vector<float> x, alpha, par, cov, chi2;
+  std::vector<int32_t> ndf;
+  std::vector<uint8_t> sector, flags;
+  std::shared_ptr<BatchMem> mem;  // kept stages
+  int tfIndex = 0;
+};
+
+struct Ctx {
+  o2tpc_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool ownStream = false;
+  GeomConst* dGeom = nullptr;
+  GeomConst hGeom{};
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cvWork, cvDone;
+  std::deque<std::shared_ptr<Job>> queue;
+  std::map<uint64_t, std::shared_ptr<Job>> jobs;
+  uint64_t nextTicket = 1;
+  int inflight = 0;
+  bool stop = false;
+  int fatal = O2TPC_OK;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t evs[11] = {};
+  // pinned staging for descriptors and results
+  void* hStage = nullptr;
+  size_t hStageBytes = 0;
+
+  void* dev_alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (cfg.dev_alloc) {
+      p = cfg.dev_alloc(bytes, cfg.alloc_user);
+    } else {
+      if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+      }
+    }
+    if (!p) throw AllocError{};
+    return p;
+  }
+  void dev_free(void* p) {
+    if (!p) return;
+    if (cfg.dev_free) cfg.dev_free(p, cfg.alloc_user);
+    else cudaFreeAsync(p, stream);
+  }
+  void* stage(size_t bytes) {
+    if (bytes > hStageBytes) {
+      if (hStage) cudaFreeHost(hStage);
+      hStage = nullptr;
+      size_t nb = std::max<size_t>(bytes, hStageBytes * 2);
+      CK(cudaMallocHost(&hStage, nb));
+      hStageBytes = nb;
+    }
+    return hStage;
+  }
+};
+
+BatchMem::~BatchMem() {
+  if (!ctx) return;
+  for (auto& b : blocks) ctx->dev_free(b.p);
+}
+void* BatchMem::alloc(size_t bytes) {
+  void* p = ctx->dev_alloc(bytes);
+  blocks.push_back({p, bytes});
+  return p;
+}
+
+template <typename T>
+T* dalloc(BatchMem& m, size_t count) {
+  return static_cast<T*>(m.alloc(sizeof(T) * std::max<size_t>(count, 1)));
+}
+
+uint64_t footprint_of(uint64_t n) { return 160ull * n + (64ull << 20); }
+
+int read_int(Ctx* c, const int* dptr) {
+  int v = 0;
+  CK(cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return v;
+}
+
+void fill_geom(GeomConst& g, double bz, double vd) {
+  const double pi = 3.14159265358979323846;
+  for (int r = 0; r < kNRow; ++r) {
+    double x = 85.0 + (double)r * 160.0 / 151.0;
+    g.rowx[r] = (float)x;
+    g.rowx_d[r] = x;
+    g.npads[r] = (int)std::floor(2.0 * x * std::tan(10.0 * pi / 180.0) / 0.4);
+  }
+  for (int s = 0; s < 18; ++s) g.sec_alpha[s] = (float)((s * 20.0 + 10.0) * pi / 180.0);
+  g.tan10 = (float)std::tan(10.0 * pi / 180.0);
+  g.rot_cos = (float)std::cos(20.0 * pi / 180.0);
+  g.rot_sin = (float)std::sin(20.0 * pi / 180.0);
+  g.rot_cos_d = std::cos(20.0 * pi / 180.0);
+  g.rot_sin_d = std::sin(20.0 * pi / 180.0);
+  g.bzc_d = -0.00299792458 * bz;
+  g.bzc = (float)g.bzc_d;
+  g.zunit_d = 0.003125 * vd;
+  g.zunit = (float)g.zunit_d;
+  g.kz = (float)(1.0 / (0.003125 * vd));
+}
+
+// ------------------------------------------------------------ the batch
+void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
+  cudaStream_t st = c->stream;
+  const bool keep = (c->cfg.flags & O2TPC_FLAG_KEEP_STAGES) != 0;
+  auto mem = std::make_shared<BatchMem>();
+  mem->ctx = c;
+  BatchMem& M = *mem;
+  const int B = (int)jobs.size();
+  const int nRows = B * kRowsPerTF;
+  M.nTF = B;
+  M.nRows = nRows;
+  CK(cudaEventRecord(c->ev0, st));
+  g_launch_count = 0;
+
+  // ---- inputs and TF table
+  std::vector<TFDesc> tfd(B);
+  std::vector<int2> tiles;
+  long long N = 0;
+  for (int i = 0; i < B; ++i) {
+    const o2tpc_tf& t = jobs[i]->tf;
+    TFDesc d{};
+    d.format = t.format;
+    d.n = (int)t.n;
+    d.inBase = (int)N;
+    if (t.location == O2TPC_LOC_DEVICE || t.n == 0) {
+      d.in0 = t.format == O2TPC_FMT_FIXED ? t.packed : (const void*)t.sector;
+      d.in1 = t.row;
+      d.y = t.y;
+      d.z = t.z;
+    } else if (t.format == O2TPC_FMT_FIXED) {
+      void* p = M.alloc(12 * t.n);
+      CK(cudaMemcpyAsync(p, t.packed, 12 * t.n, cudaMemcpyHostToDevice, st));
+      d.in0 = p;
+    } else {
+      uint8_t* p = dalloc<uint8_t>(M, 10 * t.n + 64);
+      uint8_t* ps = p;
+      uint8_t* pr = p + t.n;
+      float* py = reinterpret_cast<float*>(p + ((2 * t.n + 15) / 16) * 16);
+      float* pz = py + t.n;
+      CK(cudaMemcpyAsync(ps, t.sector, t.n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(pr, t.row, t.n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(py, t.y, 4 * t.n, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(pz, t.z, 4 * t.n, cudaMemcpyHostToDevice, st));
+      d.in0 = ps;
+      d.in1 = pr;
+      d.y = py;
+      d.z = pz;
+    }
+    int tileSize = std::max(kTileMin, (int)((t.n + kTilesPerTFMax - 1) / kTilesPerTFMax));
+    d.tileBase = (int)tiles.size();
+    d.nTiles = (int)((t.n + tileSize - 1) / tileSize);
+    for (int k = 0; k < d.nTiles; ++k) tiles.push_back(make_int2(i, k * tileSize));
+    tfd[i] = d;
+    N += (long long)t.n;
+  }
+  // one tile size for the launch: the largest any TF asked for
+  int tileSize = kTileMin;
+  for (int i = 0; i < B; ++i) tileSize = std::max(tileSize, (int)((jobs[i]->tf.n + kTilesPerTFMax - 1) / kTilesPerTFMax));
+  tiles.clear();
+  for (int i = 0; i < B; ++i) {
+    tfd[i].tileBase = (int)tiles.size();
+    tfd[i].nTiles = (int)((jobs[i]->tf.n + tileSize - 1) / tileSize);
+    for (int k = 0; k < tfd[i].nTiles; ++k) tiles.push_back(make_int2(i, k * tileSize));
+  }
+  const int nTiles = (int)tiles.size();
+  const int n = (int)N;
+  M.N = n;
+  TFDesc* dTF = dalloc<TFDesc>(M, B);
+  int2* dTiles = dalloc<int2>(M, nTiles);
+  {
+    size_t b1 = sizeof(TFDesc) * B, b2 = sizeof(int2) * nTiles;
+    char* h = static_cast<char*>(c->stage(b1 + b2));
+    memcpy(h, tfd.data(), b1);
+    memcpy(h + b1, tiles.data(), b2);
+    CK(cudaMemcpyAsync(dTF, h, b1, cudaMemcpyHostToDevice, st));
+    if (nTiles) CK(cudaMemcpyAsync(dTiles, h + b1, b2, cudaMemcpyHostToDevice, st));
+  }
+  unsigned* dErr = dalloc<unsigned>(M, 4);
+  CK(cudaMemsetAsync(dErr, 0, 16, st));
+  const GeomConst* G = c->dGeom;
+
+  // ---- A1-A4: ingest, row statistics, grid, sort
+  CK(cudaEventRecord(c->evs[0], st));
+  int* tileStats = dalloc<int>(M, (size_t)std::max(nTiles, 1) * 3 * kRowsPerTF);
+  int* rowCnt = dalloc<int>(M, nRows);
+  int* rowMin = dalloc<int>(M, nRows);
+  int* rowMax = dalloc<int>(M, nRows);
+  RowGrid* grid = dalloc<RowGrid>(M, nRows + 1);
+  int* nfBlockStart = dalloc<int>(M, nRows + 1);
+  int* totals = dalloc<int>(M, 4);
+  launch_ingest_stats(dTF, dTiles, nTiles, tileSize, G, tileStats, dErr, st);
+  CKL();
+  launch_row_reduce(dTF, B, tileStats, rowCnt, rowMin, rowMax, st);
+  CKL();
+  launch_grid(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, kNFBlock, totals, st);
+  CKL();
+  const long long cellsMax = (long long)n / kHitsPerCell + 46ll * nRows + 1;
+  CK(cudaEventRecord(c->evs[1], st));
+  int* cellStart = dalloc<int>(M, cellsMax + 1);
+  int* gscratch = dalloc<int>(M, cellsMax);
+  int4* bucket = dalloc<int4>(M, n);
+  int2* syz = dalloc<int2>(M, n);
+  int* sorig = dalloc<int>(M, n);
+  launch_row_scatter(dTF, dTiles, nTiles, tileSize, G, tileStats, grid, bucket, st);
+  CKL();
+  launch_cell_sort(nRows, grid, bucket, cellStart, syz, sorig, gscratch, totals, st);
+  CKL();
+
+  // ---- A5-A7: neighbours, cleaner, start hits
+  CK(cudaEventRecord(c->evs[2], st));
+  int* upRaw = dalloc<int>(M, n);
+  int* dnRaw = dalloc<int>(M, n);
+  int* up = dalloc<int>(M, n);
+  int* dn = dalloc<int>(M, n);
+  int* flag = dalloc<int>(M, n + 1);
+  int* pos = dalloc<int>(M, n + 1);
+  int* scratch = dalloc<int>(M, scan_scratch_ints((long long)n + 8) + (nRows + 8) * 2 / 4096 + 64);
+  const int nfBlocksMax = n / kNFBlock + nRows + 1;
+  launch_neighbours(nfBlocksMax, grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw, st);
+  CKL();
+  CK(cudaEventRecord(c->evs[3], st));
+  launch_clean(n, upRaw, dnRaw, up, dn, flag, st);
+  CKL();
+  scan_exclusive(flag, pos, n, scratch, st);
+  CKL();
+  const int nTl = read_int(c, pos + n);  // sync 1
+  M.nTl = nTl;
+  int* starts = dalloc<int>(M, nTl);
+  launch_compact(n, flag, pos, starts, st);
+  CKL();
+  int* tlTfBegin = dalloc<int>(M, B + 1);
+  launch_tf_ranges(B, grid, starts, nTl, tlTfBegin, st);
+  CKL();
+
+  // ---- A8: tracklets
+  CK(cudaEventRecord(c->evs[4], st));
+  TrackletBufs tb;
+  tb.nhits = dalloc<int>(M, nTl + 1);
+  tb.nasc = dalloc<int>(M, nTl);
+  tb.hits = dalloc<int>(M, (size_t)nTl * kMaxTlHits);
+  tb.rows = dalloc<uint8_t>(M, (size_t)nTl * kMaxTlHits);
+  tb.state = dalloc<float>(M, (size_t)nTl * 21);
+  tb.zref = dalloc<int>(M, nTl);
+  launch_tracklets(nTl, starts, up, grid, nRows, cellStart, syz, G, tb, st);
+  CKL();
+
+  // ---- A9: selection
+  CK(cudaEventRecord(c->evs[5], st));
+  unsigned long long* w = dalloc<unsigned long long>(M, n);
+  CK(cudaMemsetAsync(w, 0, sizeof(unsigned long long) * std::max(n, 1), st));
+  launch_ownership(nTl, tlTfBegin, B, tb, w, st);
+  CKL();
+  int* nSeg = dalloc<int>(M, nTl + 1);
+  int* nSegHits = dalloc<int>(M, nTl + 1);
+  int* segPos = dalloc<int>(M, nTl + 1);
+  int* segHitPos = dalloc<int>(M, nTl + 1);
+  launch_segments_count(nTl, tlTfBegin, B, tb, w, nSeg, nSegHits, st);
+  CKL();
+  scan_exclusive(nSeg, segPos, nTl, scratch, st);
+  CKL();
+  scan_exclusive(nSegHits, segHitPos, nTl, scratch, st);
+  CKL();
+  int hv[2];
+  CK(cudaMemcpyAsync(&hv[0], segPos + nTl, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&hv[1], segHitPos + nTl, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));  // sync 2
+  const int nSt = hv[0], nStHits = hv[1];
+  M.nSt = nSt;
+  SectorTrackBufs sb;
+  sb.tl = dalloc<int>(M, nSt);
+  sb.sector = dalloc<int>(M, nSt);
+  sb.tf = dalloc<int>(M, nSt);
+  sb.zref = dalloc<int>(M, nSt);
+  sb.off = dalloc<int>(M, nSt + 1);
+  sb.hits = dalloc<int>(M, nStHits);
+  sb.rows = dalloc<uint8_t>(M, nStHits);
+  sb.in = dalloc<float>(M, (size_t)nSt * 21);
+  sb.out = dalloc<float>(M, (size_t)nSt * 21);
+  launch_segments_write(nTl, tlTfBegin, B, tb, w, segPos, segHitPos, syz, grid, nRows, sb, st);
+  CKL();
+  CK(cudaMemcpyAsync(sb.off + nSt, segHitPos + nTl, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  CK(cudaEventRecord(c->evs[6], st));
+  launch_sector_fit(nSt, tb, syz, G, sb, st);
+  CKL();
+  int* stTfBegin = dalloc<int>(M, B + 1);
+  {
+    std::vector<int> keys(B + 1);
+    for (int i = 0; i <= B; ++i) keys[i] = i;
+    int* dk = dalloc<int>(M, B + 1);
+    CK(cudaMemcpyAsync(dk, keys.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st));
+    launch_lower_bounds(sb.tf, nSt, dk, B + 1, stTfBegin, st);
+    CKL();
+    CK(cudaStreamSynchronize(st));
+  }
+
+  // ---- A10: merger
+  CK(cudaEventRecord(c->evs[7], st));
+  const int nKeys = B * kNSec * 2;
+  MergeBufs mb;
+  mb.keyIn = dalloc<int>(M, nSt);
+  mb.keyOut = dalloc<int>(M, nSt);
+  mb.listCnt = dalloc<int>(M, nKeys + 1);
+  mb.listStart = dalloc<int>(M, nKeys + 1);
+  mb.listItems = dalloc<int>(M, nSt);
+  mb.listKey = dalloc<int>(M, nSt);
+  mb.pairCount = dalloc<int>(M, 1);
+  mb.edgeCnt = dalloc<int>(M, nKeys + 1);
+  mb.edgeStart = dalloc<int>(M, nKeys + 1);
+  mb.next = dalloc<int>(M, nSt);
+  mb.prev = dalloc<int>(M, nSt);
+  mb.reached = dalloc<int>(M, nSt);
+  mb.pairCap = std::max(1024, 2 * nSt);
+  mb.pairs = dalloc<float4>(M, mb.pairCap);
+  mb.pairsSorted = dalloc<float4>(M, mb.pairCap);
+  mb.sortScratch = dalloc<float4>(M, 2 * (size_t)std::max(mb.pairCap, nSt) + 16);
+  launch_merge_keys(nSt, sb, G, mb, nKeys, scratch, st);
+  CKL();
+  launch_merge_pairs(nSt, sb, G, mb, dErr, st);
+  CKL();
+  int nPairs = read_int(c, mb.pairCount);  // sync 3
+  if (nPairs > mb.pairCap) {
+    mb.pairCap = nPairs + 1024;
+    mb.pairs = dalloc<float4>(M, mb.pairCap);
+    mb.pairsSorted = dalloc<float4>(M, mb.pairCap);
+    mb.sortScratch = dalloc<float4>(M, 2 * (size_t)std::max(mb.pairCap, nSt) + 16);
+    launch_merge_pairs(nSt, sb, G, mb, dErr, st);  // the overflow bit of the first pass is ignored
+    nPairs = read_int(c, mb.pairCount);
+  }
+  launch_merge_select(nPairs, nKeys, mb, scratch, st);
+  CKL();
+  int* headFlag = dalloc<int>(M, nSt + 1);
+  int* headPos = dalloc<int>(M, nSt + 1);
+  launch_chains(nSt, B, stTfBegin, mb, headFlag, st);
+  CKL();
+  scan_exclusive(headFlag, headPos, nSt, scratch, st);
+  CKL();
+  const int nHeads = read_int(c, headPos + nSt);  // sync 4
+  int* heads = dalloc<int>(M, nHeads);
+  launch_compact(nSt, headFlag, headPos, heads, st);
+  CKL();
+
+  // ---- A11: final refit and output
+  CK(cudaEventRecord(c->evs[8], st));
+  int* trkNcl = dalloc<int>(M, nHeads + 1);
+  OutBufs ob;
+  ob.off = dalloc<int>(M, nHeads + 1);
+  ob.cl = dalloc<int>(M, nStHits);
+  ob.x = dalloc<float>(M, nHeads);
+  ob.alpha = dalloc<float>(M, nHeads);
+  ob.par = dalloc<float>(M, (size_t)nHeads * 5);
+  ob.cov = dalloc<float>(M, (size_t)nHeads * 15);
+  ob.chi2 = dalloc<float>(M, nHeads);
+  ob.ndf = dalloc<int>(M, nHeads);
+  ob.sector = dalloc<uint8_t>(M, nHeads);
+  ob.flags = dalloc<uint8_t>(M, nHeads);
+  ob.zref = dalloc<int>(M, nHeads);
+  ob.nFallback = dalloc<int>(M, 1);
+  CK(cudaMemsetAsync(ob.nFallback, 0, sizeof(int), st));
+  launch_chain_counts(nHeads, heads, sb, mb, trkNcl, st);
+  CKL();
+  scan_exclusive(trkNcl, ob.off, nHeads, scratch, st);
+  CKL();
+  launch_final_refit(nHeads, heads, sb, mb, syz, sorig, G, (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, ob, st);
+  CKL();
+  int* trkTfBegin = dalloc<int>(M, B + 1);
+  launch_lower_bounds(heads, nHeads, stTfBegin, B + 1, trkTfBegin, st);
+  CKL();
+  CK(cudaEventRecord(c->ev1, st));
+  CK(cudaEventRecord(c->evs[9], st));
+
+  // ---- A12: download
+  const size_t nT = (size_t)nHeads;
+  const size_t bOff = 4 * (nT + 1), bCl = 4 * (size_t)nStHits, bX = 4 * nT, bPar = 20 * nT, bCov = 60 * nT;
+  auto r16 = [](size_t b) { return (b + 15) / 16 * 16; };
+  const size_t tot = r16(bOff) + r16(bCl) + 5 * r16(bX) /*x alpha chi2 ndf zref*/ + r16(bPar) + r16(bCov) +
+                     2 * r16(nT) /*sector flags*/ + 3 * r16(sizeof(int) * (B + 1)) + 2 * r16(4);
+  char* h = static_cast<char*>(c->stage(tot));
+  char* q = h;
+  auto take = [&](const void* dsrc, size_t bytes) -> char* {
+    char* dst = q;
+    if (bytes) CK(cudaMemcpyAsync(dst, dsrc, bytes, cudaMemcpyDeviceToHost, st));
+    q += (bytes + 15) / 16 * 16;
+    return dst;
+  };
+  const int* hOff = reinterpret_cast<const int*>(take(ob.off, bOff));
+  const int* hCl = reinterpret_cast<const int*>(take(ob.cl, bCl));
+  const float* hX = reinterpret_cast<const float*>(take(ob.x, bX));
+  const float* hA = reinterpret_cast<const float*>(take(ob.alpha, bX));
+  const float* hPar = reinterpret_cast<const float*>(take(ob.par, bPar));
+  const float* hCov = reinterpret_cast<const float*>(take(ob.cov, bCov));
+  const float* hChi = reinterpret_cast<const float*>(take(ob.chi2, bX));
+  const int* hNdf = reinterpret_cast<const int*>(take(ob.ndf, bX));
+  const uint8_t* hSec = reinterpret_cast<const uint8_t*>(take(ob.sector, nT));
+  const uint8_t* hFl = reinterpret_cast<const uint8_t*>(take(ob.flags, nT));
+  const int* hZr = reinterpret_cast<const int*>(take(ob.zref, bX));
+  const int* hTrkTf = reinterpret_cast<const int*>(take(trkTfBegin, sizeof(int) * (B + 1)));
+  const int* hStTf = reinterpret_cast<const int*>(take(stTfBegin, sizeof(int) * (B + 1)));
+  const int* hTlTf = reinterpret_cast<const int*>(take(tlTfBegin, sizeof(int) * (B + 1)));
+  const unsigned* hErr = reinterpret_cast<const unsigned*>(take(dErr, 4));
+  const int* hFb = reinterpret_cast<const int*>(take(ob.nFallback, 4));
+  std::vector<RowGrid> tfFirstRow(B);
+  for (int i = 0; i < B; ++i) CK(cudaMemcpyAsync(&tfFirstRow[i], grid + (size_t)i * kRowsPerTF, sizeof(RowGrid),
+                                                 cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(c->evs[10], st));
+  CK(cudaStreamSynchronize(st));
+  float devMs = 0.f;
+  float stageMs[10];
+  for (int k = 0; k < 10; ++k) {
+    stageMs[k] = 0.f;
+    cudaEventElapsedTime(&stageMs[k], c->evs[k], c->evs[k + 1]);
+  }
+  const long long nLaunch = g_launch_count;
+  cudaEventElapsedTime(&devMs, c->ev0, c->ev1);
+  (void)hFb;
+  const bool inputBad = (*hErr & kErrInput) != 0;
+
+  const double tEnd = now_ms();
+  M.tfHitBase.resize(B);
+  M.tfHitEnd.resize(B);
+  M.tfInBase.resize(B);
+  M.tfTlBegin.assign(hTlTf, hTlTf + B + 1);
+  M.tfStBegin.assign(hStTf, hStTf + B + 1);
+  for (int i = 0; i < B; ++i) {
+    M.tfHitBase[i] = tfFirstRow[i].start;
+    M.tfHitEnd[i] = (i + 1 < B) ? tfFirstRow[i + 1].start : n;
+    M.tfInBase[i] = tfd[i].inBase;
+  }
+  for (int i = 0; i < B; ++i) {
+    Job& J = *jobs[i];
+    const int t0 = hTrkTf[i], t1 = hTrkTf[i + 1], nt = t1 - t0;
+    J.off.resize(nt + 1);
+    const int c0 = hOff[t0];
+    for (int k = 0; k <= nt; ++k) J.off[k] = (uint64_t)(hOff[t0 + k] - c0);
+    const int ncl = hOff[t1] - c0;
+    J.cl.resize(ncl);
+    for (int k = 0; k < ncl; ++k) J.cl[k] = (uint32_t)(hCl[c0 + k] - tfd[i].inBase);
+    J.x.assign(hX + t0, hX + t1);
+    J.alpha.assign(hA + t0, hA + t1);
+    J.par.assign(hPar + 5 * (size_t)t0, hPar + 5 * (size_t)t1);
+    J.cov.assign(hCov + 15 * (size_t)t0, hCov + 15 * (size_t)t1);
+    J.chi2.assign(hChi + t0, hChi + t1);
+    J.ndf.assign(hNdf + t0, hNdf + t1);
+    J.sector.assign(hSec + t0, hSec + t1);
+    J.flags.assign(hFl + t0, hFl + t1);
+    J.zref.resize(nt);
+    uint64_t fb = 0;
+    for (int k = 0; k < nt; ++k) {
+      J.zref[k] = (uint32_t)hZr[t0 + k];
+      fb += (J.flags[k] & 1) ? 1 : 0;
+    }
+    o2tpc_result& R = J.res;
+    R.n_tracks = (uint64_t)nt;
+    R.offsets = J.off.data();
+    R.cluster_idx = J.cl.data();
+    R.x = J.x.data();
+    R.alpha = J.alpha.data();
+    R.par = J.par.data();
+    R.cov = J.cov.data();
+    R.chi2 = J.chi2.data();
+    R.ndf = J.ndf.data();
+    R.sector = J.sector.data();
+    R.flags = J.flags.data();
+    R.zeta_ref = J.zref.data();
+    R.user_tag = J.tf.user_tag;
+    R.stats.n_clusters = J.tf.n;
+    R.stats.n_tracklets = (uint64_t)(hTlTf[i + 1] - hTlTf[i]);
+    R.stats.n_sector_tracks = (uint64_t)(hStTf[i + 1] - hStTf[i]);
+    R.stats.n_tracks = (uint64_t)nt;
+    R.stats.n_fp64_fallback = fb;
+    R.stats.batch_size = (uint32_t)B;
+    R.stats.ms_queue = (float)(J.t_start - J.t_submit);
+    R.stats.ms_batch = (float)(tEnd - J.t_start);
+    R.stats.ms_device = devMs;
+    R.stats.n_launches = (uint64_t)nLaunch;
+    for (int k = 0; k < 10; ++k) R.stats.ms_stage[k] = stageMs[k];
+    J.status = inputBad ? O2TPC_EINVAL : O2TPC_OK;
+    R.status = J.status;
+    J.tfIndex = i;
+  }
+  if (keep) {
+    M.grid = grid;
+    M.cellStart = cellStart;
+    M.sorig = sorig;
+    M.syz = syz;
+    M.upRaw = upRaw;
+    M.dnRaw = dnRaw;
+    M.up = up;
+    M.dn = dn;
+    M.starts = starts;
+    M.tb = tb;
+    M.sb = sb;
+    M.mb = mb;
+    M.refs = B;
+    for (int i = 0; i < B; ++i) jobs[i]->mem = mem;
+  }
+  // without kept stages the batch memory is freed here (stream-ordered)
+}
+
+void worker_main(Ctx* c) {
+  cudaSetDevice(c->cfg.device);
+  for (;;) {
+    std::vector<std::shared_ptr<Job>> batch;
+    {
+      std::unique_lock<std::mutex> lk(c->mu);
+      c->cvWork.wait(lk, [&] { return c->stop || !c->queue.empty(); });
+      if (c->queue.empty() && c->stop) return;
+      uint64_t fp = 0, hits = 0;
+      const int maxB = (c->cfg.flags & O2TPC_FLAG_NO_BATCHING) ? 1 : c->cfg.max_batch;
+      while (!c->queue.empty() && (int)batch.size() < maxB) {
+        auto& j = c->queue.front();
+        if (!batch.empty() && (fp + j->footprint > c->cfg.mem_budget || hits + j->tf.n > kMaxBatchHits)) break;
+        fp += j->footprint;
+        hits += j->tf.n;
+        batch.push_back(j);
+        c->queue.pop_front();
+      }
+    }
+    const double t0 = now_ms();
+    for (auto& j : batch) j->t_start = t0;
+    int status = O2TPC_OK;
+    if (c->fatal != O2TPC_OK) {
+      status = c->fatal;
+    } else {
+      try {
+        run_batch(c, batch);
+      } catch (const CudaError& e) {
+        std::fprintf(stderr, "o2tpc: CUDA error %s at o2tpc_capi.cu:%d\n", cudaGetErrorString(e.e), e.line);
+        cudaGetLastError();
+        status = O2TPC_ECUDA;
+        c->fatal = O2TPC_ECUDA;
+      } catch (const AllocError&) {
+        status = O2TPC_ENOMEM;
+      } catch (const std::bad_alloc&) {
+        status = O2TPC_ENOMEM;
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(c->mu);
+      for (auto& j : batch) {
+        if (status != O2TPC_OK) {
+          j->status = status;
+          j->res = o2tpc_result{};
+          j->res.status = status;
+          j->res.user_tag = j->tf.user_tag;
+          j->off.assign(1, 0);
+          j->res.offsets = j->off.data();
+        }
+        j->t_end = now_ms();
+        j->done = true;
+      }
+    }
+    c->cvDone.notify_all();
+  }
+}
+
+}  // namespace
+
+// =================================================================== C-ABI
+extern "C" {
+
+const char* o2tpc_strerror(int32_t s) {
+  switch (s) {
+    case O2TPC_OK: return "ok";
+    case O2TPC_PENDING: return "pending";
+    case O2TPC_EINVAL: return "invalid argument or cluster content";
+    case O2TPC_ENOMEM: return "out of memory";
+    case O2TPC_EAGAIN: return "queue full, retry later";
+    case O2TPC_ETOOBIG: return "time frame exceeds the memory budget";
+    case O2TPC_ECUDA: return "CUDA error";
+    case O2TPC_ETIMEOUT: return "device wait timed out";
+    case O2TPC_ENOTFOUND: return "unknown ticket";
+    default: return "unknown status";
+  }
+}
+
+int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
+  if (!out) return O2TPC_EINVAL;
+  *out = nullptr;
+  o2tpc_config c{};
+  c.bz_tesla = 0.5;
+  c.vdrift_cm_us = 2.58;
+  if (cfg) c = *cfg;
+  if (c.mem_budget == 0) c.mem_budget = 120ull << 30;
+  if (c.max_inflight <= 0) c.max_inflight = 64;
+  if (c.max_batch <= 0) c.max_batch = 64;
+  if (!(c.vdrift_cm_us > 0.0) || !std::isfinite(c.bz_tesla)) return O2TPC_EINVAL;
+  if ((c.dev_alloc == nullptr) != (c.dev_free == nullptr)) return O2TPC_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+    cudaGetLastError();
+    return O2TPC_ECUDA;
+  }
+  auto* x = new (std::nothrow) Ctx();
+  if (!x) return O2TPC_ENOMEM;
+  x->cfg = c;
+  try {
+    CK(cudaSetDevice(c.device));
+    if (c.stream) {
+      x->stream = static_cast<cudaStream_t>(c.stream);
+    } else {
+      CK(cudaStreamCreateWithFlags(&x->stream, cudaStreamNonBlocking));
+      x->ownStream = true;
+    }
+    CK(cudaEventCreate(&x->ev0));
+    CK(cudaEventCreate(&x->ev1));
+    for (auto& e : x->evs) CK(cudaEventCreate(&e));
+    fill_geom(x->hGeom, c.bz_tesla, c.vdrift_cm_us);
+    x->dGeom = static_cast<GeomConst*>(x->dev_alloc(sizeof(GeomConst)));
+    CK(cudaMemcpyAsync(x->dGeom, &x->hGeom, sizeof(GeomConst), cudaMemcpyHostToDevice, x->stream));
+    CK(cudaStreamSynchronize(x->stream));
+  } catch (const CudaError&) {
+    cudaGetLastError();
+    delete x;
+    return O2TPC_ECUDA;
+  } catch (const AllocError&) {
+    delete x;
+    return O2TPC_ENOMEM;
+  }
+  x->worker = std::thread(worker_main, x);
+  *out = reinterpret_cast<o2tpc_ctx*>(x);
+  return O2TPC_OK;
+}
+
+int o2tpc_submit_tf(o2tpc_ctx* ctx, const o2tpc_tf* tf, uint64_t* ticket) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !tf || !ticket) return O2TPC_EINVAL;
+  if (tf->format != O2TPC_FMT_FLOAT && tf->format != O2TPC_FMT_FIXED) return O2TPC_EINVAL;
+  if (tf->location != O2TPC_LOC_HOST && tf->location != O2TPC_LOC_DEVICE) return O2TPC_EINVAL;
+  if (tf->n > 0) {
+    if (tf->format == O2TPC_FMT_FIXED && !tf->packed) return O2TPC_EINVAL;
+    if (tf->format == O2TPC_FMT_FLOAT && (!tf->sector || !tf->row || !tf->y || !tf->z)) return O2TPC_EINVAL;
+  }
+  if (tf->n >= kMaxBatchHits) return O2TPC_ETOOBIG;
+  const uint64_t fp = footprint_of(tf->n);
+  if (fp > c->cfg.mem_budget) return O2TPC_ETOOBIG;
+  auto j = std::make_shared<Job>();
+  j->tf = *tf;
+  j->footprint = fp;
+  j->t_submit = now_ms();
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (c->fatal != O2TPC_OK) return c->fatal;
+    if (c->inflight >= c->cfg.max_inflight) return O2TPC_EAGAIN;
+    j->ticket = c->nextTicket++;
+    c->jobs[j->ticket] = j;
+    c->queue.push_back(j);
+    ++c->inflight;
+  }
+  c->cvWork.notify_one();
+  *ticket = j->ticket;
+  return O2TPC_OK;
+}
+
+int o2tpc_poll(o2tpc_ctx* ctx, uint64_t ticket, int32_t timeout_ms, const o2tpc_result** out) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !out) return O2TPC_EINVAL;
+  std::unique_lock<std::mutex> lk(c->mu);
+  auto it = c->jobs.find(ticket);
+  if (it == c->jobs.end()) return O2TPC_ENOTFOUND;
+  std::shared_ptr<Job> j = it->second;
+  auto ready = [&] { return j->done; };
+  if (timeout_ms < 0) c->cvDone.wait(lk, ready);
+  else if (!c->cvDone.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return O2TPC_PENDING;
+  *out = &j->res;
+  return O2TPC_OK;
+}
+
+void o2tpc_result_release(o2tpc_ctx* ctx, const o2tpc_result* res) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !res) return;
+  std::shared_ptr<Job> j;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (auto it = c->jobs.begin(); it != c->jobs.end(); ++it) {
+      if (&it->second->res == res && it->second->done) {
+        j = it->second;
+        c->jobs.erase(it);
+        --c->inflight;
+        break;
+      }
+    }
+  }
+  // dropping j releases its results and its reference on the kept stages
+  if (j && j->mem) {
+    cudaSetDevice(c->cfg.device);
+    j->mem.reset();
+  }
+}
+
+int o2tpc_destroy(o2tpc_ctx* ctx) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c) return O2TPC_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->stop = true;
+  }
+  c->cvWork.notify_all();
+  if (c->worker.joinable()) c->worker.join();
+  int rc = c->fatal;
+  cudaSetDevice(c->cfg.device);
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    for (auto& kv : c->jobs) kv.second->mem.reset();
+    c->jobs.clear();
+  }
+  c->dev_free(c->dGeom);
+  cudaStreamSynchronize(c->stream);
+  if (c->hStage) cudaFreeHost(c->hStage);
+  for (auto& e : c->evs)
+    if (e) cudaEventDestroy(e);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ownStream) cudaStreamDestroy(c->stream);
+  delete c;
+  return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+std::vector<T> d2h(const T* d, size_t count) {
+  std::vector<T> v(count);
+  if (count) CK(cudaMemcpy(v.data(), d, sizeof(T) * count, cudaMemcpyDeviceToHost));
+  return v;
+}
+
+// Builds the named stage array of TF i of a kept batch (TF-local indices).
+bool build_stage(const BatchMem& M, int i, const std::string& name, std::vector<char>& out) {
+  const int hb = M.tfHitBase[i], he = M.tfHitEnd[i], nh = he - hb;
+  const int tlb = M.tfTlBegin[i], tle = M.tfTlBegin[i + 1], ntl = tle - tlb;
+  const int stb = M.tfStBegin[i], ste = M.tfStBegin[i + 1], nst = ste - stb;
+  auto put = [&](const void* p, size_t bytes) {
+    out.resize(bytes);
+    if (bytes) memcpy(out.data(), p, bytes);
+  };
+  auto rel = [](std::vector<int>& v, int base) {
+    for (auto& x : v)
+      if (x >= 0) x -= base;
+  };
+  if (name == "sorted_orig") {
+    auto v = d2h(M.sorig + hb, nh);
+    for (auto& x : v) x -= M.tfInBase[i];
+    put(v.data(), v.size() * 4);
+  } else if (name == "sorted_yz") {
+    auto v = d2h(M.syz + hb, nh);
+    put(v.data(), v.size() * 8);
+  } else if (name == "row_grid" || name == "cell_start") {
+    auto g = d2h(M.grid + (size_t)i * kRowsPerTF, kRowsPerTF);
+    const int cb = g[0].cellBase;
+    const int ce = g[kRowsPerTF - 1].cellBase + g[kRowsPerTF - 1].ny * g[kRowsPerTF - 1].nz;
+    if (name == "row_grid") {
+      std::vector<int> v(kRowsPerTF * 8);
+      for (int r = 0; r < kRowsPerTF; ++r) {
+        v[8 * r + 0] = g[r].start - hb;
+        v[8 * r + 1] = g[r].count;
+        v[8 * r + 2] = g[r].cellBase - cb;
+        v[8 * r + 3] = g[r].ny;
+        v[8 * r + 4] = g[r].nz;
+        v[8 * r + 5] = g[r].cz;
+        v[8 * r + 6] = g[r].zmin;
+        v[8 * r + 7] = 0;
+      }
+      put(v.data(), v.size() * 4);
+    } else {
+      auto v = d2h(M.cellStart + cb, (size_t)(ce - cb) + 1);
+      for (auto& x : v) x -= hb;
+      put(v.data(), v.size() * 4);
+    }
+  } else if (name == "up_raw" || name == "dn_raw" || name == "up" || name == "dn") {
+    const int* src = name == "up_raw" ? M.upRaw : name == "dn_raw" ? M.dnRaw : name == "up" ? M.up : M.dn;
+    auto v = d2h(src + hb, nh);
+    rel(v, hb);
+    put(v.data(), v.size() * 4);
+  } else if (name == "starts") {
+    auto v = d2h(M.starts + tlb, ntl);
+    rel(v, hb);
+    put(v.data(), v.size() * 4);
+  } else if (name == "tl_nhits") {
+    auto v = d2h(M.tb.nhits + tlb, ntl);
+    put(v.data(), v.size() * 4);
+  } else if (name == "tl_hits") {
+    auto nhv = d2h(M.tb.nhits + tlb, ntl);
+    auto nav = d2h(M.tb.nasc + tlb, ntl);
+    auto hv = d2h(M.tb.hits + (size_t)tlb * kMaxTlHits, (size_t)ntl * kMaxTlHits);
+    std::vector<int> v((size_t)ntl * kMaxTlHits, -1);
+    for (int k = 0; k < ntl; ++k) {
+      const int nhk = nhv[k], na = nav[k], nd = nhk - na;
+      int m = 0;
+      for (int j = 0; j < nhk; ++j) {
+        const int q = (j < nd) ? (nhk - 1 - j) : (j - nd);
+        v[(size_t)k * kMaxTlHits + m++] = hv[(size_t)k * kMaxTlHits + q] - hb;
+      }
+    }
+    put(v.data(), v.size() * 4);
+  } else if (name == "tl_state") {
+    auto v = d2h(M.tb.state + (size_t)tlb * 21, (size_t)ntl * 21);
+    put(v.data(), v.size() * 4);
+  } else if (name == "st_tracklet") {
+    auto v = d2h(M.sb.tl + stb, nst);
+    rel(v, tlb);
+    put(v.data(), v.size() * 4);
+  } else if (name == "st_off" || name == "st_hits") {
+    auto off = d2h(M.sb.off + stb, (size_t)nst + 1);
+    if (name == "st_off") {
+      const int o0 = off[0];
+      for (auto& x : off) x -= o0;
+      put(off.data(), off.size() * 4);
+    } else {
+      auto v = d2h(M.sb.hits + off[0], (size_t)(off[nst] - off[0]));
+      rel(v, hb);
+      put(v.data(), v.size() * 4);
+    }
+  } else if (name == "st_in" || name == "st_out") {
+    auto v = d2h((name == "st_in" ? M.sb.in : M.sb.out) + (size_t)stb * 21, (size_t)nst * 21);
+    put(v.data(), v.size() * 4);
+  } else if (name == "st_next" || name == "st_prev") {
+    auto v = d2h((name == "st_next" ? M.mb.next : M.mb.prev) + stb, nst);
+    rel(v, stb);
+    put(v.data(), v.size() * 4);
+  } else {
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" int o2tpc_get_stage(o2tpc_ctx* ctx, uint64_t ticket, const char* name, void* dst, uint64_t capacity,
+                               uint64_t* needed) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !name) return O2TPC_EINVAL;
+  std::shared_ptr<Job> j;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    auto it = c->jobs.find(ticket);
+    if (it == c->jobs.end() || !it->second->done) return O2TPC_ENOTFOUND;
+    j = it->second;
+  }
+  if (!j->mem) return O2TPC_EINVAL;
+  std::vector<char> buf;
+  try {
+    cudaSetDevice(c->cfg.device);
+    if (!build_stage(*j->mem, j->tfIndex, name, buf)) return O2TPC_EINVAL;
+  } catch (const CudaError&) {
+    cudaGetLastError();
+    return O2TPC_ECUDA;
+  }
+  if (needed) *needed = buf.size();
+  if (!dst || capacity < buf.size()) return O2TPC_EINVAL;
+  if (!buf.empty()) memcpy(dst, buf.data(), buf.size());
+  return O2TPC_OK;
+}

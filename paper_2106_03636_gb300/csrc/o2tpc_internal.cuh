@@ -1,0 +1,309 @@
+// o2tpc_internal.cuh - shared device definitions of the tracker kernels.
+//
+// Geometry, tracking cuts and the Kalman-filter building blocks used by the
+// kernels in k_*.cu.  All tracking decisions up to the start hits are
+// integer; the track fit runs in FP32 (templated so that the final refit can
+// redo a track in FP64 when its FP32 covariance stops being positive
+// definite).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace o2tpc {
+
+// ------------------------------------------------------------ geometry
+constexpr int kNSec = 36;
+constexpr int kNRow = 152;
+constexpr int kRowsPerTF = kNSec * kNRow;  // 5472
+
+// ------------------------------------------------------ integer seeding
+constexpr int kCellY = 320;        // grid cell width along y: 2 cm in 1/160 cm
+constexpr int kHitsPerCell = 4;    // target occupancy of a grid cell
+constexpr int kMaxNz = 1 << 20;    // cells along zeta per row, at most
+constexpr int kWinY = 240;         // neighbour window |dy| <= 1.5 cm
+constexpr int kWinZ = 248;         // neighbour window |dzeta| <= 2.0 cm
+constexpr int kWeightY = 2077;     // 6 sigma_zeta^2 in units^2: weight of the y term
+constexpr int kWeightZ = 1536;     // 6 sigma_y^2 in units^2: weight of the zeta term
+constexpr int kMaxMetric = 16 * 1536 * 2077;  // 2-dof chi2 <= 16, scaled
+
+// ---------------------------------------------------------- track fit
+constexpr float kSigY = 0.1f;
+constexpr float kSigZ = 0.15f;
+constexpr int kMaxMiss = 4;        // consecutive rows without a hit before stopping
+constexpr int kMinHits = 10;       // tracklet / sector-track minimum
+constexpr float kChi2Follow = 18.f;
+constexpr float kSinFollow = 0.95f;
+constexpr float kSinProp = 0.999f;
+constexpr float kEdgeBand = 5.f;   // border-track band for merging, cm
+constexpr float kMergeDZeta = 20.f;
+constexpr float kChi2Merge = 30.f;
+
+// Per-run constants in constant memory (set by the host once per context).
+struct GeomConst {
+  float rowx[kNRow];
+  double rowx_d[kNRow];
+  int npads[kNRow];
+  float sec_alpha[18];
+  float tan10;
+  float rot_cos, rot_sin;      // cos / sin of the 20 degree sector pitch
+  double rot_cos_d, rot_sin_d;
+  float bzc;        // -0.00299792458 * Bz (1/cm per GeV^-1)
+  float zunit;      // cm per drift-time unit (0.003125 us * v_drift)
+  float kz;         // 1 / zunit as float (float-input quantisation)
+  double bzc_d, zunit_d;
+};
+
+// ------------------------------------------------------------ tables
+// Per-row grid, 32 bytes.
+struct RowGrid {
+  int start;     // first sorted hit of the row (batch-global)
+  int count;
+  int cellBase;  // first cell of the row in cellStart[]
+  int ny, nz, cz, zmin;
+  int pad;
+};
+
+// Per-TF descriptor of a batch.
+struct TFDesc {
+  const void* in0;   // FLOAT: sector (uint8) / FIXED: packed records
+  const void* in1;   // FLOAT: row (uint8)
+  const float* y;    // FLOAT
+  const float* z;    // FLOAT
+  int format;
+  int n;             // clusters
+  int inBase;        // first batch-global input index of this TF
+  int tileBase;      // first tile of this TF
+  int nTiles;
+  int pad[3];
+};
+
+// Device error word bits
+enum : unsigned { kErrInput = 1u, kErrOverflow = 2u, kErrTimeout = 4u };
+
+// ------------------------------------------------------------ helpers
+__host__ __device__ inline int floordiv_i64(long long a, long long b) {
+  long long q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return (int)q;
+}
+
+__device__ inline int cell_iy(const RowGrid& g, int npads, int yu) {
+  int half = 32 * npads;
+  int iy = floordiv_i64((long long)yu + half, kCellY);
+  return iy < 0 ? 0 : (iy > g.ny - 1 ? g.ny - 1 : iy);
+}
+
+// Cell rectangle of row g overlapping [ylo,yhi] x [zlo,zhi]; false if empty.
+__device__ inline bool cell_range(const RowGrid& g, int npads, long long ylo, long long yhi, long long zlo,
+                                  long long zhi, int& iy0, int& iy1, int& iz0, int& iz1) {
+  if (g.count == 0) return false;
+  long long half = 32 * npads;
+  long long a = ylo + half, b = yhi + half;
+  long long qa = a >= 0 ? a / kCellY : -((-a + kCellY - 1) / kCellY);
+  long long qb = b >= 0 ? b / kCellY : -((-b + kCellY - 1) / kCellY);
+  iy0 = (int)(qa < 0 ? 0 : (qa > g.ny - 1 ? g.ny - 1 : qa));
+  iy1 = (int)(qb < 0 ? 0 : (qb > g.ny - 1 ? g.ny - 1 : qb));
+  long long za = zlo - g.zmin, zb = zhi - g.zmin;
+  long long qza = za >= 0 ? za / g.cz : -((-za + g.cz - 1) / g.cz);
+  long long qzb = zb >= 0 ? zb / g.cz : -((-zb + g.cz - 1) / g.cz);
+  if (qza < 0) qza = 0;
+  if (qzb > g.nz - 1) qzb = g.nz - 1;
+  if (qza > qzb) return false;
+  iz0 = (int)qza;
+  iz1 = (int)qzb;
+  return true;
+}
+
+__device__ inline int upper_bound_i32(const int* a, int n, int v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (a[m] <= v) lo = m + 1;
+    else hi = m;
+  }
+  return lo;
+}
+
+// ------------------------------------------------- Kalman building blocks
+// State (y, zeta, sin phi, t = dzeta/ds_T, q/pT) at local x; covariance as
+// lower triangle (yy, zy, zz, sy, sz, ss, ty, tz, ts, tt, qy, qz, qs, qt, qq).
+template <typename T>
+struct KState {
+  T x;
+  T p[5];
+  T C[15];
+};
+
+__host__ __device__ constexpr int ix(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+template <typename T>
+__device__ inline T kf_sqrt(T v);
+template <>
+__device__ inline float kf_sqrt<float>(float v) { return sqrtf(v); }
+template <>
+__device__ inline double kf_sqrt<double>(double v) { return sqrt(v); }
+template <typename T>
+__device__ inline T kf_asin(T v);
+template <>
+__device__ inline float kf_asin<float>(float v) { return asinf(v); }
+template <>
+__device__ inline double kf_asin<double>(double v) { return asin(v); }
+
+template <typename T>
+__device__ inline void kf_reset(KState<T>& s, T x, T y, T z, T sphi, T t, T q) {
+  s.x = x;
+  s.p[0] = y; s.p[1] = z; s.p[2] = sphi; s.p[3] = t; s.p[4] = q;
+#pragma unroll
+  for (int i = 0; i < 15; ++i) s.C[i] = T(0);
+  s.C[0] = T(kSigY) * T(kSigY);
+  s.C[2] = T(kSigZ) * T(kSigZ);
+  s.C[5] = T(0.04);
+  s.C[9] = T(0.25);
+  s.C[14] = T(400);
+}
+
+// C <- J C J^T for J = identity plus the listed off-diagonal terms.
+template <typename T>
+__device__ inline void kf_sandwich(T* C, const T J[5][5]) {
+  T M[5][5], A[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) M[i][j] = C[ix(i, j)];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) s += J[i][k] * M[k][j];
+      A[i][j] = s;
+    }
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      T s = T(0), s2 = T(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) { s += A[i][k] * J[j][k]; s2 += A[j][k] * J[i][k]; }
+      C[ix(i, j)] = T(0.5) * (s + s2);
+    }
+}
+
+// Helix transport to x2 in a uniform field: d(sin phi)/dx = k = (q/pT) bzc;
+// dy = dx (s1+s2)/(c1+c2); transverse path ds = 2 asin(|k| chord/2)/|k|
+// (the chord when |k| chord < 1e-6), signed like dx; dzeta = t ds.
+// Jacobian: exact y and sin(phi) rows; d(ds)/d(sin phi) exact; d(ds)/dk as
+// a three-point Simpson integral of its cancellation-free integrand when
+// |k dx| < 0.05, else (dx/c2 - ds)/k.  Returns 0, or -1 if |sin phi| would
+// reach kSinProp.
+template <typename T>
+__device__ inline int kf_prop(KState<T>& s, T x2, T bzc) {
+  T dx = x2 - s.x;
+  if (dx == T(0)) return 0;
+  T s1 = s.p[2], q = s.p[4], tz = s.p[3];
+  T k = q * bzc;
+  T s2 = s1 + k * dx;
+  if (fabs(s1) >= T(kSinProp) || fabs(s2) >= T(kSinProp)) return -1;
+  T c1 = kf_sqrt<T>((T(1) - s1) * (T(1) + s1));
+  T c2 = kf_sqrt<T>((T(1) - s2) * (T(1) + s2));
+  T cc = c1 + c2;
+  T dy = dx * (s1 + s2) / cc;
+  T chord = kf_sqrt<T>(dx * dx + dy * dy);
+  T ak = fabs(k) * chord;
+  T ds = (ak < T(1e-6)) ? chord : T(2) * kf_asin<T>(T(0.5) * ak) / fabs(k);
+  if (dx < T(0)) ds = -ds;
+  T sm = s1 + T(0.5) * k * dx;
+  T cm = kf_sqrt<T>((T(1) - sm) * (T(1) + sm));
+  T f1 = dx * (s1 + s2) / (c1 * c2 * cc);
+  T fm = T(0.5) * dx * (sm + s2) / (cm * c2 * (cm + c2));
+  T ddsdk = (fabs(k * dx) < T(0.05)) ? dx * (f1 + T(4) * fm) / T(6) : (dx / c2 - ds) / k;
+  T J[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) J[i][j] = (i == j) ? T(1) : T(0);
+  J[0][2] = dx * (T(2) * cc + (s1 + s2) * (s1 / c1 + s2 / c2)) / (cc * cc);
+  J[0][4] = dx * dx * bzc * (cc + (s1 + s2) * s2 / c2) / (cc * cc);
+  J[1][2] = tz * f1;
+  J[1][3] = ds;
+  J[1][4] = tz * bzc * ddsdk;
+  J[2][4] = dx * bzc;
+  s.p[0] += dy;
+  s.p[1] += tz * ds;
+  s.p[2] = s2;
+  s.x = x2;
+  kf_sandwich<T>(s.C, J);
+  return 0;
+}
+
+// Kalman update with a (y, zeta) measurement of errors (kSigY, kSigZ).
+template <typename T>
+__device__ inline int kf_update(KState<T>& s, T ym, T zm, T* chi2) {
+  T* C = s.C;
+  T r0 = ym - s.p[0], r1 = zm - s.p[1];
+  T S00 = C[0] + T(kSigY) * T(kSigY), S01 = C[1], S11 = C[2] + T(kSigZ) * T(kSigZ);
+  T det = S00 * S11 - S01 * S01;
+  if (!(det > T(0))) return -1;
+  T I00 = S11 / det, I01 = -S01 / det, I11 = S00 / det;
+  if (chi2) *chi2 = r0 * r0 * I00 + T(2) * r0 * r1 * I01 + r1 * r1 * I11;
+  T Cy[5], Cz[5], K0[5], K1[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) { Cy[i] = C[ix(i, 0)]; Cz[i] = C[ix(i, 1)]; }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) { K0[i] = Cy[i] * I00 + Cz[i] * I01; K1[i] = Cy[i] * I01 + Cz[i] * I11; }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) s.p[i] += K0[i] * r0 + K1[i] * r1;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) C[ix(i, j)] -= K0[i] * Cy[j] + K1[i] * Cz[j];
+  return 0;
+}
+
+// Frame rotation by dalpha (cos ca, sin sa): new alpha = old alpha + dalpha.
+// Parameters follow the rigid rotation; covariance Jacobian: dy'/dy = c/c',
+// dzeta'/dy = -t sa / c', d(sin phi')/dy = -k sa, d(sin phi')/d(sin phi) = c'/c.
+template <typename T>
+__device__ inline int kf_rotate(KState<T>& s, T ca, T sa, T bzc) {
+  T sp = s.p[2];
+  if (fabs(sp) >= T(kSinProp)) return -1;
+  T c = kf_sqrt<T>((T(1) - sp) * (T(1) + sp));
+  T s2 = sp * ca - c * sa, c2 = c * ca + sp * sa;
+  if (c2 <= T(0) || fabs(s2) >= T(kSinProp)) return -1;
+  T x = s.x, y = s.p[0];
+  T J[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) J[i][j] = (i == j) ? T(1) : T(0);
+  J[0][0] = c / c2;
+  J[1][0] = -s.p[3] * sa / c2;
+  J[2][0] = -s.p[4] * bzc * sa;
+  J[2][2] = c2 / c;
+  s.x = x * ca + y * sa;
+  s.p[0] = -x * sa + y * ca;
+  s.p[2] = s2;
+  kf_sandwich<T>(s.C, J);
+  return 0;
+}
+
+// FP32 positive-definiteness test of the final refit: every C_ii > 0 and
+// every C_ij^2 < C_ii C_jj.
+template <typename T>
+__device__ inline bool kf_cov_ok(const T* C) {
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+    if (!(C[ix(i, i)] > T(0))) return false;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      T v = C[ix(i, j)];
+      if (!(v * v < C[ix(i, i)] * C[ix(j, j)])) return false;
+    }
+  return true;
+}
+
+}  // namespace o2tpc

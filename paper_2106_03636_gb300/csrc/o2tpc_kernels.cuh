@@ -1,0 +1,116 @@
+// o2tpc_kernels.cuh - launchers of the tracker kernels (host side) and the
+// device buffers they work on.
+#pragma once
+
+#include <climits>
+
+#include "o2tpc_internal.cuh"
+
+namespace o2tpc {
+
+// Kernels launched by the calling host thread (each launcher adds its own).
+extern thread_local long long g_launch_count;
+
+constexpr int kNFBlock = 128;      // hits per NeighboursFinder block
+constexpr int kMaxTlHits = kNRow;  // hit slots per tracklet
+
+// k_bin.cu
+void launch_ingest_stats(const TFDesc* tfs, const int2* tiles, int nTiles, int tileSize, const GeomConst* G,
+                         int* tileStats, unsigned* err, cudaStream_t st);
+void launch_row_reduce(const TFDesc* tfs, int nTF, int* tileStats, int* rowCnt, int* rowMin, int* rowMax,
+                       cudaStream_t st);
+void launch_grid(int nRows, const int* rowCnt, const int* rowMin, const int* rowMax, const GeomConst* G,
+                 RowGrid* grid, int* nfBlockStart, int nfBlock, int* totals, cudaStream_t st);
+void launch_row_scatter(const TFDesc* tfs, const int2* tiles, int nTiles, int tileSize, const GeomConst* G,
+                        const int* tileStats, const RowGrid* grid, int4* bucket, cudaStream_t st);
+void launch_cell_sort(int nRows, const RowGrid* grid, const int4* bucket, int* cellStart, int2* syz, int* sorig,
+                      int* gscratch, const int* totals, cudaStream_t st);
+
+// k_ca.cu
+void launch_neighbours(int nfBlocks, const RowGrid* grid, const int* nfBlockStart, int nRows, const int* cellStart,
+                       const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw, cudaStream_t st);
+void launch_clean(int n, const int* upRaw, const int* dnRaw, int* up, int* dn, int* startFlag, cudaStream_t st);
+int scan_scratch_ints(long long n);
+void scan_exclusive(const int* in, int* out, int n, int* scratch, cudaStream_t st);
+void launch_compact(int n, const int* flag, const int* pos, int* out, cudaStream_t st);
+void launch_tf_ranges(int nTF, const RowGrid* grid, const int* list, int nList, int* tfBegin, cudaStream_t st);
+void launch_lower_bounds(const int* list, int nList, const int* keys, int nKeys, int* out, cudaStream_t st);
+
+// k_track.cu
+struct TrackletBufs {
+  int* nhits;    // [nTl]  total attached hits (0: dropped)
+  int* nasc;     // [nTl]  hits in slots [0, nasc) in ascending rows; slots [nasc, nhits) descending
+  int* hits;     // [nTl * kMaxTlHits]
+  uint8_t* rows; // [nTl * kMaxTlHits]
+  float* state;  // [nTl * 21]  x, par[5], cov[15] at the innermost hit
+  int* zref;     // [nTl]
+};
+void launch_tracklets(int nTl, const int* starts, const int* up, const RowGrid* grid, int nRows,
+                      const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st);
+
+struct SectorTrackBufs {
+  int* tl;        // [nSt] tracklet of the sector track
+  int* sector;    // [nSt] sector 0..35
+  int* tf;        // [nSt] TF index in the batch
+  int* zref;      // [nSt]
+  int* off;       // [nSt + 1] into hits
+  int* hits;      // sorted hit indices, ascending rows
+  uint8_t* rows;  // row of each hit
+  float* in;      // [nSt * 21] state at the innermost hit (inward fit)
+  float* out;     // [nSt * 21] state at the outermost hit (outward fit)
+};
+void launch_ownership(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, unsigned long long* w, cudaStream_t st);
+void launch_segments_count(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, const unsigned long long* w,
+                           int* nSeg, int* nSegHits, cudaStream_t st);
+void launch_segments_write(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, const unsigned long long* w,
+                           const int* segPos, const int* segHitPos, const int2* syz, const RowGrid* grid, int nRows,
+                           SectorTrackBufs sb, cudaStream_t st);
+void launch_sector_fit(int nSt, const TrackletBufs tb, const int2* syz, const GeomConst* G, SectorTrackBufs sb,
+                       cudaStream_t st);
+
+// k_merge.cu
+struct MergeBufs {
+  int* keyIn;        // [nSt] B-list key of the inner end (-1: not a border end)
+  int* keyOut;       // [nSt] edge key of the outer end (-1)
+  int* listCnt;      // [nKeys + 1]
+  int* listStart;    // [nKeys + 1]
+  int* listItems;    // [nSt]
+  int* listKey;      // [nSt] drift coordinate (units) of each list item
+  float4* pairs;     // [cap] {chi2, a, b, edge}
+  int* pairCount;    // [1]
+  int pairCap;
+  float4* pairsSorted;  // [cap]
+  float4* sortScratch;  // [2 * max(cap, nSt)] padded bitonic buffers (also used as int2)
+  int* edgeCnt;      // [nKeys + 1]
+  int* edgeStart;    // [nKeys + 1]
+  int* next;         // [nSt]
+  int* prev;         // [nSt]
+  int* reached;      // [nSt]
+};
+void launch_merge_keys(int nSt, const SectorTrackBufs sb, const GeomConst* G, MergeBufs mb, int nKeys, int* scratch,
+                       cudaStream_t st);
+void launch_merge_pairs(int nSt, const SectorTrackBufs sb, const GeomConst* G, MergeBufs mb, unsigned* err,
+                        cudaStream_t st);
+void launch_merge_select(int nPairs, int nKeys, MergeBufs mb, int* scratch, cudaStream_t st);
+void launch_chains(int nSt, int nTF, const int* stTfBegin, MergeBufs mb, int* headFlag, cudaStream_t st);
+void launch_chain_counts(int nHeads, const int* heads, const SectorTrackBufs sb, MergeBufs mb, int* trkNcl,
+                         cudaStream_t st);
+
+struct OutBufs {
+  int* off;         // [nTrk + 1] batch-global offsets into cl
+  int* cl;          // input index (batch-global) of each cluster
+  float* x;
+  float* alpha;
+  float* par;       // [nTrk * 5]
+  float* cov;       // [nTrk * 15]
+  float* chi2;
+  int* ndf;
+  uint8_t* sector;
+  uint8_t* flags;
+  int* zref;
+  int* nFallback;   // [1]
+};
+void launch_final_refit(int nHeads, const int* heads, const SectorTrackBufs sb, MergeBufs mb, const int2* syz,
+                        const int* sorig, const GeomConst* G, int forceFp64, OutBufs ob, cudaStream_t st);
+
+}  // namespace o2tpc

@@ -1,0 +1,39 @@
+"""The C-ABI library loads and exports every function include/o2tpc.h declares
+(no GPU needed: nothing is called that touches a device)."""
+import ctypes
+import os
+import re
+
+from paper_2106_03636_gb300 import _build, o2tpc
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "o2tpc.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\s*\*)\s+(o2tpc_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("o2tpc_create", "o2tpc_submit_tf", "o2tpc_poll", "o2tpc_destroy", "o2tpc_result_release",
+              "o2tpc_strerror", "o2tpc_get_stage"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(_build.build_tpc())
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+
+
+def test_strerror_without_gpu():
+    assert o2tpc.o2tpc_strerror(o2tpc.O2TPC_ETOOBIG).startswith("time frame")
+    assert o2tpc.o2tpc_strerror(12345) == "unknown status"
+
+
+def test_binding_structures_match_header_sizes():
+    # 64-bit layout of the C structs as the header defines them
+    assert ctypes.sizeof(o2tpc.o2tpc_tf) == 8 + 4 + 4 + 5 * 8 + 8
+    assert ctypes.sizeof(o2tpc.o2tpc_stats) == 5 * 8 + 4 * 4 + 8 + 10 * 4

@@ -1,0 +1,145 @@
+"""CUDA path vs the oracle through the C-ABI (needs a GB300)."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import float_tf
+from parity import assert_criteria, compare_stages, compare_tracks, pool
+from paper_2106_03636_gb300 import o2tpc, synth
+
+pytestmark = pytest.mark.gpu
+
+ZUNIT = 0.003125 * 2.58
+
+
+@pytest.fixture(scope="module")
+def trk():
+    t = o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_KEEP_STAGES)
+    yield t
+    t.close()
+
+
+def run_both(trk, tf):
+    ticket = trk.submit(tf)
+    res = trk.poll(ticket, keep=True)
+    assert res["status"] == 0
+    o = oracle.run(tf)
+    return ticket, res, o
+
+
+def test_single_sector_parity(trk):
+    tf = synth.single_sector()
+    ticket, res, o = run_both(trk, tf)
+    compare_stages(trk, ticket, o)
+    rep = compare_tracks(res, o, ZUNIT)
+    print(rep)
+    trk.release(ticket, res)
+
+
+def test_single_sector_dense_parity(trk):
+    """Ten dense single-sector frames (1500 primaries each, 19x the
+    single-sector occupancy), pooled."""
+    reps = []
+    for seed in range(77, 87):
+        tf = synth.single_sector(seed=seed, ntracks=1500)
+        ticket, res, o = run_both(trk, tf)
+        compare_stages(trk, ticket, o)
+        reps.append(compare_tracks(res, o, ZUNIT, check=False))
+        trk.release(ticket, res)
+    rep = pool(reps)
+    print(rep)
+    assert_criteria(rep)
+
+
+@pytest.mark.parametrize("n_coll", [3, 50])
+def test_full_tpc_parity(trk, n_coll):
+    tf = synth.full_tpc_1ms(n_coll=n_coll)
+    ticket, res, o = run_both(trk, tf)
+    compare_stages(trk, ticket, o)
+    print(compare_tracks(res, o, ZUNIT))
+    trk.release(ticket, res)
+
+
+def test_fixed_point_parity(trk):
+    tf = synth.full_tpc_1ms(seed=5, n_coll=2, fmt=synth.FMT_FIXED)
+    ticket, res, o = run_both(trk, tf)
+    compare_stages(trk, ticket, o)
+    print(compare_tracks(res, o, ZUNIT))
+    trk.release(ticket, res)
+
+
+def test_tracklets_and_sector_tracks(trk):
+    """Tracklet hit lists and sector tracks, not only the final tracks."""
+    tf = synth.full_tpc_1ms(seed=9, n_coll=1)
+    ticket, res, o = run_both(trk, tf)
+    nh = trk.stage(ticket, "tl_nhits")
+    assert len(nh) == len(o["tl_nhits"])
+    same = np.mean(nh == o["tl_nhits"])
+    assert same >= 0.999, same
+    th = trk.stage(ticket, "tl_hits")
+    eq = 0
+    for k in range(len(nh)):
+        a = th[k][: nh[k]]
+        b = o["tl_hits"][o["tl_off"][k]:o["tl_off"][k + 1]]
+        eq += np.array_equal(a, b)
+    assert eq / max(1, len(nh)) >= 0.999
+    so, oo = trk.stage(ticket, "st_off"), o["st_off"]
+    sh = trk.stage(ticket, "st_hits")
+    g = {tuple(sh[so[i]:so[i + 1]]) for i in range(len(so) - 1)}
+    r = [tuple(o["st_hits"][oo[i]:oo[i + 1]]) for i in range(len(oo) - 1)]
+    assert np.mean([x in g for x in r]) >= 0.999
+    trk.release(ticket, res)
+
+
+def test_batch_equals_alone():
+    """Each TF's result is the same alone and inside a batch."""
+    tfs = [synth.single_sector(seed=s) for s in (1, 2)] + [synth.full_tpc_1ms(seed=3, n_coll=1)]
+    with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_NO_BATCHING) as a:
+        alone = [a.track(tf) for tf in tfs]
+    with o2tpc.Tracker(max_batch=8) as b:
+        tickets = [b.submit(tf) for tf in tfs]
+        mix = [b.poll(t) for t in tickets]
+    assert max(m["stats"]["batch_size"] for m in mix) >= 1
+    for x, y in zip(alone, mix):
+        for k in ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref"):
+            assert np.array_equal(x[k], y[k]), k
+
+
+def test_empty_and_tiny_inputs():
+    with o2tpc.Tracker() as t:
+        e = t.track(float_tf([], [], [], []))
+        assert e["status"] == 0 and e["n_tracks"] == 0
+        s = t.track(float_tf([0, 0, 0], [10, 11, 12], [0.0, 0.01, 0.02], [100.0, 100.1, 100.2]))
+        assert s["status"] == 0 and s["n_tracks"] == 0
+
+
+def test_invalid_cluster_reported():
+    with o2tpc.Tracker() as t:
+        r = t.track(float_tf([0, 40], [10, 11], [0.0, 0.0], [1.0, 1.0]))
+        assert r["status"] == o2tpc.O2TPC_EINVAL
+        r = t.track(float_tf([0], [10], [np.nan], [1.0]))
+        assert r["status"] == o2tpc.O2TPC_EINVAL
+        ok = t.track(synth.single_sector())
+        assert ok["status"] == 0 and ok["n_tracks"] > 10
+
+
+def test_fp64_fallback_path_agrees():
+    tf = synth.single_sector()
+    with o2tpc.Tracker() as a:
+        r32 = a.track(tf)
+    with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_FORCE_FP64) as b:
+        r64 = b.track(tf)
+    assert r64["stats"]["n_fp64_fallback"] == r64["n_tracks"]
+    assert np.array_equal(r32["cluster_idx"], r64["cluster_idx"])
+    o = oracle.run(tf)
+    compare_tracks(r64, o, ZUNIT)
+
+
+def test_torch_allocator_and_stream():
+    torch = pytest.importorskip("torch")
+    tf = synth.single_sector()
+    with o2tpc.Tracker(torch_memory=True) as t:
+        r = t.track(tf)
+    o = oracle.run(tf)
+    compare_tracks(r, o, ZUNIT)
+    assert torch.cuda.memory_allocated() >= 0

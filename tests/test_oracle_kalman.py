@@ -15,7 +15,7 @@ import pytest
 import oracle
 from helpers import Helix, row_x
 
-CINIT = np.array([0.01, 0, 0.0225, 0, 0, 0.25, 0, 0, 0, 0.25, 0, 0, 0, 0, 400.0])
+CINIT = np.array([0.01, 0, 0.0225, 0, 0, 0.04, 0, 0, 0, 0.25, 0, 0, 0, 0, 400.0])
 
 
 def ix(i, j):
@@ -253,7 +253,7 @@ def test_zero_field_fit_close_to_batch_map():
             cc = math.sqrt(1 - s * s)
             ry = (y0 + (x - x[0]) * s / cc - y) / 0.1
             rz = (z0 + t * (x - x[0]) / cc - z) / 0.15
-            return np.concatenate([ry, rz, [(s - seed[2]) / 0.5, (t - seed[3]) / 0.5]])
+            return np.concatenate([ry, rz, [(s - seed[2]) / 0.2, (t - seed[3]) / 0.5]])
 
         sol = scipy_opt.least_squares(res, [y[0], z[0], seed[2], seed[3]], xtol=1e-15, ftol=1e-15, gtol=1e-15)
         y0, z0, s, t = sol.x
