@@ -50,7 +50,9 @@ STAGE_BYTES = {
     "sector_fit": 1.0,
     "merge": 0.5,
     "refit": 0.5,
+    "sizes": 0.0,
     "download": 0.0,
+    "host_alloc": 0.0,
 }
 PATH_BYTES = 64.0
 
@@ -208,7 +210,7 @@ def main():
     st = trk.stream
 
     def step(location, arrays):
-        r = trk.poll(trk.submit(tf, location=location, arrays=arrays))
+        r = trk.wait(trk.submit(tf, location=location, arrays=arrays))
         if r["status"] != 0:
             raise RuntimeError(o2tpc.o2tpc_strerror(r["status"]))
         return r
@@ -221,7 +223,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        stage = np.zeros(10)
+        stage = np.zeros(12)
         launches = 0
         lat = []
         e0.record(st)
@@ -255,7 +257,7 @@ def main():
         step(o2tpc.O2TPC_LOC_HOST, pin)
         ms_h, _, _, lat_h, rh = timed(o2tpc.O2TPC_LOC_HOST, pin)
         h2d = 12 * n if tf.fmt == 1 else 10 * n
-        nt, ncl = rh["n_tracks"], int(rh["offsets"][-1])
+        nt, ncl = rh["n_tracks"], rh["n_cluster_refs"]
         d2h = 8 * (nt + 1) + 4 * ncl + nt * (4 * 2 + 20 + 60 + 4 + 4 + 1 + 1 + 4)
         e2e = {"value": world * n / (ms_h / args.steps / 1e3), "unit": "clusters/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_h / args.steps,
@@ -263,7 +265,7 @@ def main():
 
     peak, peak_kind = peaks()
     names = o2tpc.STAGES
-    k = int(np.argmax(stage))
+    k = int(np.argmax(stage[:11]))
     dom = names[k]
     achieved = STAGE_BYTES[dom] * n / (stage[k] / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -284,7 +286,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "tf_per_s": world / (ms_step / 1e3), "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)),
-            "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(10)},
+            "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(12)},
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "frac": path_frac, "peak": peak},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     if rank == 0:

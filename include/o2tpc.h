@@ -134,8 +134,10 @@ typedef struct {
    * gaps for the host reading sizes included): 0 ingest + row statistics +
    * grid, 1 row/cell sort, 2 NeighboursFinder, 3 NeighboursCleaner +
    * StartHitsFinder, 4 TrackletConstructor, 5 TrackletSelector, 6 sector-track
-   * fits, 7 merger, 8 final refit, 9 result download */
-  float ms_stage[10];
+   * fits, 7 merger, 8 final refit, 9 read-back of the result sizes,
+   * 10 result download; 11 is host time (not device) spent obtaining pinned
+   * result memory */
+  float ms_stage[12];
 } o2tpc_stats;
 
 /* Result of one TF; library-owned memory, valid until o2tpc_result_release. */

@@ -369,17 +369,19 @@ __device__ int refit_chain(const int* segs, int nseg, const SectorTrackBufs& sb,
 
 __global__ void __launch_bounds__(128) k_final_refit(int nHeads, const int* __restrict__ heads, SectorTrackBufs sb,
                                                      MergeBufs mb, const int2* __restrict__ syz,
-                                                     const int* __restrict__ sorig, const GeomConst* __restrict__ G,
-                                                     int forceFp64, OutBufs ob) {
+                                                     const int* __restrict__ sorig, const TFDesc* __restrict__ tfs,
+                                                     const GeomConst* __restrict__ G, int forceFp64, OutBufs ob) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nHeads) return;
   int segs[kMaxChain];
   int nseg = 0;
   for (int c = heads[t]; c >= 0 && nseg < kMaxChain; c = mb.next[c]) segs[nseg++] = c;
-  // cluster list: segments in chain order, ascending rows inside each
+  // cluster list: segments in chain order, ascending rows inside each, as
+  // indices into the TF's submitted order
+  const int inBase = tfs[sb.tf[segs[0]]].inBase;
   int o = ob.off[t];
   for (int j = 0; j < nseg; ++j)
-    for (int i = sb.off[segs[j]]; i < sb.off[segs[j] + 1]; ++i) ob.cl[o++] = sorig[sb.hits[i]];
+    for (int i = sb.off[segs[j]]; i < sb.off[segs[j] + 1]; ++i) ob.cl[o++] = sorig[sb.hits[i]] - inBase;
   const int zref = syz[sb.hits[sb.off[segs[0]]]].y;
   int flags = nseg > 1 ? 2 : 0;
   float par[5], cov[15], x, chi2;
@@ -505,9 +507,10 @@ void launch_chain_counts(int nHeads, const int* heads, const SectorTrackBufs sb,
 }
 
 void launch_final_refit(int nHeads, const int* heads, const SectorTrackBufs sb, MergeBufs mb, const int2* syz,
-                        const int* sorig, const GeomConst* G, int forceFp64, OutBufs ob, cudaStream_t st) {
+                        const int* sorig, const TFDesc* tfs, const GeomConst* G, int forceFp64, OutBufs ob,
+                        cudaStream_t st) {
   if (nHeads > 0)
-    k_final_refit<<<(nHeads + 127) / 128, 128, 0, st>>>(nHeads, heads, sb, mb, syz, sorig, G, forceFp64, ob);
+    k_final_refit<<<(nHeads + 127) / 128, 128, 0, st>>>(nHeads, heads, sb, mb, syz, sorig, tfs, G, forceFp64, ob);
     ++g_launch_count;
 }
 

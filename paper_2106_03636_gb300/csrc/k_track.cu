@@ -97,11 +97,16 @@ __device__ inline void load_state(KState<float>& s, const float* src) {
   for (int i = 0; i < 15; ++i) s.C[i] = src[6 + i];
 }
 
-// K7: one thread per start hit.
-__global__ void __launch_bounds__(128) k_tracklets(int nTl, const int* __restrict__ starts, const int* __restrict__ up,
-                                                   const RowGrid* __restrict__ grid, int nRows,
-                                                   const int* __restrict__ cellStart, const int2* __restrict__ syz,
-                                                   const GeomConst* __restrict__ G, TrackletBufs tb) {
+// K7: one thread per start hit.  The four passes of a tracklet (chain fit,
+// outward following, inward refit of the attached hits, inward following
+// below the chain) run as phases of one loop whose body holds a single
+// transport, search and update: a quarter of the code, and threads of a warp
+// in different phases still issue the same instructions.
+__global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, const int* __restrict__ starts,
+                                                      const int* __restrict__ up, const RowGrid* __restrict__ grid,
+                                                      int nRows, const int* __restrict__ cellStart,
+                                                      const int2* __restrict__ syz, const GeomConst* __restrict__ G,
+                                                      TrackletBufs tb) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nTl) return;
   const float zunit = G->zunit, bzc = G->bzc;
@@ -125,73 +130,131 @@ __global__ void __launch_bounds__(128) k_tracklets(int nTl, const int* __restric
   const float tphi = dy / dx;
   const float s0 = tphi / sqrtf(1.f + tphi * tphi);
   const float t0 = (hit_z(a2.y, zref, zunit) - hit_z(a0.y, zref, zunit)) / sqrtf(dx * dx + dy * dy);
+  // the state after the last accepted hit lives in shared memory (one column
+  // per thread) rather than in registers
+  __shared__ float s_last[21][128];
+  auto save_last = [&](const KState<float>& q) {
+    s_last[0][threadIdx.x] = q.x;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) s_last[1 + j][threadIdx.x] = q.p[j];
+#pragma unroll
+    for (int j = 0; j < 15; ++j) s_last[6 + j][threadIdx.x] = q.C[j];
+  };
+  auto load_last = [&](KState<float>& q) {
+    q.x = s_last[0][threadIdx.x];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) q.p[j] = s_last[1 + j][threadIdx.x];
+#pragma unroll
+    for (int j = 0; j < 15; ++j) q.C[j] = s_last[6 + j][threadIdx.x];
+  };
   KState<float> st;
   kf_reset<float>(st, x0, hit_y(a0.x, yref), hit_z(a0.y, zref, zunit), s0, t0, 0.f);
-  for (int i = 1; i < nc; ++i) {
-    if (kf_prop<float>(st, G->rowx[r0 + i], bzc) != 0) {
-      tb.nhits[k] = 0;
-      tb.nasc[k] = 0;
-      return;
-    }
-    const int2 p = syz[H[i]];
-    kf_update<float>(st, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
-  }
-  // outward following
-  KState<float> last = st;
-  int top = H[nc - 1];
-  int na = nc, misses = 0;
-  for (int r = r0 + nc; r < kNRow; ++r) {
-    if (kf_prop<float>(st, G->rowx[r], bzc) != 0) break;
-    if (fabsf(st.p[2]) > kSinFollow) break;
-    const int h = search_row(grid[Rs + r], G->npads[r], cellStart, syz, st, yref, zref, zunit);
-    if (h >= 0) {
-      const int2 p = syz[h];
-      kf_update<float>(st, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
-      H[na] = h;
-      Rw[na] = (uint8_t)r;
-      ++na;
-      top = h;
-      last = st;
-      misses = 0;
-    } else if (++misses >= kMaxMiss) {
-      break;
-    }
-  }
-  // inward: restart at the top hit, refit the attached hits, follow below
-  st = last;
-  {
+  // phases: 0 chain fit, 1 outward following, 2 inward refit, 3 inward following
+  int phase = 0, i = 1, r = 0, na = nc, nd = 0, misses = 0, top = H[nc - 1];
+  bool dropped = false;
+  // end of the outward following: restart at the top hit, fresh covariance
+  auto begin_refit = [&]() {
+    load_last(st);
     const int2 p = syz[top];
     st.p[0] = hit_y(p.x, yref);
     st.p[1] = hit_z(p.y, zref, zunit);
     reset_cov(st);
-  }
-  for (int i = na - 2; i >= 0; --i) {
-    if (kf_prop<float>(st, G->rowx[Rw[i]], bzc) != 0) continue;
-    const int2 p = syz[H[i]];
-    kf_update<float>(st, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
-  }
-  last = st;
-  int nd = 0;
-  misses = 0;
-  for (int r = r0 - 1; r >= 0; --r) {
-    if (kf_prop<float>(st, G->rowx[r], bzc) != 0) break;
-    if (fabsf(st.p[2]) > kSinFollow) break;
-    const int h = search_row(grid[Rs + r], G->npads[r], cellStart, syz, st, yref, zref, zunit);
-    if (h >= 0) {
-      const int2 p = syz[h];
-      kf_update<float>(st, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
-      H[na + nd] = h;
-      Rw[na + nd] = (uint8_t)r;
-      ++nd;
-      last = st;
-      misses = 0;
-    } else if (++misses >= kMaxMiss) {
+    i = na - 2;
+    phase = 2;
+  };
+  for (;;) {
+    int row, hit = -1;
+    bool search = false;
+    if (phase == 0) {
+      if (i >= nc) {
+        save_last(st);
+        r = r0 + nc;
+        misses = 0;
+        phase = 1;
+        continue;
+      }
+      row = r0 + i;
+      hit = H[i];
+    } else if (phase == 1) {
+      if (r >= kNRow) {
+        begin_refit();
+        continue;
+      }
+      row = r;
+      search = true;
+    } else if (phase == 2) {
+      if (i < 0) {
+        save_last(st);
+        r = r0 - 1;
+        misses = 0;
+        phase = 3;
+        continue;
+      }
+      row = Rw[i];
+      hit = H[i];
+    } else {
+      if (r < 0) break;
+      row = r;
+      search = true;
+    }
+    bool stop = kf_prop<float>(st, G->rowx[row], bzc) != 0;
+    if (!stop && search) {
+      stop = fabsf(st.p[2]) > kSinFollow;
+      if (!stop) hit = search_row(grid[Rs + row], G->npads[row], cellStart, syz, st, yref, zref, zunit);
+    }
+    if (stop) {
+      if (phase == 0) {
+        dropped = true;
+        break;
+      }
+      if (phase == 2) {
+        --i;
+        continue;
+      }
+      if (phase == 1) {
+        begin_refit();
+        continue;
+      }
       break;
     }
+    if (hit >= 0) {
+      const int2 p = syz[hit];
+      kf_update<float>(st, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
+      if (phase == 1) {
+        H[na] = hit;
+        Rw[na] = (uint8_t)row;
+        ++na;
+        top = hit;
+        save_last(st);
+        misses = 0;
+      } else if (phase == 3) {
+        H[na + nd] = hit;
+        Rw[na + nd] = (uint8_t)row;
+        ++nd;
+        save_last(st);
+        misses = 0;
+      }
+    } else if (search && ++misses >= kMaxMiss) {
+      if (phase == 1) {
+        begin_refit();
+        continue;
+      }
+      break;
+    }
+    if (phase == 0) ++i;
+    else if (phase == 1) ++r;
+    else if (phase == 2) --i;
+    else --r;
+  }
+  if (dropped) {
+    tb.nhits[k] = 0;
+    tb.nasc[k] = 0;
+    return;
   }
   tb.nhits[k] = na + nd;
   tb.nasc[k] = na;
-  store_state(tb.state + (size_t)k * 21, last, yref);
+  load_last(st);
+  store_state(tb.state + (size_t)k * 21, st, yref);
 }
 
 __device__ inline int tf_of(const int* __restrict__ begin, int nTF, int k) {

@@ -88,13 +88,11 @@ struct Job {
   double t_submit = 0, t_start = 0, t_end = 0;
   bool done = false;
   int status = O2TPC_OK;
-  // result storage
+  // result storage: one pinned host block from the context's pool
   o2tpc_result res{};
-  std::vector<uint64_t> off;
-  std::vector<uint32_t> cl, zref;
-  std::vector<float> x, alpha, par, cov, chi2;
-  std::vector<int32_t> ndf;
-  std::vector<uint8_t> sector, flags;
+  void* host = nullptr;
+  size_t hostBytes = 0;
+  uint64_t emptyOffset = 0;
   std::shared_ptr<BatchMem> mem;  // kept stages
   int tfIndex = 0;
 };
@@ -115,7 +113,7 @@ struct Ctx {
   bool stop = false;
   int fatal = O2TPC_OK;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  cudaEvent_t evs[11] = {};
+  cudaEvent_t evs[12] = {};
   // pinned staging for descriptors and results
   void* hStage = nullptr;
   size_t hStageBytes = 0;
@@ -138,6 +136,31 @@ struct Ctx {
     if (!p) return;
     if (cfg.dev_free) cfg.dev_free(p, cfg.alloc_user);
     else cudaFreeAsync(p, stream);
+  }
+  // Pool of pinned host blocks for results (sizes rounded to 1 MiB).
+  std::mutex poolMu;
+  std::multimap<size_t, void*> pinnedFree;
+  void* pinned_get(size_t bytes, size_t* got) {
+    size_t want = (bytes + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
+    {
+      std::lock_guard<std::mutex> lk(poolMu);
+      auto it = pinnedFree.lower_bound(want);
+      if (it != pinnedFree.end() && it->first <= 2 * want) {
+        void* p = it->second;
+        *got = it->first;
+        pinnedFree.erase(it);
+        return p;
+      }
+    }
+    void* p = nullptr;
+    CK(cudaMallocHost(&p, want));
+    *got = want;
+    return p;
+  }
+  void pinned_put(void* p, size_t bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(poolMu);
+    pinnedFree.emplace(bytes, p);
   }
   void* stage(size_t bytes) {
     if (bytes > hStageBytes) {
@@ -458,7 +481,8 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CKL();
   scan_exclusive(trkNcl, ob.off, nHeads, scratch, st);
   CKL();
-  launch_final_refit(nHeads, heads, sb, mb, syz, sorig, G, (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, ob, st);
+  launch_final_refit(nHeads, heads, sb, mb, syz, sorig, dTF, G, (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, ob,
+                     st);
   CKL();
   int* trkTfBegin = dalloc<int>(M, B + 1);
   launch_lower_bounds(heads, nHeads, stTfBegin, B + 1, trkTfBegin, st);
@@ -466,50 +490,72 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CK(cudaEventRecord(c->ev1, st));
   CK(cudaEventRecord(c->evs[9], st));
 
-  // ---- A12: download
+  // ---- A12: download: sizes first, then every TF's arrays straight into
+  // its own pinned result block
   const size_t nT = (size_t)nHeads;
-  const size_t bOff = 4 * (nT + 1), bCl = 4 * (size_t)nStHits, bX = 4 * nT, bPar = 20 * nT, bCov = 60 * nT;
-  auto r16 = [](size_t b) { return (b + 15) / 16 * 16; };
-  const size_t tot = r16(bOff) + r16(bCl) + 5 * r16(bX) /*x alpha chi2 ndf zref*/ + r16(bPar) + r16(bCov) +
-                     2 * r16(nT) /*sector flags*/ + 3 * r16(sizeof(int) * (B + 1)) + 2 * r16(4);
-  char* h = static_cast<char*>(c->stage(tot));
-  char* q = h;
-  auto take = [&](const void* dsrc, size_t bytes) -> char* {
-    char* dst = q;
-    if (bytes) CK(cudaMemcpyAsync(dst, dsrc, bytes, cudaMemcpyDeviceToHost, st));
-    q += (bytes + 15) / 16 * 16;
-    return dst;
-  };
-  const int* hOff = reinterpret_cast<const int*>(take(ob.off, bOff));
-  const int* hCl = reinterpret_cast<const int*>(take(ob.cl, bCl));
-  const float* hX = reinterpret_cast<const float*>(take(ob.x, bX));
-  const float* hA = reinterpret_cast<const float*>(take(ob.alpha, bX));
-  const float* hPar = reinterpret_cast<const float*>(take(ob.par, bPar));
-  const float* hCov = reinterpret_cast<const float*>(take(ob.cov, bCov));
-  const float* hChi = reinterpret_cast<const float*>(take(ob.chi2, bX));
-  const int* hNdf = reinterpret_cast<const int*>(take(ob.ndf, bX));
-  const uint8_t* hSec = reinterpret_cast<const uint8_t*>(take(ob.sector, nT));
-  const uint8_t* hFl = reinterpret_cast<const uint8_t*>(take(ob.flags, nT));
-  const int* hZr = reinterpret_cast<const int*>(take(ob.zref, bX));
-  const int* hTrkTf = reinterpret_cast<const int*>(take(trkTfBegin, sizeof(int) * (B + 1)));
-  const int* hStTf = reinterpret_cast<const int*>(take(stTfBegin, sizeof(int) * (B + 1)));
-  const int* hTlTf = reinterpret_cast<const int*>(take(tlTfBegin, sizeof(int) * (B + 1)));
-  const unsigned* hErr = reinterpret_cast<const unsigned*>(take(dErr, 4));
-  const int* hFb = reinterpret_cast<const int*>(take(ob.nFallback, 4));
+  int* hSmall = static_cast<int*>(c->stage(sizeof(int) * (nT + 1 + 3 * (B + 1) + 8)));
+  int* hOff = hSmall;
+  int* hTrkTf = hOff + nT + 1;
+  int* hStTf = hTrkTf + B + 1;
+  int* hTlTf = hStTf + B + 1;
+  unsigned* hErr = reinterpret_cast<unsigned*>(hTlTf + B + 1);
+  CK(cudaMemcpyAsync(hOff, ob.off, sizeof(int) * (nT + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hTrkTf, trkTfBegin, sizeof(int) * (B + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hStTf, stTfBegin, sizeof(int) * (B + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hTlTf, tlTfBegin, sizeof(int) * (B + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hErr, dErr, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   std::vector<RowGrid> tfFirstRow(B);
   for (int i = 0; i < B; ++i) CK(cudaMemcpyAsync(&tfFirstRow[i], grid + (size_t)i * kRowsPerTF, sizeof(RowGrid),
                                                  cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(c->evs[10], st));
   CK(cudaStreamSynchronize(st));
+  auto r16 = [](size_t x) { return (x + 15) / 16 * 16; };
+  double hostAllocMs = 0.0;
+  for (int i = 0; i < B; ++i) {
+    Job& J = *jobs[i];
+    const int t0 = hTrkTf[i], t1 = hTrkTf[i + 1];
+    const size_t nt = (size_t)(t1 - t0);
+    const size_t ncl = (size_t)(hOff[t1] - hOff[t0]);
+    const size_t bytes = r16(8 * (nt + 1)) + r16(4 * ncl) + 5 * r16(4 * nt) + r16(20 * nt) + r16(60 * nt) +
+                         2 * r16(nt) + 64;
+    const double ta = now_ms();
+    J.host = c->pinned_get(bytes, &J.hostBytes);
+    hostAllocMs += now_ms() - ta;
+    char* q = static_cast<char*>(J.host);
+    auto take = [&](const void* dsrc, size_t nb) -> char* {
+      char* dst = q;
+      if (nb) CK(cudaMemcpyAsync(dst, dsrc, nb, cudaMemcpyDeviceToHost, st));
+      q += r16(nb);
+      return dst;
+    };
+    uint64_t* off64 = reinterpret_cast<uint64_t*>(q);
+    q += r16(8 * (nt + 1));
+    o2tpc_result& R = J.res;
+    R.n_tracks = (uint64_t)nt;
+    R.offsets = off64;
+    R.cluster_idx = reinterpret_cast<const uint32_t*>(take(ob.cl + hOff[t0], 4 * ncl));
+    R.x = reinterpret_cast<const float*>(take(ob.x + t0, 4 * nt));
+    R.alpha = reinterpret_cast<const float*>(take(ob.alpha + t0, 4 * nt));
+    R.par = reinterpret_cast<const float*>(take(ob.par + 5 * (size_t)t0, 20 * nt));
+    R.cov = reinterpret_cast<const float*>(take(ob.cov + 15 * (size_t)t0, 60 * nt));
+    R.chi2 = reinterpret_cast<const float*>(take(ob.chi2 + t0, 4 * nt));
+    R.ndf = reinterpret_cast<const int32_t*>(take(ob.ndf + t0, 4 * nt));
+    R.zeta_ref = reinterpret_cast<const uint32_t*>(take(ob.zref + t0, 4 * nt));
+    R.sector = reinterpret_cast<const uint8_t*>(take(ob.sector + t0, nt));
+    R.flags = reinterpret_cast<const uint8_t*>(take(ob.flags + t0, nt));
+    for (size_t k = 0; k <= nt; ++k) off64[k] = (uint64_t)(hOff[t0 + k] - hOff[t0]);
+  }
+  CK(cudaEventRecord(c->evs[11], st));
+  CK(cudaStreamSynchronize(st));
   float devMs = 0.f;
-  float stageMs[10];
-  for (int k = 0; k < 10; ++k) {
+  float stageMs[12] = {};
+  for (int k = 0; k < 11; ++k) {
     stageMs[k] = 0.f;
     cudaEventElapsedTime(&stageMs[k], c->evs[k], c->evs[k + 1]);
   }
+  stageMs[11] = (float)hostAllocMs;
   const long long nLaunch = g_launch_count;
   cudaEventElapsedTime(&devMs, c->ev0, c->ev1);
-  (void)hFb;
   const bool inputBad = (*hErr & kErrInput) != 0;
 
   const double tEnd = now_ms();
@@ -525,52 +571,21 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   }
   for (int i = 0; i < B; ++i) {
     Job& J = *jobs[i];
-    const int t0 = hTrkTf[i], t1 = hTrkTf[i + 1], nt = t1 - t0;
-    J.off.resize(nt + 1);
-    const int c0 = hOff[t0];
-    for (int k = 0; k <= nt; ++k) J.off[k] = (uint64_t)(hOff[t0 + k] - c0);
-    const int ncl = hOff[t1] - c0;
-    J.cl.resize(ncl);
-    for (int k = 0; k < ncl; ++k) J.cl[k] = (uint32_t)(hCl[c0 + k] - tfd[i].inBase);
-    J.x.assign(hX + t0, hX + t1);
-    J.alpha.assign(hA + t0, hA + t1);
-    J.par.assign(hPar + 5 * (size_t)t0, hPar + 5 * (size_t)t1);
-    J.cov.assign(hCov + 15 * (size_t)t0, hCov + 15 * (size_t)t1);
-    J.chi2.assign(hChi + t0, hChi + t1);
-    J.ndf.assign(hNdf + t0, hNdf + t1);
-    J.sector.assign(hSec + t0, hSec + t1);
-    J.flags.assign(hFl + t0, hFl + t1);
-    J.zref.resize(nt);
-    uint64_t fb = 0;
-    for (int k = 0; k < nt; ++k) {
-      J.zref[k] = (uint32_t)hZr[t0 + k];
-      fb += (J.flags[k] & 1) ? 1 : 0;
-    }
     o2tpc_result& R = J.res;
-    R.n_tracks = (uint64_t)nt;
-    R.offsets = J.off.data();
-    R.cluster_idx = J.cl.data();
-    R.x = J.x.data();
-    R.alpha = J.alpha.data();
-    R.par = J.par.data();
-    R.cov = J.cov.data();
-    R.chi2 = J.chi2.data();
-    R.ndf = J.ndf.data();
-    R.sector = J.sector.data();
-    R.flags = J.flags.data();
-    R.zeta_ref = J.zref.data();
+    uint64_t fb = 0;
+    for (uint64_t k = 0; k < R.n_tracks; ++k) fb += (R.flags[k] & 1) ? 1 : 0;
     R.user_tag = J.tf.user_tag;
     R.stats.n_clusters = J.tf.n;
     R.stats.n_tracklets = (uint64_t)(hTlTf[i + 1] - hTlTf[i]);
     R.stats.n_sector_tracks = (uint64_t)(hStTf[i + 1] - hStTf[i]);
-    R.stats.n_tracks = (uint64_t)nt;
+    R.stats.n_tracks = R.n_tracks;
     R.stats.n_fp64_fallback = fb;
     R.stats.batch_size = (uint32_t)B;
     R.stats.ms_queue = (float)(J.t_start - J.t_submit);
     R.stats.ms_batch = (float)(tEnd - J.t_start);
     R.stats.ms_device = devMs;
     R.stats.n_launches = (uint64_t)nLaunch;
-    for (int k = 0; k < 10; ++k) R.stats.ms_stage[k] = stageMs[k];
+    for (int k = 0; k < 12; ++k) R.stats.ms_stage[k] = stageMs[k];
     J.status = inputBad ? O2TPC_EINVAL : O2TPC_OK;
     R.status = J.status;
     J.tfIndex = i;
@@ -640,8 +655,8 @@ void worker_main(Ctx* c) {
           j->res = o2tpc_result{};
           j->res.status = status;
           j->res.user_tag = j->tf.user_tag;
-          j->off.assign(1, 0);
-          j->res.offsets = j->off.data();
+          j->emptyOffset = 0;
+          j->res.offsets = &j->emptyOffset;
         }
         j->t_end = now_ms();
         j->done = true;
@@ -779,9 +794,13 @@ void o2tpc_result_release(o2tpc_ctx* ctx, const o2tpc_result* res) {
     }
   }
   // dropping j releases its results and its reference on the kept stages
-  if (j && j->mem) {
-    cudaSetDevice(c->cfg.device);
-    j->mem.reset();
+  if (j) {
+    c->pinned_put(j->host, j->hostBytes);
+    j->host = nullptr;
+    if (j->mem) {
+      cudaSetDevice(c->cfg.device);
+      j->mem.reset();
+    }
   }
 }
 
@@ -798,9 +817,14 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
   cudaSetDevice(c->cfg.device);
   {
     std::lock_guard<std::mutex> lk(c->mu);
-    for (auto& kv : c->jobs) kv.second->mem.reset();
+    for (auto& kv : c->jobs) {
+      kv.second->mem.reset();
+      if (kv.second->host) cudaFreeHost(kv.second->host);
+    }
     c->jobs.clear();
   }
+  for (auto& kv : c->pinnedFree) cudaFreeHost(kv.second);
+  c->pinnedFree.clear();
   c->dev_free(c->dGeom);
   cudaStreamSynchronize(c->stream);
   if (c->hStage) cudaFreeHost(c->hStage);

@@ -191,6 +191,38 @@ __device__ inline void kf_sandwich(T* C, const T J[5][5]) {
     }
 }
 
+// C <- J C J^T for the transport Jacobian J = I + a02 e0e2' + a04 e0e4' +
+// a12 e1e2' + a13 e1e3' + a14 e1e4' + a24 e2e4' (the only non-zero
+// off-diagonal terms), written out: T = J C for rows 0-2 (rows 3, 4 of T are
+// those of C), then C' = T J^T on the lower triangle.
+template <typename T>
+__device__ inline void kf_sandwich_transport(T* C, T a02, T a04, T a12, T a13, T a14, T a24) {
+  T c[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) c[i][j] = C[ix(i, j)];
+  T t0[5], t1[5], t2[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    t0[k] = c[0][k] + a02 * c[2][k] + a04 * c[4][k];
+    t1[k] = c[1][k] + a12 * c[2][k] + a13 * c[3][k] + a14 * c[4][k];
+    t2[k] = c[2][k] + a24 * c[4][k];
+  }
+  C[ix(0, 0)] = t0[0] + a02 * t0[2] + a04 * t0[4];
+  C[ix(1, 0)] = t1[0] + a02 * t1[2] + a04 * t1[4];
+  C[ix(1, 1)] = t1[1] + a12 * t1[2] + a13 * t1[3] + a14 * t1[4];
+  C[ix(2, 0)] = t2[0] + a02 * t2[2] + a04 * t2[4];
+  C[ix(2, 1)] = t2[1] + a12 * t2[2] + a13 * t2[3] + a14 * t2[4];
+  C[ix(2, 2)] = t2[2] + a24 * t2[4];
+  C[ix(3, 0)] = c[3][0] + a02 * c[3][2] + a04 * c[3][4];
+  C[ix(3, 1)] = c[3][1] + a12 * c[3][2] + a13 * c[3][3] + a14 * c[3][4];
+  C[ix(3, 2)] = c[3][2] + a24 * c[3][4];
+  C[ix(4, 0)] = c[4][0] + a02 * c[4][2] + a04 * c[4][4];
+  C[ix(4, 1)] = c[4][1] + a12 * c[4][2] + a13 * c[4][3] + a14 * c[4][4];
+  C[ix(4, 2)] = c[4][2] + a24 * c[4][4];
+}
+
 // Helix transport to x2 in a uniform field: d(sin phi)/dx = k = (q/pT) bzc;
 // dy = dx (s1+s2)/(c1+c2); transverse path ds = 2 asin(|k| chord/2)/|k|
 // (the chord when |k| chord < 1e-6), signed like dx; dzeta = t ds.
@@ -219,22 +251,17 @@ __device__ inline int kf_prop(KState<T>& s, T x2, T bzc) {
   T f1 = dx * (s1 + s2) / (c1 * c2 * cc);
   T fm = T(0.5) * dx * (sm + s2) / (cm * c2 * (cm + c2));
   T ddsdk = (fabs(k * dx) < T(0.05)) ? dx * (f1 + T(4) * fm) / T(6) : (dx / c2 - ds) / k;
-  T J[5][5];
-#pragma unroll
-  for (int i = 0; i < 5; ++i)
-#pragma unroll
-    for (int j = 0; j < 5; ++j) J[i][j] = (i == j) ? T(1) : T(0);
-  J[0][2] = dx * (T(2) * cc + (s1 + s2) * (s1 / c1 + s2 / c2)) / (cc * cc);
-  J[0][4] = dx * dx * bzc * (cc + (s1 + s2) * s2 / c2) / (cc * cc);
-  J[1][2] = tz * f1;
-  J[1][3] = ds;
-  J[1][4] = tz * bzc * ddsdk;
-  J[2][4] = dx * bzc;
+  const T a02 = dx * (T(2) * cc + (s1 + s2) * (s1 / c1 + s2 / c2)) / (cc * cc);
+  const T a04 = dx * dx * bzc * (cc + (s1 + s2) * s2 / c2) / (cc * cc);
+  const T a12 = tz * f1;
+  const T a13 = ds;
+  const T a14 = tz * bzc * ddsdk;
+  const T a24 = dx * bzc;
   s.p[0] += dy;
   s.p[1] += tz * ds;
   s.p[2] = s2;
   s.x = x2;
-  kf_sandwich<T>(s.C, J);
+  kf_sandwich_transport<T>(s.C, a02, a04, a12, a13, a14, a24);
   return 0;
 }
 

@@ -98,7 +98,7 @@ void launch_chain_counts(int nHeads, const int* heads, const SectorTrackBufs sb,
 
 struct OutBufs {
   int* off;         // [nTrk + 1] batch-global offsets into cl
-  int* cl;          // input index (batch-global) of each cluster
+  int* cl;          // input index of each cluster inside its TF
   float* x;
   float* alpha;
   float* par;       // [nTrk * 5]
@@ -111,6 +111,7 @@ struct OutBufs {
   int* nFallback;   // [1]
 };
 void launch_final_refit(int nHeads, const int* heads, const SectorTrackBufs sb, MergeBufs mb, const int2* syz,
-                        const int* sorig, const GeomConst* G, int forceFp64, OutBufs ob, cudaStream_t st);
+                        const int* sorig, const TFDesc* tfs, const GeomConst* G, int forceFp64, OutBufs ob,
+                        cudaStream_t st);
 
 }  // namespace o2tpc

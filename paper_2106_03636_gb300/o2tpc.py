@@ -81,11 +81,11 @@ class o2tpc_stats(ctypes.Structure):
         ("ms_batch", ctypes.c_float),
         ("ms_device", ctypes.c_float),
         ("n_launches", ctypes.c_uint64),
-        ("ms_stage", ctypes.c_float * 10),
+        ("ms_stage", ctypes.c_float * 12),
     ]
 
 STAGES = ("ingest", "sort", "neighbours", "clean_starts", "tracklets", "selection", "sector_fit", "merge",
-          "refit", "download")
+          "refit", "sizes", "download", "host_alloc")
 
 
 class o2tpc_result(ctypes.Structure):
@@ -294,6 +294,24 @@ class Tracker:
         else:
             o2tpc_result_release(self.ctx, res)
             self._pending.pop(ticket, None)
+        return out
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Waits for ``ticket`` and releases it without copying the arrays;
+        returns status, track / cluster counts and the stats (None on
+        timeout)."""
+        rc, res = o2tpc_poll(self.ctx, ticket, timeout_ms)
+        if rc == O2TPC_PENDING:
+            return None
+        if rc != O2TPC_OK:
+            raise O2TPCError(rc, "o2tpc_poll")
+        r = res.contents
+        n = int(r.n_tracks)
+        out = dict(status=int(r.status), n_tracks=n, n_cluster_refs=int(r.offsets[n]),
+                   stats={k: (list(getattr(r.stats, k)) if k == "ms_stage" else getattr(r.stats, k))
+                          for k, _ in o2tpc_stats._fields_})
+        o2tpc_result_release(self.ctx, res)
+        self._pending.pop(ticket, None)
         return out
 
     def release(self, ticket: int, result: dict) -> None:
