@@ -214,6 +214,40 @@ const char* o2tpc_strerror(int32_t status);
 int o2tpc_get_stage(o2tpc_ctx* ctx, uint64_t ticket, const char* name, void* dst, uint64_t capacity,
                     uint64_t* needed);
 
+/* Allocation-free grid binning and stable sort of one TF.
+ *
+ * The paper has no counterpart of this entry point.  It is for callers that
+ * cannot allocate device memory while they run (a host framework that owns
+ * every device buffer, a fixed memory plan, code that must not synchronise
+ * the device through cudaMalloc or grow its footprint after start-up): the
+ * step's scratch memory is a set of file-scope static device arrays of fixed
+ * size (about 6 MB, held by every GPU that loads the library until the
+ * process exits), so this call allocates nothing, neither directly nor
+ * through any allocating library routine.
+ *
+ * It computes, for one TF, what o2tpc_get_stage reports after a full run as
+ * "sorted_orig", "sorted_yz", "row_grid" and "cell_start".
+ *   tf           n <= O2TPC_STATIC_MAX_CLUSTERS (else O2TPC_ETOOBIG), location
+ *                O2TPC_LOC_DEVICE; its buffers are read, not modified.
+ *   vdrift_cm_us drift velocity (> 0) of the float-input quantisation.
+ *   sorted_orig  device int32[n]: input index of each sorted hit.
+ *   sorted_yz    device int32[n][2]: y and zeta in integer units, sorted.
+ *   row_grid     device int32[5472][8]: start, count, cellBase, ny, nz, cz,
+ *                zmin, 0 per (sector, row).
+ *   cell_start   device int32[cell_capacity] with cell_capacity >=
+ *                n / 4 + 46 * 5472 + 2 (else O2TPC_EINVAL): the first sorted
+ *                hit of every cell, plus the total at index cells.
+ *   stream       cudaStream_t to run on (NULL: the default stream).
+ * The call returns when the work is done: O2TPC_OK, O2TPC_EINVAL (bad
+ * arguments or invalid cluster content), O2TPC_ETOOBIG, O2TPC_ECUDA.
+ * The static arrays' device addresses are looked up during the first call on
+ * each device (with that device current), so make that first call before any
+ * stream capture.  Every call shares the arrays and leaves its contents in
+ * them: calls that overlap on the GPU race and must be serialised. */
+#define O2TPC_STATIC_MAX_CLUSTERS 262144
+int o2tpc_sort_tf_static(const o2tpc_tf* tf, double vdrift_cm_us, int32_t* sorted_orig, int32_t* sorted_yz,
+                         int32_t* row_grid, int32_t* cell_start, uint64_t cell_capacity, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

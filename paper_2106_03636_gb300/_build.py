@@ -29,6 +29,7 @@ CUDA_SOURCES = [
     "k_ca.cu",
     "k_track.cu",
     "k_merge.cu",
+    "o2tpc_static.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

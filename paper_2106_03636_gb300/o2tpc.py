@@ -138,6 +138,9 @@ def load(build: bool = True) -> ctypes.CDLL:
         lib.o2tpc_destroy.argtypes = [vp]
         lib.o2tpc_strerror.restype = ctypes.c_char_p
         lib.o2tpc_strerror.argtypes = [ctypes.c_int32]
+        lib.o2tpc_sort_tf_static.restype = ctypes.c_int
+        lib.o2tpc_sort_tf_static.argtypes = [ctypes.POINTER(o2tpc_tf), ctypes.c_double, vp, vp, vp, vp,
+                                             ctypes.c_uint64, vp]
         lib.o2tpc_get_stage.restype = ctypes.c_int
         lib.o2tpc_get_stage.argtypes = [vp, ctypes.c_uint64, ctypes.c_char_p, vp, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_uint64)]
@@ -180,6 +183,17 @@ def o2tpc_get_stage(ctx, ticket: int, name: str, dst, capacity: int):
     need = ctypes.c_uint64()
     rc = load().o2tpc_get_stage(ctx, ticket, name.encode(), dst, capacity, ctypes.byref(need))
     return rc, need.value
+
+
+O2TPC_STATIC_MAX_CLUSTERS = 262144
+
+
+def o2tpc_sort_tf_static(tf: o2tpc_tf, vdrift: float, sorted_orig, sorted_yz, row_grid, cell_start,
+                         cell_capacity: int, stream) -> int:
+    """Allocation-free binning + sort of one TF: every pointer is a device
+    buffer the caller owns; nothing is allocated by the call."""
+    return load().o2tpc_sort_tf_static(ctypes.byref(tf), vdrift, sorted_orig, sorted_yz, row_grid, cell_start,
+                                       cell_capacity, stream)
 
 
 # ---------------------------------------------------------- helpers
