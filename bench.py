@@ -53,7 +53,7 @@ STAGE_BYTES = {
     "refit": 0.5,
     "sizes": 0.0,
     "download": 0.0,
-    "host_alloc": 0.0,
+    "host_prep": 0.0,
 }
 PATH_BYTES = 64.0
 

@@ -135,8 +135,8 @@ typedef struct {
    * grid, 1 row/cell sort, 2 NeighboursFinder, 3 NeighboursCleaner +
    * StartHitsFinder, 4 TrackletConstructor, 5 TrackletSelector, 6 sector-track
    * fits, 7 merger, 8 final refit, 9 read-back of the result sizes,
-   * 10 result download; 11 is host time (not device) spent obtaining pinned
-   * result memory */
+   * 10 result download; 11 is host time (not device) spent preparing the
+   * result copies (pinned blocks, offsets) inside step 10 */
   float ms_stage[12];
 } o2tpc_stats;
 

@@ -12,6 +12,8 @@
 
 namespace o2tpc {
 
+constexpr int kNFCand = 4;  // candidates per side held in registers by the NeighboursFinder
+
 // K4: one thread per hit; blocks tile the rows (nfBlockStart maps a block to
 // its row).
 __global__ void __launch_bounds__(kNFBlock) k_neighbours(const RowGrid* __restrict__ grid,
@@ -34,27 +36,85 @@ __global__ void __launch_bounds__(kNFBlock) k_neighbours(const RowGrid* __restri
     int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
     if (cell_range(gu, npu, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, uy0, uy1, uz0, uz1) &&
         cell_range(gd, npd, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, dy0, dy1, dz0, dz1)) {
-      int bestD = INT_MAX;
-      const int y2 = 2 * hh.x, z2 = 2 * hh.y;
+      // Collect the in-window candidates of each side into registers (up to
+      // kNFCand each), then evaluate the pairs in one fixed, predicated loop:
+      // every lane of the warp runs the same iterations.  Lanes with more
+      // candidates take the general nested loop.  The result is the
+      // lexicographic minimum of (D, u, d) either way.
+      int ui[kNFCand], di[kNFCand];
+      int2 up_[kNFCand], dp_[kNFCand];
+      int nu = 0, nd = 0;
       for (int izu = uz0; izu <= uz1; ++izu) {
         const int ua = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy0);
         const int ub = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy1 + 1);
         for (int u = ua; u < ub; ++u) {
           const int2 pu = __ldg(syz + u);
           if (abs(pu.x - hh.x) > kWinY || abs(pu.y - hh.y) > kWinZ) continue;
-          for (int izd = dz0; izd <= dz1; ++izd) {
-            const int da = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy0);
-            const int db = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy1 + 1);
-            for (int d = da; d < db; ++d) {
-              const int2 pd = __ldg(syz + d);
-              if (abs(pd.x - hh.x) > kWinY || abs(pd.y - hh.y) > kWinZ) continue;
-              const int ey = y2 - pu.x - pd.x, ez = z2 - pu.y - pd.y;
+#pragma unroll
+          for (int q = 0; q < kNFCand; ++q)
+            if (q == nu) {
+              ui[q] = u;
+              up_[q] = pu;
+            }
+          ++nu;
+        }
+      }
+      if (nu > 0) {
+        for (int izd = dz0; izd <= dz1; ++izd) {
+          const int da = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy0);
+          const int db = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy1 + 1);
+          for (int d = da; d < db; ++d) {
+            const int2 pd = __ldg(syz + d);
+            if (abs(pd.x - hh.x) > kWinY || abs(pd.y - hh.y) > kWinZ) continue;
+#pragma unroll
+            for (int q = 0; q < kNFCand; ++q)
+              if (q == nd) {
+                di[q] = d;
+                dp_[q] = pd;
+              }
+            ++nd;
+          }
+        }
+      }
+      int bestD = INT_MAX;
+      const int y2 = 2 * hh.x, z2 = 2 * hh.y;
+      if (nu <= kNFCand && nd <= kNFCand) {
+#pragma unroll
+        for (int a = 0; a < kNFCand; ++a)
+#pragma unroll
+          for (int b = 0; b < kNFCand; ++b) {
+            if (a < nu && b < nd) {
+              const int ey = y2 - up_[a].x - dp_[b].x, ez = z2 - up_[a].y - dp_[b].y;
               const int D = kWeightY * ey * ey + kWeightZ * ez * ez;
-              if (D > kMaxMetric) continue;
-              if (D < bestD || (D == bestD && (u < bu || (u == bu && d < bd)))) {
+              const int u = ui[a], d = di[b];
+              if (D <= kMaxMetric && (D < bestD || (D == bestD && (u < bu || (u == bu && d < bd))))) {
                 bestD = D;
                 bu = u;
                 bd = d;
+              }
+            }
+          }
+      } else {
+        for (int izu = uz0; izu <= uz1; ++izu) {
+          const int ua = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy0);
+          const int ub = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy1 + 1);
+          for (int u = ua; u < ub; ++u) {
+            const int2 pu = __ldg(syz + u);
+            if (abs(pu.x - hh.x) > kWinY || abs(pu.y - hh.y) > kWinZ) continue;
+            for (int izd = dz0; izd <= dz1; ++izd) {
+              const int da = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy0);
+              const int db = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy1 + 1);
+              for (int d = da; d < db; ++d) {
+                const int2 pd = __ldg(syz + d);
+                if (abs(pd.x - hh.x) > kWinY || abs(pd.y - hh.y) > kWinZ) continue;
+                const int ey = y2 - pu.x - pd.x, ez = z2 - pu.y - pd.y;
+                const int D = kWeightY * ey * ey + kWeightZ * ez * ez;
+                if (D > kMaxMetric) continue;
+                if (D < bestD || (D == bestD && (u < bu || (u == bu && d < bd)))) {
+                  bestD = D;
+                  bu = u;
+                  bd = d;
+                }
               }
             }
           }

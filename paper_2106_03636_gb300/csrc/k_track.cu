@@ -9,6 +9,8 @@
 // (nHits << 32 | ~id), which makes the result independent of thread order,
 // splits tracklets at gaps of more than 4 rows and keeps segments of >= 10
 // owned hits as sector tracks, each refitted outward and inward.
+#include <algorithm>
+
 #include "o2tpc_kernels.cuh"
 
 namespace o2tpc {
@@ -50,6 +52,7 @@ __device__ int search_row(const RowGrid& g, int npads, const int* __restrict__ c
   long long zhi = zref + clamp_ll(ceilf((s.p[1] + wz) / zunit)) + 1;
   int iy0, iy1, iz0, iz1;
   if (!cell_range(g, npads, ylo, yhi, zlo, zhi, iy0, iy1, iz0, iz1)) return -1;
+  const float isy2 = 1.f / sy2, isz2 = 1.f / sz2;
   int best = -1;
   float bchi = 0.f;
   for (int iz = iz0; iz <= iz1; ++iz) {
@@ -59,7 +62,7 @@ __device__ int search_row(const RowGrid& g, int npads, const int* __restrict__ c
       const int2 p = __ldg(syz + h);
       const float dy = hit_y(p.x, yref) - s.p[0], dz = hit_z(p.y, zref, zunit) - s.p[1];
       if (fabsf(dy) > wy || fabsf(dz) > wz) continue;
-      const float chi = dy * dy / sy2 + dz * dz / sz2;
+      const float chi = dy * dy * isy2 + dz * dz * isz2;
       if (chi > kChi2Follow) continue;
       if (best < 0 || chi < bchi || (chi == bchi && h < best)) {
         best = h;
@@ -97,39 +100,20 @@ __device__ inline void load_state(KState<float>& s, const float* src) {
   for (int i = 0; i < 15; ++i) s.C[i] = src[6 + i];
 }
 
-// K7: one thread per start hit.  The four passes of a tracklet (chain fit,
-// outward following, inward refit of the attached hits, inward following
-// below the chain) run as phases of one loop whose body holds a single
-// transport, search and update: a quarter of the code, and threads of a warp
-// in different phases still issue the same instructions.
-__global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, const int* __restrict__ starts,
+// K7: persistent threads, one tracklet at a time each, taking the next start
+// hit from a global counter as soon as the previous tracklet is done (no lane
+// idles until the longest tracklet of its warp ends).  The passes of a
+// tracklet (chain fit, outward following, inward refit of the attached hits,
+// inward following below the chain) are phases of one loop whose body holds a
+// single transport, search and update: threads of a warp in different phases
+// still issue the same instructions.  Results do not depend on which thread
+// builds which tracklet.
+__global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, int* __restrict__ workCounter,
+                                                      const int* __restrict__ starts,
                                                       const int* __restrict__ up, const RowGrid* __restrict__ grid,
                                                       int nRows, const int* __restrict__ cellStart,
                                                       const int2* __restrict__ syz, const GeomConst* __restrict__ G,
                                                       TrackletBufs tb) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nTl) return;
-  const float zunit = G->zunit, bzc = G->bzc;
-  const int h0 = starts[k];
-  const int R0 = find_row(grid, nRows, h0);
-  const int r0 = (R0 % kRowsPerTF) % kNRow;
-  const int Rs = R0 - r0;
-  int* H = tb.hits + (size_t)k * kMaxTlHits;
-  uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
-  const int zref = syz[h0].y, yref = syz[h0].x;
-  tb.zref[k] = zref;
-  int nc = 0;
-  for (int h = h0; h >= 0 && nc < kNRow - r0; h = up[h]) {
-    H[nc] = h;
-    Rw[nc] = (uint8_t)(r0 + nc);
-    ++nc;
-  }
-  const int2 a0 = syz[H[0]], a2 = syz[H[2]];
-  const float x0 = G->rowx[r0], x2 = G->rowx[r0 + 2];
-  const float dx = x2 - x0, dy = hit_y(a2.x, yref) - hit_y(a0.x, yref);
-  const float tphi = dy / dx;
-  const float s0 = tphi / sqrtf(1.f + tphi * tphi);
-  const float t0 = (hit_z(a2.y, zref, zunit) - hit_z(a0.y, zref, zunit)) / sqrtf(dx * dx + dy * dy);
   // the state after the last accepted hit lives in shared memory (one column
   // per thread) rather than in registers
   __shared__ float s_last[21][128];
@@ -147,11 +131,14 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, const int* __rest
 #pragma unroll
     for (int j = 0; j < 15; ++j) q.C[j] = s_last[6 + j][threadIdx.x];
   };
+  const float zunit = G->zunit, bzc = G->bzc;
+  // phases: 0 chain fit, 1 outward following, 2 inward refit, 3 inward
+  // following, 5 take the next tracklet
+  int phase = 5, k = 0, r0 = 0, Rs = 0, zref = 0, yref = 0;
+  int i = 0, r = 0, nc = 0, na = 0, nd = 0, misses = 0, top = 0, chainHit = -1;
+  int* H = nullptr;
+  uint8_t* Rw = nullptr;
   KState<float> st;
-  kf_reset<float>(st, x0, hit_y(a0.x, yref), hit_z(a0.y, zref, zunit), s0, t0, 0.f);
-  // phases: 0 chain fit, 1 outward following, 2 inward refit, 3 inward following
-  int phase = 0, i = 1, r = 0, na = nc, nd = 0, misses = 0, top = H[nc - 1];
-  bool dropped = false;
   // end of the outward following: restart at the top hit, fresh covariance
   auto begin_refit = [&]() {
     load_last(st);
@@ -162,19 +149,63 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, const int* __rest
     i = na - 2;
     phase = 2;
   };
+  auto finish = [&](bool dropped) {
+    if (dropped) {
+      tb.nhits[k] = 0;
+      tb.nasc[k] = 0;
+    } else {
+      tb.nhits[k] = na + nd;
+      tb.nasc[k] = na;
+      load_last(st);
+      store_state(tb.state + (size_t)k * 21, st, yref);
+    }
+    phase = 5;
+  };
   for (;;) {
+    if (phase == 5) {
+      k = atomicAdd(workCounter, 1);
+      if (k >= nTl) break;
+      const int h0 = starts[k];
+      const int R0 = find_row(grid, nRows, h0);
+      r0 = (R0 % kRowsPerTF) % kNRow;
+      Rs = R0 - r0;
+      H = tb.hits + (size_t)k * kMaxTlHits;
+      Rw = tb.rows + (size_t)k * kMaxTlHits;
+      const int2 a0 = syz[h0];
+      zref = a0.y;
+      yref = a0.x;
+      tb.zref[k] = zref;
+      const int h1 = up[h0];
+      const int2 a2 = syz[up[h1]];
+      const float x0 = G->rowx[r0], x2 = G->rowx[r0 + 2];
+      const float dx = x2 - x0, dy = hit_y(a2.x, yref) - hit_y(a0.x, yref);
+      const float tphi = dy / dx;
+      const float s0 = tphi / sqrtf(1.f + tphi * tphi);
+      const float t0 = (hit_z(a2.y, zref, zunit) - hit_z(a0.y, zref, zunit)) / sqrtf(dx * dx + dy * dy);
+      kf_reset<float>(st, x0, hit_y(a0.x, yref), hit_z(a0.y, zref, zunit), s0, t0, 0.f);
+      H[0] = h0;
+      Rw[0] = (uint8_t)r0;
+      nc = 1;
+      chainHit = h1;
+      nd = 0;
+      misses = 0;
+      phase = 0;
+      continue;
+    }
     int row, hit = -1;
     bool search = false;
     if (phase == 0) {
-      if (i >= nc) {
+      if (chainHit < 0 || nc >= kNRow - r0) {
+        na = nc;
+        top = H[nc - 1];
         save_last(st);
         r = r0 + nc;
         misses = 0;
         phase = 1;
         continue;
       }
-      row = r0 + i;
-      hit = H[i];
+      row = r0 + nc;
+      hit = chainHit;
     } else if (phase == 1) {
       if (r >= kNRow) {
         begin_refit();
@@ -193,7 +224,10 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, const int* __rest
       row = Rw[i];
       hit = H[i];
     } else {
-      if (r < 0) break;
+      if (r < 0) {
+        finish(false);
+        continue;
+      }
       row = r;
       search = true;
     }
@@ -203,24 +237,21 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, const int* __rest
       if (!stop) hit = search_row(grid[Rs + row], G->npads[row], cellStart, syz, st, yref, zref, zunit);
     }
     if (stop) {
-      if (phase == 0) {
-        dropped = true;
-        break;
-      }
-      if (phase == 2) {
-        --i;
-        continue;
-      }
-      if (phase == 1) {
-        begin_refit();
-        continue;
-      }
-      break;
+      if (phase == 0) finish(true);
+      else if (phase == 2) --i;
+      else if (phase == 1) begin_refit();
+      else finish(false);
+      continue;
     }
     if (hit >= 0) {
       const int2 p = syz[hit];
       kf_update<float>(st, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
-      if (phase == 1) {
+      if (phase == 0) {
+        H[nc] = hit;
+        Rw[nc] = (uint8_t)row;
+        ++nc;
+        chainHit = up[hit];
+      } else if (phase == 1) {
         H[na] = hit;
         Rw[na] = (uint8_t)row;
         ++na;
@@ -235,26 +266,14 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, const int* __rest
         misses = 0;
       }
     } else if (search && ++misses >= kMaxMiss) {
-      if (phase == 1) {
-        begin_refit();
-        continue;
-      }
-      break;
+      if (phase == 1) begin_refit();
+      else finish(false);
+      continue;
     }
-    if (phase == 0) ++i;
-    else if (phase == 1) ++r;
+    if (phase == 1) ++r;
     else if (phase == 2) --i;
-    else --r;
+    else if (phase == 3) --r;
   }
-  if (dropped) {
-    tb.nhits[k] = 0;
-    tb.nasc[k] = 0;
-    return;
-  }
-  tb.nhits[k] = na + nd;
-  tb.nasc[k] = na;
-  load_last(st);
-  store_state(tb.state + (size_t)k * 21, st, yref);
 }
 
 __device__ inline int tf_of(const int* __restrict__ begin, int nTF, int k) {
@@ -404,12 +423,21 @@ __global__ void __launch_bounds__(128) k_sector_fit(int nSt, TrackletBufs tb, co
 }
 
 // ------------------------------------------------------------- launchers
-void launch_tracklets(int nTl, const int* starts, const int* up, const RowGrid* grid, int nRows,
+void launch_tracklets(int nTl, int* workCounter, const int* starts, const int* up, const RowGrid* grid, int nRows,
                       const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st) {
-  if (nTl > 0) {
-    k_tracklets<<<(nTl + 127) / 128, 128, 0, st>>>(nTl, starts, up, grid, nRows, cellStart, syz, G, tb);
-    ++g_launch_count;
+  if (nTl <= 0) return;
+  static int sms = 0, perSm = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSm, k_tracklets, 128, 0);
+    if (perSm < 1) perSm = 1;
   }
+  const int blocks = std::min((nTl + 127) / 128, sms * perSm);
+  cudaMemsetAsync(workCounter, 0, sizeof(int), st);
+  k_tracklets<<<blocks, 128, 0, st>>>(nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb);
+  ++g_launch_count;
 }
 
 void launch_ownership(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, unsigned long long* w, cudaStream_t st) {

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -114,6 +115,8 @@ struct Ctx {
   int fatal = O2TPC_OK;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t evs[12] = {};
+  bool traceCopies = false;  // O2TPC_TRACE_COPIES=1: time every result copy (stderr); =2: the
+  int traceMode = 0;         // download phases without extra synchronisation
   // pinned staging for descriptors and results
   void* hStage = nullptr;
   size_t hStageBytes = 0;
@@ -362,7 +365,8 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   tb.rows = dalloc<uint8_t>(M, (size_t)nTl * kMaxTlHits);
   tb.state = dalloc<float>(M, (size_t)nTl * 21);
   tb.zref = dalloc<int>(M, nTl);
-  launch_tracklets(nTl, starts, up, grid, nRows, cellStart, syz, G, tb, st);
+  int* workCounter = dalloc<int>(M, 4);
+  launch_tracklets(nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st);
   CKL();
 
   // ---- A9: selection
@@ -508,9 +512,10 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   for (int i = 0; i < B; ++i) CK(cudaMemcpyAsync(&tfFirstRow[i], grid + (size_t)i * kRowsPerTF, sizeof(RowGrid),
                                                  cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(c->evs[10], st));
+  const double tSizes = now_ms();
   CK(cudaStreamSynchronize(st));
   auto r16 = [](size_t x) { return (x + 15) / 16 * 16; };
-  double hostAllocMs = 0.0;
+  const double tPrep = now_ms();
   for (int i = 0; i < B; ++i) {
     Job& J = *jobs[i];
     const int t0 = hTrkTf[i], t1 = hTrkTf[i + 1];
@@ -518,13 +523,32 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     const size_t ncl = (size_t)(hOff[t1] - hOff[t0]);
     const size_t bytes = r16(8 * (nt + 1)) + r16(4 * ncl) + 5 * r16(4 * nt) + r16(20 * nt) + r16(60 * nt) +
                          2 * r16(nt) + 64;
-    const double ta = now_ms();
     J.host = c->pinned_get(bytes, &J.hostBytes);
-    hostAllocMs += now_ms() - ta;
     char* q = static_cast<char*>(J.host);
     auto take = [&](const void* dsrc, size_t nb) -> char* {
       char* dst = q;
-      if (nb) CK(cudaMemcpyAsync(dst, dsrc, nb, cudaMemcpyDeviceToHost, st));
+      if (nb) {
+        if (c->traceCopies && c->traceMode == 1) {
+          cudaEvent_t a, b;
+          cudaEventCreate(&a);
+          cudaEventCreate(&b);
+          cudaEventRecord(a, st);
+          CK(cudaMemcpyAsync(dst, dsrc, nb, cudaMemcpyDeviceToHost, st));
+          cudaEventRecord(b, st);
+          cudaEventSynchronize(b);
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, a, b);
+          cudaPointerAttributes pa{}, pb{};
+          cudaPointerGetAttributes(&pa, dst);
+          cudaPointerGetAttributes(&pb, dsrc);
+          std::fprintf(stderr, "o2tpc copy %zu bytes %.3f ms %.1f GB/s dst type %d src type %d\n", nb, ms,
+                       nb / (ms * 1e6), (int)pa.type, (int)pb.type);
+          cudaEventDestroy(a);
+          cudaEventDestroy(b);
+        } else {
+          CK(cudaMemcpyAsync(dst, dsrc, nb, cudaMemcpyDeviceToHost, st));
+        }
+      }
       q += r16(nb);
       return dst;
     };
@@ -545,15 +569,23 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     R.flags = reinterpret_cast<const uint8_t*>(take(ob.flags + t0, nt));
     for (size_t k = 0; k <= nt; ++k) off64[k] = (uint64_t)(hOff[t0 + k] - hOff[t0]);
   }
+  const double hostPrepMs = now_ms() - tPrep;
   CK(cudaEventRecord(c->evs[11], st));
+  const double tWait = now_ms();
   CK(cudaStreamSynchronize(st));
+  if (c->traceCopies && c->traceMode == 2) {
+    float msCopy = 0.f;
+    cudaEventElapsedTime(&msCopy, c->evs[10], c->evs[11]);
+    std::fprintf(stderr, "o2tpc download: host prep %.3f ms, final wait %.3f ms, device %.3f ms, sizes sync at %.3f\n",
+                 hostPrepMs, now_ms() - tWait, msCopy, tPrep - tSizes);
+  }
   float devMs = 0.f;
   float stageMs[12] = {};
   for (int k = 0; k < 11; ++k) {
     stageMs[k] = 0.f;
     cudaEventElapsedTime(&stageMs[k], c->evs[k], c->evs[k + 1]);
   }
-  stageMs[11] = (float)hostAllocMs;
+  stageMs[11] = (float)hostPrepMs;
   const long long nLaunch = g_launch_count;
   cudaEventElapsedTime(&devMs, c->ev0, c->ev1);
   const bool inputBad = (*hErr & kErrInput) != 0;
@@ -706,6 +738,8 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
   auto* x = new (std::nothrow) Ctx();
   if (!x) return O2TPC_ENOMEM;
   x->cfg = c;
+  x->traceCopies = std::getenv("O2TPC_TRACE_COPIES") != nullptr;
+  x->traceMode = x->traceCopies ? std::atoi(std::getenv("O2TPC_TRACE_COPIES")) : 0;
   try {
     CK(cudaSetDevice(c.device));
     if (c.stream) {

@@ -241,18 +241,20 @@ __device__ inline int kf_prop(KState<T>& s, T x2, T bzc) {
   T c1 = kf_sqrt<T>((T(1) - s1) * (T(1) + s1));
   T c2 = kf_sqrt<T>((T(1) - s2) * (T(1) + s2));
   T cc = c1 + c2;
-  T dy = dx * (s1 + s2) / cc;
+  // reciprocals once, products after (the divisions dominate the cost)
+  const T icc = T(1) / cc, ic1 = T(1) / c1, ic2 = T(1) / c2;
+  T dy = dx * (s1 + s2) * icc;
   T chord = kf_sqrt<T>(dx * dx + dy * dy);
   T ak = fabs(k) * chord;
   T ds = (ak < T(1e-6)) ? chord : T(2) * kf_asin<T>(T(0.5) * ak) / fabs(k);
   if (dx < T(0)) ds = -ds;
   T sm = s1 + T(0.5) * k * dx;
   T cm = kf_sqrt<T>((T(1) - sm) * (T(1) + sm));
-  T f1 = dx * (s1 + s2) / (c1 * c2 * cc);
-  T fm = T(0.5) * dx * (sm + s2) / (cm * c2 * (cm + c2));
-  T ddsdk = (fabs(k * dx) < T(0.05)) ? dx * (f1 + T(4) * fm) / T(6) : (dx / c2 - ds) / k;
-  const T a02 = dx * (T(2) * cc + (s1 + s2) * (s1 / c1 + s2 / c2)) / (cc * cc);
-  const T a04 = dx * dx * bzc * (cc + (s1 + s2) * s2 / c2) / (cc * cc);
+  T f1 = dx * (s1 + s2) * ic1 * ic2 * icc;
+  T fm = T(0.5) * dx * (sm + s2) * ic2 / (cm * (cm + c2));
+  T ddsdk = (fabs(k * dx) < T(0.05)) ? dx * (f1 + T(4) * fm) * T(1.0 / 6.0) : (dx * ic2 - ds) / k;
+  const T a02 = dx * (T(2) * cc + (s1 + s2) * (s1 * ic1 + s2 * ic2)) * icc * icc;
+  const T a04 = dx * dx * bzc * (cc + (s1 + s2) * s2 * ic2) * icc * icc;
   const T a12 = tz * f1;
   const T a13 = ds;
   const T a14 = tz * bzc * ddsdk;
@@ -273,7 +275,8 @@ __device__ inline int kf_update(KState<T>& s, T ym, T zm, T* chi2) {
   T S00 = C[0] + T(kSigY) * T(kSigY), S01 = C[1], S11 = C[2] + T(kSigZ) * T(kSigZ);
   T det = S00 * S11 - S01 * S01;
   if (!(det > T(0))) return -1;
-  T I00 = S11 / det, I01 = -S01 / det, I11 = S00 / det;
+  const T idet = T(1) / det;
+  T I00 = S11 * idet, I01 = -S01 * idet, I11 = S00 * idet;
   if (chi2) *chi2 = r0 * r0 * I00 + T(2) * r0 * r1 * I01 + r1 * r1 * I11;
   T Cy[5], Cz[5], K0[5], K1[5];
 #pragma unroll

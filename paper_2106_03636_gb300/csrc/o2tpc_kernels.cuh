@@ -45,7 +45,7 @@ struct TrackletBufs {
   float* state;  // [nTl * 21]  x, par[5], cov[15] at the innermost hit
   int* zref;     // [nTl]
 };
-void launch_tracklets(int nTl, const int* starts, const int* up, const RowGrid* grid, int nRows,
+void launch_tracklets(int nTl, int* workCounter, const int* starts, const int* up, const RowGrid* grid, int nRows,
                       const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st);
 
 struct SectorTrackBufs {

@@ -85,7 +85,7 @@ class o2tpc_stats(ctypes.Structure):
     ]
 
 STAGES = ("ingest", "sort", "neighbours", "clean_starts", "tracklets", "selection", "sector_fit", "merge",
-          "refit", "sizes", "download", "host_alloc")
+          "refit", "sizes", "download", "host_prep")
 
 
 class o2tpc_result(ctypes.Structure):
