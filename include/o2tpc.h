@@ -89,13 +89,19 @@ typedef struct {
   int32_t device;          /* CUDA device ordinal                                     */
   uint64_t mem_budget;     /* device bytes the admitted TFs may use (0: 120 GB)       */
   int32_t max_inflight;    /* TFs queued or running at once (0: 64)                   */
-  int32_t max_batch;       /* TFs per batch (0: 64)                                   */
+  int32_t max_batch;       /* TFs per batch (0: 64); a batch also stops taking TFs
+                              once it holds 2^25 clusters or would exceed mem_budget */
   double bz_tesla;         /* solenoid field (0 allowed: straight lines)              */
   double vdrift_cm_us;     /* drift velocity (> 0)                                    */
   uint32_t flags;          /* O2TPC_FLAG_*                                            */
   /* Device memory: if dev_alloc is set, every device buffer comes from it
-   * (e.g. a framework's caching allocator) and goes back through dev_free;
-   * otherwise cudaMallocAsync/cudaFreeAsync on the context's stream. */
+   * (e.g. a framework's caching allocator) and goes back through dev_free,
+   * and host-resident inputs are copied in the batch's own stream.
+   * Otherwise buffers come from a stream-ordered memory pool the context
+   * owns (freed memory is kept for the next batch until o2tpc_destroy), and
+   * host-resident inputs still waiting in the queue are uploaded ahead on a
+   * second (copy) stream while earlier batches compute; these copies use up
+   * to mem_budget / 8 device bytes beyond mem_budget. */
   void* (*dev_alloc)(size_t bytes, void* user);
   void (*dev_free)(void* ptr, void* user);
   void* alloc_user;
@@ -136,8 +142,12 @@ typedef struct {
    * StartHitsFinder, 4 TrackletConstructor, 5 TrackletSelector, 6 sector-track
    * fits, 7 merger, 8 final refit, 9 read-back of the result sizes,
    * 10 result download; 11 is host time (not device) spent preparing the
-   * result copies (pinned blocks, offsets) inside step 10 */
-  float ms_stage[12];
+   * result copies (pinned blocks, offsets) inside step 10; 12 upload: from
+   * the batch start to the start of step 0 (host-resident inputs copied in
+   * the batch's own stream, descriptor tables); 13 time the batch waited for
+   * inputs that were uploaded ahead on the context's copy stream; 14-15 are
+   * reserved (zero) */
+  float ms_stage[16];
 } o2tpc_stats;
 
 /* Result of one TF; library-owned memory, valid until o2tpc_result_release. */

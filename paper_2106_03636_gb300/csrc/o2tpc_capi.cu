@@ -35,6 +35,9 @@ namespace {
 constexpr int kTileMin = 65536;           // clusters per ingest tile, at least
 constexpr int kTilesPerTFMax = 4096;
 constexpr uint64_t kMaxBatchHits = 2000000000ull;
+// A batch that already holds this many clusters fills the GPU: more TFs would
+// only add latency, so it stops taking them (they wait, uploaded ahead).
+constexpr uint64_t kBatchFullHits = 1ull << 25;
 
 struct CudaError {
   cudaError_t e;
@@ -96,7 +99,19 @@ struct Job {
   uint64_t emptyOffset = 0;
   std::shared_ptr<BatchMem> mem;  // kept stages
   int tfIndex = 0;
+  // upload ahead (host-resident input copied on the context's copy stream
+  // while earlier batches compute): 0 not started, 1 being issued, 2 issued,
+  // 3 left to the batch's own stream, 4 copy owned by the batch's memory
+  int upState = 0;
+  void* dIn = nullptr;
+  uint64_t dInBytes = 0;
+  cudaEvent_t upEv = nullptr;
 };
+
+// Device bytes of a host-resident TF's input copy.
+uint64_t input_bytes(const o2tpc_tf& t) {
+  return t.format == O2TPC_FMT_FIXED ? 12ull * t.n : 10ull * t.n + 64;
+}
 
 struct Ctx {
   o2tpc_config cfg{};
@@ -113,21 +128,29 @@ struct Ctx {
   int inflight = 0;
   bool stop = false;
   int fatal = O2TPC_OK;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evWait = nullptr;
   cudaEvent_t evs[12] = {};
+  // copy stream, its thread and the bytes uploaded ahead of their batch
+  cudaStream_t upStream = nullptr;
+  std::thread uploader;
+  std::condition_variable cvUp;
+  uint64_t upAheadBytes = 0, upAheadLimit = 0;
+  // the library's own stream-ordered pool (no user allocator)
+  cudaMemPool_t pool = nullptr;
   bool traceCopies = false;  // O2TPC_TRACE_COPIES=1: time every result copy (stderr); =2: the
   int traceMode = 0;         // download phases without extra synchronisation
   // pinned staging for descriptors and results
   void* hStage = nullptr;
   size_t hStageBytes = 0;
 
-  void* dev_alloc(size_t bytes) {
+  void* dev_alloc(size_t bytes) { return dev_alloc_on(bytes, stream); }
+  void* dev_alloc_on(size_t bytes, cudaStream_t s) {
     if (bytes == 0) bytes = 16;
     void* p = nullptr;
     if (cfg.dev_alloc) {
       p = cfg.dev_alloc(bytes, cfg.alloc_user);
     } else {
-      if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+      if (cudaMallocFromPoolAsync(&p, bytes, pool, s) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
       }
@@ -194,6 +217,34 @@ T* dalloc(BatchMem& m, size_t count) {
 
 uint64_t footprint_of(uint64_t n) { return 160ull * n + (64ull << 20); }
 
+// Device layout of a host-resident TF's copy: the packed records, or
+// sector[n] u8 | row[n] u8 | pad to 16 B | y[n] f32 | z[n] f32.
+void input_layout(const o2tpc_tf& t, void* p, TFDesc& d) {
+  if (t.format == O2TPC_FMT_FIXED) {
+    d.in0 = p;
+    return;
+  }
+  uint8_t* b = static_cast<uint8_t*>(p);
+  float* py = reinterpret_cast<float*>(b + ((2 * t.n + 15) / 16) * 16);
+  d.in0 = b;
+  d.in1 = b + t.n;
+  d.y = py;
+  d.z = py + t.n;
+}
+
+void input_upload(const o2tpc_tf& t, void* p, cudaStream_t s) {
+  TFDesc d{};
+  input_layout(t, p, d);
+  if (t.format == O2TPC_FMT_FIXED) {
+    CK(cudaMemcpyAsync(p, t.packed, 12 * t.n, cudaMemcpyHostToDevice, s));
+    return;
+  }
+  CK(cudaMemcpyAsync(const_cast<void*>(d.in0), t.sector, t.n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(const_cast<void*>(d.in1), t.row, t.n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(const_cast<float*>(d.y), t.y, 4 * t.n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(const_cast<float*>(d.z), t.z, 4 * t.n, cudaMemcpyHostToDevice, s));
+}
+
 int read_int(Ctx* c, const int* dptr) {
   int v = 0;
   CK(cudaMemcpyAsync(&v, dptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -235,6 +286,16 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   M.nRows = nRows;
   CK(cudaEventRecord(c->ev0, st));
   g_launch_count = 0;
+  // inputs uploaded ahead: the batch waits for their copies and owns their memory
+  for (auto& jp : jobs) {
+    if (jp->upState != 2) continue;
+    M.blocks.push_back({jp->dIn, (size_t)jp->dInBytes});
+    jp->upState = 4;  // the batch owns the copy now
+    CK(cudaStreamWaitEvent(st, jp->upEv, 0));
+    cudaEventDestroy(jp->upEv);
+    jp->upEv = nullptr;
+  }
+  CK(cudaEventRecord(c->evWait, st));
 
   // ---- inputs and TF table
   std::vector<TFDesc> tfd(B);
@@ -251,24 +312,12 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
       d.in1 = t.row;
       d.y = t.y;
       d.z = t.z;
-    } else if (t.format == O2TPC_FMT_FIXED) {
-      void* p = M.alloc(12 * t.n);
-      CK(cudaMemcpyAsync(p, t.packed, 12 * t.n, cudaMemcpyHostToDevice, st));
-      d.in0 = p;
+    } else if (jobs[i]->upState == 4) {
+      input_layout(t, jobs[i]->dIn, d);  // uploaded ahead on the copy stream
     } else {
-      uint8_t* p = dalloc<uint8_t>(M, 10 * t.n + 64);
-      uint8_t* ps = p;
-      uint8_t* pr = p + t.n;
-      float* py = reinterpret_cast<float*>(p + ((2 * t.n + 15) / 16) * 16);
-      float* pz = py + t.n;
-      CK(cudaMemcpyAsync(ps, t.sector, t.n, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(pr, t.row, t.n, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(py, t.y, 4 * t.n, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(pz, t.z, 4 * t.n, cudaMemcpyHostToDevice, st));
-      d.in0 = ps;
-      d.in1 = pr;
-      d.y = py;
-      d.z = pz;
+      void* p = M.alloc(input_bytes(t));
+      input_upload(t, p, st);
+      input_layout(t, p, d);
     }
     int tileSize = std::max(kTileMin, (int)((t.n + kTilesPerTFMax - 1) / kTilesPerTFMax));
     d.tileBase = (int)tiles.size();
@@ -580,12 +629,14 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
                  hostPrepMs, now_ms() - tWait, msCopy, tPrep - tSizes);
   }
   float devMs = 0.f;
-  float stageMs[12] = {};
+  float stageMs[16] = {};
   for (int k = 0; k < 11; ++k) {
     stageMs[k] = 0.f;
     cudaEventElapsedTime(&stageMs[k], c->evs[k], c->evs[k + 1]);
   }
   stageMs[11] = (float)hostPrepMs;
+  cudaEventElapsedTime(&stageMs[12], c->evWait, c->evs[0]);
+  cudaEventElapsedTime(&stageMs[13], c->ev0, c->evWait);
   const long long nLaunch = g_launch_count;
   cudaEventElapsedTime(&devMs, c->ev0, c->ev1);
   const bool inputBad = (*hErr & kErrInput) != 0;
@@ -617,7 +668,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     R.stats.ms_batch = (float)(tEnd - J.t_start);
     R.stats.ms_device = devMs;
     R.stats.n_launches = (uint64_t)nLaunch;
-    for (int k = 0; k < 12; ++k) R.stats.ms_stage[k] = stageMs[k];
+    for (int k = 0; k < 16; ++k) R.stats.ms_stage[k] = stageMs[k];
     J.status = inputBad ? O2TPC_EINVAL : O2TPC_OK;
     R.status = J.status;
     J.tfIndex = i;
@@ -641,6 +692,74 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   // without kept stages the batch memory is freed here (stream-ordered)
 }
 
+// Frees an upload made ahead that no batch took over (failed batch, destroy).
+void release_upload(Ctx* c, Job& j) {
+  if (j.upState != 2) return;
+  if (j.upEv) {
+    cudaEventSynchronize(j.upEv);
+    cudaEventDestroy(j.upEv);
+    j.upEv = nullptr;
+  }
+  c->dev_free(j.dIn);
+  j.dIn = nullptr;
+  j.upState = 3;
+}
+
+// Copy thread: uploads host-resident TFs that wait in the queue on the copy
+// stream, so that their H2D transfer overlaps the batch computing before
+// them (within upAheadLimit bytes of device memory).  Only with the
+// library's own memory pool: a user allocator hands out memory that is
+// ordered on the compute stream alone.
+void uploader_main(Ctx* c) {
+  cudaSetDevice(c->cfg.device);
+  for (;;) {
+    std::shared_ptr<Job> j;
+    {
+      std::unique_lock<std::mutex> lk(c->mu);
+      c->cvUp.wait(lk, [&] {
+        if (c->stop) return true;
+        for (auto& q : c->queue) {
+          if (q->upState != 0 || q->tf.location != O2TPC_LOC_HOST || q->tf.n == 0) continue;
+          if (c->upAheadBytes + input_bytes(q->tf) > c->upAheadLimit) return false;  // keep queue order
+          j = q;
+          return true;
+        }
+        return false;
+      });
+      if (c->stop) return;
+      j->upState = 1;
+      j->dInBytes = input_bytes(j->tf);
+      c->upAheadBytes += j->dInBytes;
+    }
+    bool ok = true;
+    try {
+      j->dIn = c->dev_alloc_on(j->dInBytes, c->upStream);
+      input_upload(j->tf, j->dIn, c->upStream);
+      CK(cudaEventCreateWithFlags(&j->upEv, cudaEventDisableTiming));
+      CK(cudaEventRecord(j->upEv, c->upStream));
+    } catch (...) {
+      ok = false;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      // memory not given back here stays with the copy stream until it drains
+      if (j->upEv) cudaEventDestroy(j->upEv);
+      j->upEv = nullptr;
+      if (j->dIn) {
+        cudaStreamSynchronize(c->upStream);
+        c->dev_free(j->dIn);
+        j->dIn = nullptr;
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(c->mu);
+      j->upState = ok ? 2 : 3;
+      if (!ok) c->upAheadBytes -= j->dInBytes;
+    }
+    c->cvUp.notify_all();
+  }
+}
+
 void worker_main(Ctx* c) {
   cudaSetDevice(c->cfg.device);
   for (;;) {
@@ -653,13 +772,27 @@ void worker_main(Ctx* c) {
       const int maxB = (c->cfg.flags & O2TPC_FLAG_NO_BATCHING) ? 1 : c->cfg.max_batch;
       while (!c->queue.empty() && (int)batch.size() < maxB) {
         auto& j = c->queue.front();
-        if (!batch.empty() && (fp + j->footprint > c->cfg.mem_budget || hits + j->tf.n > kMaxBatchHits)) break;
+        if (!batch.empty() && (fp + j->footprint > c->cfg.mem_budget || hits + j->tf.n > kMaxBatchHits ||
+                               hits >= kBatchFullHits))
+          break;
         fp += j->footprint;
         hits += j->tf.n;
         batch.push_back(j);
         c->queue.pop_front();
       }
+      // a TF whose upload the copy thread is issuing right now is waited for;
+      // the rest are left to the batch's stream
+      c->cvUp.wait(lk, [&] {
+        for (auto& j : batch)
+          if (j->upState == 1) return false;
+        return true;
+      });
+      for (auto& j : batch) {
+        if (j->upState == 2) c->upAheadBytes -= j->dInBytes;
+        else if (j->upState == 0) j->upState = 3;
+      }
     }
+    c->cvUp.notify_all();
     const double t0 = now_ms();
     for (auto& j : batch) j->t_start = t0;
     int status = O2TPC_OK;
@@ -679,6 +812,7 @@ void worker_main(Ctx* c) {
         status = O2TPC_ENOMEM;
       }
     }
+    for (auto& j : batch) release_upload(c, *j);
     {
       std::lock_guard<std::mutex> lk(c->mu);
       for (auto& j : batch) {
@@ -750,6 +884,23 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
     }
     CK(cudaEventCreate(&x->ev0));
     CK(cudaEventCreate(&x->ev1));
+    CK(cudaEventCreate(&x->evWait));
+    CK(cudaStreamCreateWithFlags(&x->upStream, cudaStreamNonBlocking));
+    if (!c.dev_alloc) {
+      cudaMemPoolProps props{};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = c.device;
+      CK(cudaMemPoolCreate(&x->pool, &props));
+      // keep freed memory for the next batch; never make the copy stream wait
+      // for the compute stream to reuse a block
+      uint64_t keepAll = ~0ull;
+      int noInternalDeps = 0;
+      CK(cudaMemPoolSetAttribute(x->pool, cudaMemPoolAttrReleaseThreshold, &keepAll));
+      CK(cudaMemPoolSetAttribute(x->pool, cudaMemPoolReuseAllowInternalDependencies, &noInternalDeps));
+      x->upAheadLimit = c.mem_budget / 8;
+    }
     for (auto& e : x->evs) CK(cudaEventCreate(&e));
     fill_geom(x->hGeom, c.bz_tesla, c.vdrift_cm_us);
     x->dGeom = static_cast<GeomConst*>(x->dev_alloc(sizeof(GeomConst)));
@@ -764,6 +915,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
     return O2TPC_ENOMEM;
   }
   x->worker = std::thread(worker_main, x);
+  if (x->pool) x->uploader = std::thread(uploader_main, x);
   *out = reinterpret_cast<o2tpc_ctx*>(x);
   return O2TPC_OK;
 }
@@ -794,6 +946,7 @@ int o2tpc_submit_tf(o2tpc_ctx* ctx, const o2tpc_tf* tf, uint64_t* ticket) {
     ++c->inflight;
   }
   c->cvWork.notify_one();
+  c->cvUp.notify_all();
   *ticket = j->ticket;
   return O2TPC_OK;
 }
@@ -846,12 +999,15 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
     c->stop = true;
   }
   c->cvWork.notify_all();
+  c->cvUp.notify_all();
   if (c->worker.joinable()) c->worker.join();
+  if (c->uploader.joinable()) c->uploader.join();
   int rc = c->fatal;
   cudaSetDevice(c->cfg.device);
   {
     std::lock_guard<std::mutex> lk(c->mu);
     for (auto& kv : c->jobs) {
+      release_upload(c, *kv.second);
       kv.second->mem.reset();
       if (kv.second->host) cudaFreeHost(kv.second->host);
     }
@@ -866,7 +1022,13 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
     if (e) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->evWait) cudaEventDestroy(c->evWait);
+  if (c->upStream) {
+    cudaStreamSynchronize(c->upStream);
+    cudaStreamDestroy(c->upStream);
+  }
   if (c->ownStream) cudaStreamDestroy(c->stream);
+  if (c->pool) cudaMemPoolDestroy(c->pool);
   delete c;
   return rc;
 }

@@ -81,11 +81,11 @@ class o2tpc_stats(ctypes.Structure):
         ("ms_batch", ctypes.c_float),
         ("ms_device", ctypes.c_float),
         ("n_launches", ctypes.c_uint64),
-        ("ms_stage", ctypes.c_float * 12),
+        ("ms_stage", ctypes.c_float * 16),
     ]
 
 STAGES = ("ingest", "sort", "neighbours", "clean_starts", "tracklets", "selection", "sector_fit", "merge",
-          "refit", "sizes", "download", "host_prep")
+          "refit", "sizes", "download", "host_prep", "upload", "upload_wait", "reserved14", "reserved15")
 
 
 class o2tpc_result(ctypes.Structure):
@@ -246,10 +246,12 @@ def make_tf(tf, location: int = O2TPC_LOC_HOST, arrays: dict | None = None, user
 
 
 class Tracker:
-    """One context on one GPU.
+    """One context on one GPU, running on its own ``torch.cuda.Stream``.
 
     ``torch_memory``: allocate the library's device buffers from PyTorch's
-    caching allocator on the tracker's own ``torch.cuda.Stream``."""
+    caching allocator (host-resident inputs are then copied in the batch's
+    stream); otherwise the library's own memory pool and copy stream serve
+    them and uploads of queued TFs overlap earlier batches."""
 
     def __init__(self, device: int = 0, bz: float = 0.5, vdrift: float = 2.58, flags: int = 0,
                  mem_budget: int = 0, max_inflight: int = 0, max_batch: int = 0, torch_memory: bool = False):
@@ -262,10 +264,12 @@ class Tracker:
         self.cfg.max_inflight = max_inflight
         self.cfg.max_batch = max_batch
         self._keep = []
-        if torch_memory:
-            import torch
+        import torch
 
-            self.stream = torch.cuda.Stream(device=device)
+        # the context runs on this stream (CUDA events for timing go on it)
+        self.stream = torch.cuda.Stream(device=device)
+        self.cfg.stream = self.stream.cuda_stream
+        if torch_memory:
             dev = device
             st = self.stream
 
@@ -280,7 +284,6 @@ class Tracker:
 
             self._keep = [ALLOC_FN(_alloc), FREE_FN(_free)]
             self.cfg.dev_alloc, self.cfg.dev_free = self._keep
-            self.cfg.stream = self.stream.cuda_stream
         rc, self.ctx = o2tpc_create(self.cfg)
         if rc != O2TPC_OK:
             raise O2TPCError(rc, "o2tpc_create")

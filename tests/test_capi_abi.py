@@ -36,4 +36,4 @@ def test_strerror_without_gpu():
 def test_binding_structures_match_header_sizes():
     # 64-bit layout of the C structs as the header defines them
     assert ctypes.sizeof(o2tpc.o2tpc_tf) == 8 + 4 + 4 + 5 * 8 + 8
-    assert ctypes.sizeof(o2tpc.o2tpc_stats) == 5 * 8 + 4 * 4 + 8 + 12 * 4
+    assert ctypes.sizeof(o2tpc.o2tpc_stats) == 5 * 8 + 4 * 4 + 8 + 16 * 4

@@ -143,3 +143,24 @@ def test_torch_allocator_and_stream():
     o = oracle.run(tf)
     compare_tracks(r, o, ZUNIT)
     assert torch.cuda.memory_allocated() >= 0
+
+
+def test_uploads_ahead_equal_in_stream_uploads():
+    """Host-resident TFs queued behind a running batch are copied ahead on
+    the copy stream; their results equal those of the in-stream copy path
+    (the caching-allocator context copies in the batch's stream)."""
+    pytest.importorskip("torch")
+    tfs = [synth.single_sector(seed=s) for s in (4, 5)] + \
+          [synth.full_tpc_1ms(seed=6 + k, n_coll=1, ntracks=800, fmt=synth.FMT_FIXED) for k in range(3)] + \
+          [synth.single_sector(seed=9)]
+    with o2tpc.Tracker(torch_memory=True, flags=o2tpc.O2TPC_FLAG_NO_BATCHING) as a:
+        ref = [a.track(tf) for tf in tfs]
+    with o2tpc.Tracker(max_batch=1) as b:
+        tickets = [b.submit(tf) for tf in tfs]
+        got = [b.poll(t) for t in tickets]
+    for x, y in zip(ref, got):
+        assert y["status"] == 0
+        st = y["stats"]["ms_stage"]
+        assert np.isfinite(st[12]) and np.isfinite(st[13]) and st[12] >= 0 and st[13] >= 0
+        for k in ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref"):
+            assert np.array_equal(x[k], y[k]), k
