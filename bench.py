@@ -166,13 +166,207 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def device_max(ms, world, local):
+    """Max over ranks of a duration (replicas; the only collective)."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], device=f"cuda:{local}")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def run_chunks(args, rank, world, local):
+    """Uneven sub-Time-Frame chunks (64 chunks, Poisson(20) collisions each, a
+    quarter pp-like): plain = one chunk per launch sequence, synchronised per
+    chunk; batched = all chunks in one batch (one launch sequence)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2106_03636_gb300 import o2tpc, synth
+
+    chunks = synth.chunk_mix(seed=20210610 + 1000 * rank)
+    n = sum(c.n for c in chunks)
+    dev = [{"packed": torch.from_numpy(c.packed).to(f"cuda:{local}")} for c in chunks]
+    torch.cuda.synchronize()
+    plain = o2tpc.Tracker(device=local, flags=o2tpc.O2TPC_FLAG_NO_BATCHING)
+    batched = o2tpc.Tracker(device=local, max_batch=len(chunks), batch_full_clusters=2**64 - 1)
+
+    def pass_plain(loc=o2tpc.O2TPC_LOC_DEVICE, arrays=dev):
+        out = []
+        for c, a in zip(chunks, arrays):
+            out.append(plain.wait(plain.submit(c, location=loc, arrays=a)))
+        return out
+
+    def pass_batched(loc=o2tpc.O2TPC_LOC_DEVICE, arrays=dev):
+        tk = batched.submit_many(chunks, location=loc, arrays=arrays)
+        return [batched.wait(t) for t in tk]
+
+    def timed(fn, trk, *a):
+        for _ in range(args.warmup):
+            fn(*a)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stage = np.zeros(16)
+        launches, sizes = 0, set()
+        e0.record(trk.stream)
+        for _ in range(args.steps):
+            rs = fn(*a)
+            for r in rs:
+                if r["status"] != 0:
+                    raise RuntimeError(o2tpc.o2tpc_strerror(r["status"]))
+            seen = {}
+            for r in rs:  # stages and launches once per batch
+                key = (r["stats"]["ms_device"], r["stats"]["batch_size"])
+                if key not in seen:
+                    seen[key] = r
+            for r in seen.values():
+                stage += np.asarray(r["stats"]["ms_stage"])
+                launches += int(r["stats"]["n_launches"])
+                sizes.add(int(r["stats"]["batch_size"]))
+        e1.record(trk.stream)
+        torch.cuda.synchronize()
+        ms = device_max(e0.elapsed_time(e1), world, local)
+        return ms / args.steps, stage / args.steps, launches // args.steps, sorted(sizes), rs
+
+    with ClockSampler(local) as clk:
+        ms_p, stage_p, l_p, _, _ = timed(pass_plain, plain)
+        ms_b, stage_b, l_b, sizes_b, rs = timed(pass_batched, batched)
+    e2e = None
+    if not args.no_e2e:
+        pin = [{"packed": torch.from_numpy(c.packed).pin_memory()} for c in chunks]
+        ms_e, _, _, _, _ = timed(pass_batched, batched, o2tpc.O2TPC_LOC_HOST, pin)
+        nt = sum(r["n_tracks"] for r in rs)
+        ncl = sum(r["n_cluster_refs"] for r in rs)
+        e2e = {"value": world * n / (ms_e / 1e3), "unit": "clusters/s", "h2d_bytes_per_step": 12 * n,
+               "d2h_bytes_per_step": 8 * (nt + len(chunks)) + 4 * ncl + nt * 106, "ms_per_step": ms_e,
+               "mode": "batched from pinned host memory"}
+    peak, peak_kind = peaks()
+    names = o2tpc.STAGES
+    k = int(np.argmax(stage_b[:11]))
+    achieved = STAGE_BYTES[names[k]] * n / (stage_b[k] / 1e3) / 1e9
+    line = {"metric": METRIC, "value": world * n / (ms_b / 1e3), "unit": "clusters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "chunks_64x36sectors_poisson20", "chunks": len(chunks), "clusters": int(n),
+                       "chunk_clusters_min": int(min(c.n for c in chunks)),
+                       "chunk_clusters_max": int(max(c.n for c in chunks)), "format": "fixed12",
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+            "batched": {"value": world * n / (ms_b / 1e3), "ms_per_step": ms_b, "batch_sizes": sizes_b,
+                        "gpu_launches": l_b},
+            "plain": {"value": world * n / (ms_p / 1e3), "ms_per_step": ms_p, "gpu_launches": l_p,
+                      "stage_ms": {names[i]: round(float(stage_p[i]), 3) for i in range(14)}},
+            "speedup_batched_vs_plain": ms_p / ms_b,
+            "stage_ms": {names[i]: round(float(stage_b[i]), 3) for i in range(14)},
+            "roofline": {"bound": "hbm", "kernel": names[k], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind},
+            "path_roofline": {"bytes_per_cluster": PATH_BYTES, "peak": peak,
+                              "frac": n / (ms_b / 1e3) * PATH_BYTES / 1e9 / peak},
+            "cpu_baseline": None, "e2e": e2e, "gpu_launches": l_b, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plain.close()
+    batched.close()
+
+
+def run_serving(args, rank, world, local):
+    """Served stream: Time Frames drawn from a pool of 24 (half Pb-Pb with
+    10..570 collisions, half pp-like ~3 M clusters) arrive as a Poisson
+    process from pinned host memory; at most --max-queue are admitted at
+    once (an arrival that finds the server full is dropped and counted).
+    Latency = arrival -> result polled on the host."""
+    import torch
+
+    from paper_2106_03636_gb300 import o2tpc, synth
+
+    pool = synth.serving_pool(seed=20210611 + 1000 * rank)
+    pin = [{"packed": torch.from_numpy(t.packed).pin_memory()} for t in pool]
+    trk = o2tpc.Tracker(device=local, max_inflight=args.max_queue)
+    for i in range(min(len(pool), max(args.warmup, 3))):  # warm the pools (device memory, pinned results)
+        trk.wait(trk.submit(pool[i], location=o2tpc.O2TPC_LOC_HOST, arrays=pin[i]))
+    rng = np.random.default_rng(20210611 + rank)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate_hz, int(args.rate_hz * args.serve_seconds * 2) + 10))
+    arrivals = arrivals[arrivals < args.serve_seconds]
+    picks = rng.integers(0, len(pool), len(arrivals))
+
+    done = collections.deque()
+    pending = collections.deque()
+    cv = threading.Condition()
+    state = {"closed": False}
+
+    def poller():
+        while True:
+            with cv:
+                cv.wait_for(lambda: pending or state["closed"])
+                if not pending:
+                    return
+                tk, t_arr, i = pending.popleft()
+            r = trk.wait(tk)
+            done.append((t_arr, time.perf_counter(), i, r["status"], r["stats"]["batch_size"]))
+
+    th = threading.Thread(target=poller, daemon=True)
+    dropped = 0
+    with ClockSampler(local) as clk:
+        th.start()
+        t0 = time.perf_counter()
+        for t_a, i in zip(arrivals, picks):
+            now = time.perf_counter() - t0
+            if t_a > now:
+                time.sleep(t_a - now)
+            t_arr = t0 + t_a
+            try:
+                tk = trk.submit(pool[i], location=o2tpc.O2TPC_LOC_HOST, arrays=pin[i])
+            except o2tpc.O2TPCError as e:
+                if e.status != o2tpc.O2TPC_EAGAIN:
+                    raise
+                dropped += 1
+                continue
+            with cv:
+                pending.append((tk, t_arr, i))
+                cv.notify()
+        with cv:
+            state["closed"] = True
+            cv.notify()
+        th.join()
+    lat = np.array([1e3 * (b - a) for a, b, _, _, _ in done])
+    bad = sum(1 for d in done if d[3] != 0)
+    if bad:
+        raise RuntimeError(f"{bad} TFs failed")
+    ncl = sum(pool[d[2]].n for d in done)
+    t_end = max(d[1] for d in done)
+    wall = t_end - t0
+    sizes = np.array([d[4] for d in done])
+    line = {"metric": METRIC, "value": ncl / wall, "unit": "clusters/s", "n_gpus": world, "steps": len(done),
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, len(done)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving_pool24_poisson", "rate_hz": args.rate_hz,
+                       "arrival_window_s": args.serve_seconds, "max_queue": args.max_queue,
+                       "pool_clusters": [int(t.n) for t in pool], "format": "fixed12",
+                       "input": "pinned host memory", "parallelism": f"replicas x{world}"},
+            "offered": int(len(arrivals)), "served": int(len(done)), "dropped": int(dropped),
+            "tf_per_s": len(done) / wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_batch": float(sizes.mean()),
+            "wall_s": wall, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    trk.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="full_tf", choices=["full_tf", "full_tpc_1ms"])
+    ap.add_argument("--workload", default="full_tf", choices=["full_tf", "full_tpc_1ms", "chunks", "serving"])
+    ap.add_argument("--rate-hz", type=float, default=50.0, help="serving: Poisson arrival rate of TFs")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: arrival window")
+    ap.add_argument("--max-queue", type=int, default=16, help="serving: TFs admitted at once (more are dropped)")
     ap.add_argument("--seed", type=int, default=20210609)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -199,6 +393,11 @@ def main():
 
     torch.cuda.set_device(local)
     from paper_2106_03636_gb300 import o2tpc
+
+    if args.workload == "chunks":
+        return run_chunks(args, rank, world, local)
+    if args.workload == "serving":
+        return run_serving(args, rank, world, local)
 
     tf, cfg = make_workload(args.workload, args.seed + 1000 * rank)
     n = tf.n

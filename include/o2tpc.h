@@ -90,7 +90,8 @@ typedef struct {
   uint64_t mem_budget;     /* device bytes the admitted TFs may use (0: 120 GB)       */
   int32_t max_inflight;    /* TFs queued or running at once (0: 64)                   */
   int32_t max_batch;       /* TFs per batch (0: 64); a batch also stops taking TFs
-                              once it holds 2^25 clusters or would exceed mem_budget */
+                              once it holds batch_full_clusters clusters or would
+                              exceed mem_budget                                      */
   double bz_tesla;         /* solenoid field (0 allowed: straight lines)              */
   double vdrift_cm_us;     /* drift velocity (> 0)                                    */
   uint32_t flags;          /* O2TPC_FLAG_*                                            */
@@ -106,6 +107,9 @@ typedef struct {
   void (*dev_free)(void* ptr, void* user);
   void* alloc_user;
   void* stream;            /* cudaStream_t to run on, or NULL for a library stream    */
+  uint64_t batch_full_clusters; /* clusters that fill the GPU: a batch holding this
+                              many takes no further TF (0: 2^25; UINT64_MAX: only
+                              max_batch and mem_budget limit a batch)                 */
 } o2tpc_config;
 
 typedef struct {
@@ -184,6 +188,14 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out);
  * O2TPC_ENOMEM.  Invalid cluster content is detected on the device and
  * reported by o2tpc_poll as the TF's status O2TPC_EINVAL. */
 int o2tpc_submit_tf(o2tpc_ctx* ctx, const o2tpc_tf* tf, uint64_t* ticket);
+
+/* Queues n TFs at once (tfs[0..n-1], tickets[0..n-1] set on success): the
+ * worker sees all of them together, so they go into one batch as far as
+ * max_batch, batch_full_clusters and mem_budget allow (e.g. the chunks of one
+ * Time Frame processed in a single launch sequence).  All or nothing: on any
+ * error no TF is queued.  Same returns and borrowing rules as
+ * o2tpc_submit_tf; O2TPC_EAGAIN if the n TFs do not fit in max_inflight. */
+int o2tpc_submit_many(o2tpc_ctx* ctx, const o2tpc_tf* tfs, uint32_t n, uint64_t* tickets);
 
 /* Waits up to timeout_ms (< 0: forever, 0: just test) for a TF.  On
  * O2TPC_OK, *out is the result (its own status may still be an error).

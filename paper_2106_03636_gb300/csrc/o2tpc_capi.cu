@@ -35,8 +35,9 @@ namespace {
 constexpr int kTileMin = 65536;           // clusters per ingest tile, at least
 constexpr int kTilesPerTFMax = 4096;
 constexpr uint64_t kMaxBatchHits = 2000000000ull;
-// A batch that already holds this many clusters fills the GPU: more TFs would
-// only add latency, so it stops taking them (they wait, uploaded ahead).
+// Default for o2tpc_config::batch_full_clusters: a batch that already holds
+// this many clusters fills the GPU, more TFs would only add latency, so it
+// stops taking them (they wait, uploaded ahead).
 constexpr uint64_t kBatchFullHits = 1ull << 25;
 
 struct CudaError {
@@ -773,7 +774,7 @@ void worker_main(Ctx* c) {
       while (!c->queue.empty() && (int)batch.size() < maxB) {
         auto& j = c->queue.front();
         if (!batch.empty() && (fp + j->footprint > c->cfg.mem_budget || hits + j->tf.n > kMaxBatchHits ||
-                               hits >= kBatchFullHits))
+                               hits >= c->cfg.batch_full_clusters))
           break;
         fp += j->footprint;
         hits += j->tf.n;
@@ -862,6 +863,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
   if (c.mem_budget == 0) c.mem_budget = 120ull << 30;
   if (c.max_inflight <= 0) c.max_inflight = 64;
   if (c.max_batch <= 0) c.max_batch = 64;
+  if (c.batch_full_clusters == 0) c.batch_full_clusters = kBatchFullHits;
   if (!(c.vdrift_cm_us > 0.0) || !std::isfinite(c.bz_tesla)) return O2TPC_EINVAL;
   if ((c.dev_alloc == nullptr) != (c.dev_free == nullptr)) return O2TPC_EINVAL;
   int ndev = 0;
@@ -920,9 +922,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
   return O2TPC_OK;
 }
 
-int o2tpc_submit_tf(o2tpc_ctx* ctx, const o2tpc_tf* tf, uint64_t* ticket) {
-  Ctx* c = reinterpret_cast<Ctx*>(ctx);
-  if (!c || !tf || !ticket) return O2TPC_EINVAL;
+static int check_tf(const Ctx* c, const o2tpc_tf* tf) {
   if (tf->format != O2TPC_FMT_FLOAT && tf->format != O2TPC_FMT_FIXED) return O2TPC_EINVAL;
   if (tf->location != O2TPC_LOC_HOST && tf->location != O2TPC_LOC_DEVICE) return O2TPC_EINVAL;
   if (tf->n > 0) {
@@ -930,25 +930,43 @@ int o2tpc_submit_tf(o2tpc_ctx* ctx, const o2tpc_tf* tf, uint64_t* ticket) {
     if (tf->format == O2TPC_FMT_FLOAT && (!tf->sector || !tf->row || !tf->y || !tf->z)) return O2TPC_EINVAL;
   }
   if (tf->n >= kMaxBatchHits) return O2TPC_ETOOBIG;
-  const uint64_t fp = footprint_of(tf->n);
-  if (fp > c->cfg.mem_budget) return O2TPC_ETOOBIG;
-  auto j = std::make_shared<Job>();
-  j->tf = *tf;
-  j->footprint = fp;
-  j->t_submit = now_ms();
+  if (footprint_of(tf->n) > c->cfg.mem_budget) return O2TPC_ETOOBIG;
+  return O2TPC_OK;
+}
+
+int o2tpc_submit_many(o2tpc_ctx* ctx, const o2tpc_tf* tfs, uint32_t n, uint64_t* tickets) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || (n > 0 && (!tfs || !tickets))) return O2TPC_EINVAL;
+  std::vector<std::shared_ptr<Job>> js(n);
+  const double t = now_ms();
+  for (uint32_t i = 0; i < n; ++i) {
+    int rc = check_tf(c, &tfs[i]);
+    if (rc != O2TPC_OK) return rc;
+    js[i] = std::make_shared<Job>();
+    js[i]->tf = tfs[i];
+    js[i]->footprint = footprint_of(tfs[i].n);
+    js[i]->t_submit = t;
+  }
   {
     std::lock_guard<std::mutex> lk(c->mu);
     if (c->fatal != O2TPC_OK) return c->fatal;
-    if (c->inflight >= c->cfg.max_inflight) return O2TPC_EAGAIN;
-    j->ticket = c->nextTicket++;
-    c->jobs[j->ticket] = j;
-    c->queue.push_back(j);
-    ++c->inflight;
+    if ((uint64_t)c->inflight + n > (uint64_t)c->cfg.max_inflight) return O2TPC_EAGAIN;
+    for (uint32_t i = 0; i < n; ++i) {
+      js[i]->ticket = c->nextTicket++;
+      c->jobs[js[i]->ticket] = js[i];
+      c->queue.push_back(js[i]);
+      ++c->inflight;
+      tickets[i] = js[i]->ticket;
+    }
   }
   c->cvWork.notify_one();
   c->cvUp.notify_all();
-  *ticket = j->ticket;
   return O2TPC_OK;
+}
+
+int o2tpc_submit_tf(o2tpc_ctx* ctx, const o2tpc_tf* tf, uint64_t* ticket) {
+  if (!ctx || !tf || !ticket) return O2TPC_EINVAL;
+  return o2tpc_submit_many(ctx, tf, 1, ticket);
 }
 
 int o2tpc_poll(o2tpc_ctx* ctx, uint64_t ticket, int32_t timeout_ms, const o2tpc_result** out) {

@@ -52,6 +52,7 @@ class o2tpc_config(ctypes.Structure):
         ("dev_free", FREE_FN),
         ("alloc_user", ctypes.c_void_p),
         ("stream", ctypes.c_void_p),
+        ("batch_full_clusters", ctypes.c_uint64),
     ]
 
 
@@ -130,6 +131,9 @@ def load(build: bool = True) -> ctypes.CDLL:
         lib.o2tpc_create.argtypes = [ctypes.POINTER(o2tpc_config), ctypes.POINTER(vp)]
         lib.o2tpc_submit_tf.restype = ctypes.c_int
         lib.o2tpc_submit_tf.argtypes = [vp, ctypes.POINTER(o2tpc_tf), ctypes.POINTER(ctypes.c_uint64)]
+        lib.o2tpc_submit_many.restype = ctypes.c_int
+        lib.o2tpc_submit_many.argtypes = [vp, ctypes.POINTER(o2tpc_tf), ctypes.c_uint32,
+                                          ctypes.POINTER(ctypes.c_uint64)]
         lib.o2tpc_poll.restype = ctypes.c_int
         lib.o2tpc_poll.argtypes = [vp, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.POINTER(o2tpc_result))]
         lib.o2tpc_result_release.restype = None
@@ -159,6 +163,13 @@ def o2tpc_submit_tf(ctx, tf: o2tpc_tf):
     t = ctypes.c_uint64()
     rc = load().o2tpc_submit_tf(ctx, ctypes.byref(tf), ctypes.byref(t))
     return rc, t.value
+
+
+def o2tpc_submit_many(ctx, tfs: list):
+    arr = (o2tpc_tf * len(tfs))(*tfs)
+    t = (ctypes.c_uint64 * len(tfs))()
+    rc = load().o2tpc_submit_many(ctx, arr, len(tfs), t)
+    return rc, list(t)
 
 
 def o2tpc_poll(ctx, ticket: int, timeout_ms: int):
@@ -254,7 +265,8 @@ class Tracker:
     them and uploads of queued TFs overlap earlier batches."""
 
     def __init__(self, device: int = 0, bz: float = 0.5, vdrift: float = 2.58, flags: int = 0,
-                 mem_budget: int = 0, max_inflight: int = 0, max_batch: int = 0, torch_memory: bool = False):
+                 mem_budget: int = 0, max_inflight: int = 0, max_batch: int = 0, torch_memory: bool = False,
+                 batch_full_clusters: int = 0):
         self.cfg = o2tpc_config()
         self.cfg.device = device
         self.cfg.bz_tesla = bz
@@ -263,6 +275,7 @@ class Tracker:
         self.cfg.mem_budget = mem_budget
         self.cfg.max_inflight = max_inflight
         self.cfg.max_batch = max_batch
+        self.cfg.batch_full_clusters = batch_full_clusters
         self._keep = []
         import torch
 
@@ -296,6 +309,18 @@ class Tracker:
             raise O2TPCError(rc, "o2tpc_submit_tf")
         self._pending[ticket] = (tf, arrays)  # inputs are borrowed until polled
         return ticket
+
+    def submit_many(self, tfs, location: int = O2TPC_LOC_HOST, arrays: list | None = None) -> list[int]:
+        """Queues all ``tfs`` at once (they share a batch as far as the limits
+        allow); ``arrays``: one dict per TF for device or pinned inputs."""
+        arrays = arrays if arrays is not None else [None] * len(tfs)
+        ts = [make_tf(tf, location, a) for tf, a in zip(tfs, arrays)]
+        rc, tickets = o2tpc_submit_many(self.ctx, ts)
+        if rc != O2TPC_OK:
+            raise O2TPCError(rc, "o2tpc_submit_many")
+        for tk, tf, a in zip(tickets, tfs, arrays):
+            self._pending[tk] = (tf, a)
+        return tickets
 
     def poll(self, ticket: int, timeout_ms: int = -1, keep: bool = False):
         """Waits for ``ticket``; returns the result as a dict (None on timeout).

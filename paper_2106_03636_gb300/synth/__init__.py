@@ -13,6 +13,9 @@ shapes of the workloads the tracker is measured on:
   multiplicity), 12-byte fixed-point records, ~250 M clusters.
 * ``chunk_mix``      - uneven sub-Time-Frame chunks (Poisson-many collisions,
   a quarter pp-like), for batched launches.
+* ``serving_pool``   - Time Frames of mixed size for a served stream: half
+  Pb-Pb with a uniform number of collisions (10..570), half pp-like with
+  2000 collisions at dN/deta = 6 (~3 M clusters).
 
 Physics of every primary: pT ~ 0.05 GeV + Exp(0.6 GeV), |eta| < 0.9,
 charge +-1, helix in Bz = 0.5 T, one cluster per crossed pad row, Gaussian
@@ -229,3 +232,28 @@ def chunk_mix(seed: int = 20210610, n_chunks: int = 64, mean_coll: float = 20.0,
                             t_window=chunk_us, fmt=fmt, with_truth=False, name=f"chunk{c}", **kw))
     return out
 
+
+
+def serving_pool(seed: int = 20210611, n_tf: int = 24, orbits: int = TF_ORBITS, coll_min: int = 10,
+                 coll_max: int = 570, pp_coll: int = 2000, pp_dndeta: float = 6.0,
+                 mult_scale: float = FULL_TF_MULT_SCALE, fmt: int = FMT_FIXED, **kw) -> list[TimeFrame]:
+    """A pool of Time Frames to replay as a served stream.  Even entries are
+    Pb-Pb (collision count uniform on [coll_min, coll_max], collision times
+    uniform over the frame, falling multiplicity scaled like ``full_tf``), odd
+    entries pp-like (``pp_coll`` collisions of dN/deta = ``pp_dndeta``)."""
+    rng = np.random.default_rng(seed)
+    t_len = orbits * ORBIT_US
+    out = []
+    for i in range(n_tf):
+        if i % 2 == 0:
+            k = int(rng.integers(coll_min, coll_max + 1))
+            t0 = np.sort(rng.uniform(0.0, t_len, k))
+            ntr = np.rint(mult_scale * 1.8 * falling_multiplicity(rng, k)).astype(np.int32)
+            name = f"pbpb{i}_{k}coll"
+        else:
+            t0 = np.sort(rng.uniform(0.0, t_len, pp_coll))
+            ntr = np.full(pp_coll, int(round(pp_dndeta * 1.8)), np.int32)
+            name = f"pp{i}"
+        out.append(generate(seed=seed * 1000 + i, t0=t0, ntracks=ntr, zvtx_sigma=5.0, t_window=t_len, fmt=fmt,
+                            with_truth=False, name=name, **kw))
+    return out

@@ -30,6 +30,7 @@
 #define G_NSEC 36
 #define G_DRIFT_LEN 250.0
 #define G_PI 3.14159265358979323846
+#define G_RHO_MAX 250.0 /* cm, beyond the outermost pad-row corner */
 
 /* ---------------------------------------------------------------- RNG */
 static inline uint64_t g_mix(uint64_t z) {
@@ -140,8 +141,17 @@ static void g_track(g_state* S, int32_t coll, int32_t it, int64_t gid, g_buf* ou
   double h = straight ? 0.0 : ((P->bz > 0) ? -(double)q : (double)q); /* +1: counter-clockwise */
   double cx = h * Rc * -sin(phi0), cy = h * Rc * cos(phi0);
 
+  /* Azimuth of the position swept out to the outer radius of the chamber:
+   * from phi0 over h * asin(rho / 2R) (a quarter turn at most).  A sector
+   * whose +-10 deg pad planes lie more than 2 deg outside that range gets no
+   * cluster (2 deg at the innermost row is 3 cm, beyond any smearing), so it
+   * is not visited. */
+  double sweep = straight ? 0.0 : (2.0 * Rc <= G_RHO_MAX ? 0.5 * G_PI : asin(G_RHO_MAX / (2.0 * Rc)));
+  double amid = phi0 + 0.5 * h * sweep;
+  double awin = 0.5 * sweep + 12.0 * G_PI / 180.0;
   for (int j = 0; j < 18; ++j) {
     if (P->sector_only >= 0 && (P->sector_only % 18) != j) continue;
+    if (fabs(remainder(g_alpha(j) - amid, 2.0 * G_PI)) > awin) continue;
     double a = g_alpha(j), ca = cos(a), sa = sin(a);
     double phil0 = phi0 - a;
     for (int r = 0; r < G_NROW; ++r) {

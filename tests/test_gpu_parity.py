@@ -97,9 +97,9 @@ def test_batch_equals_alone():
     with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_NO_BATCHING) as a:
         alone = [a.track(tf) for tf in tfs]
     with o2tpc.Tracker(max_batch=8) as b:
-        tickets = [b.submit(tf) for tf in tfs]
+        tickets = b.submit_many(tfs)
         mix = [b.poll(t) for t in tickets]
-    assert max(m["stats"]["batch_size"] for m in mix) >= 1
+    assert all(m["stats"]["batch_size"] == len(tfs) for m in mix)
     for x, y in zip(alone, mix):
         for k in ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref"):
             assert np.array_equal(x[k], y[k]), k
@@ -164,3 +164,14 @@ def test_uploads_ahead_equal_in_stream_uploads():
         assert np.isfinite(st[12]) and np.isfinite(st[13]) and st[12] >= 0 and st[13] >= 0
         for k in ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref"):
             assert np.array_equal(x[k], y[k]), k
+
+
+def test_submit_many_is_all_or_nothing():
+    tfs = [synth.single_sector(seed=s) for s in (11, 12, 13)]
+    with o2tpc.Tracker(max_inflight=2) as t:
+        with pytest.raises(o2tpc.O2TPCError) as e:
+            t.submit_many(tfs)
+        assert e.value.status == o2tpc.O2TPC_EAGAIN
+        tickets = t.submit_many(tfs[:2])
+        rs = [t.wait(k) for k in tickets]
+        assert all(r["status"] == 0 and r["n_tracks"] > 10 for r in rs)
