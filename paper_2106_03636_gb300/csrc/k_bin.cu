@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(512) k_row_scatter(const TFDesc* __restrict__ 
     decode(t, i, G, lr, yu, zu);
     const RowGrid g = grid[Rbase + lr];
     int iy = cell_iy(g, G->npads[lr % kNRow], yu);
-    int iz = (int)(((long long)zu - g.zmin) / g.cz);
+    int iz = cell_iz_floor(zu, g);  // zu >= zmin of its row: 0..nz-1
     int slot = atomicAdd(&s_cur[lr], 1);
     bucket[slot] = make_int4(yu, zu, t.inBase + i, iz * g.ny + iy);
   }

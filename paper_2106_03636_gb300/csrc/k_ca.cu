@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kNFBlock) k_neighbours(const RowGrid* __restri
     const RowGrid gu = grid[R + 1], gd = grid[R - 1];
     const int npu = G->npads[r + 1], npd = G->npads[r - 1];
     const int2 hh = syz[h];
-    const long long yh = hh.x, zh = hh.y;
+    const int yh = hh.x, zh = hh.y;
     int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
     if (cell_range(gu, npu, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, uy0, uy1, uz0, uz1) &&
         cell_range(gd, npd, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, dy0, dy1, dz0, dz1)) {

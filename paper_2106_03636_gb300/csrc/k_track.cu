@@ -32,29 +32,30 @@ __device__ inline int find_row(const RowGrid* __restrict__ grid, int nRows, int 
   return lo - 1;
 }
 
-__device__ inline long long clamp_ll(float v) {
-  v = fminf(fmaxf(v, -1.0e9f), 1.0e9f);
-  return (long long)v;
-}
+__device__ inline int clamp_i(float v) { return (int)fminf(fmaxf(v, -1.0e9f), 1.0e9f); }
 
 // Best hit of a row inside the +-3 sigma window of the prediction (ties: the
-// smaller sorted index); -1 if none has chi2 <= kChi2Follow.
+// smaller sorted index); -1 if none has chi2 <= kChi2Follow.  The best hit's
+// coordinates come back in *pbest.
 __device__ int search_row(const RowGrid& g, int npads, const int* __restrict__ cellStart,
                           const int2* __restrict__ syz, const KState<float>& s, int yref, int zref,
-                          float zunit) {
+                          float zunit, float izunit, int2* pbest) {
   if (g.count == 0) return -1;
   const float sy2 = s.C[0] + kSigY * kSigY, sz2 = s.C[2] + kSigZ * kSigZ;
   const float wy = 3.f * sqrtf(sy2), wz = 3.f * sqrtf(sz2);
   if (!(wy < 1e4f) || !(wz < 1e4f) || !isfinite(s.p[0]) || !isfinite(s.p[1])) return -1;
-  long long ylo = yref + clamp_ll(floorf((s.p[0] - wy) * 160.f)) - 1;
-  long long yhi = yref + clamp_ll(ceilf((s.p[0] + wy) * 160.f)) + 1;
-  long long zlo = zref + clamp_ll(floorf((s.p[1] - wz) / zunit)) - 1;
-  long long zhi = zref + clamp_ll(ceilf((s.p[1] + wz) / zunit)) + 1;
+  // the cell rectangle only has to cover the window: one unit of slack on
+  // each side absorbs the rounding of the float products
+  const int ylo = yref + clamp_i(floorf((s.p[0] - wy) * 160.f)) - 1;
+  const int yhi = yref + clamp_i(ceilf((s.p[0] + wy) * 160.f)) + 1;
+  const int zlo = zref + clamp_i(floorf((s.p[1] - wz) * izunit)) - 1;
+  const int zhi = zref + clamp_i(ceilf((s.p[1] + wz) * izunit)) + 1;
   int iy0, iy1, iz0, iz1;
   if (!cell_range(g, npads, ylo, yhi, zlo, zhi, iy0, iy1, iz0, iz1)) return -1;
   const float isy2 = 1.f / sy2, isz2 = 1.f / sz2;
   int best = -1;
   float bchi = 0.f;
+  int2 bp = make_int2(0, 0);
   for (int iz = iz0; iz <= iz1; ++iz) {
     const int a = __ldg(cellStart + g.cellBase + iz * g.ny + iy0);
     const int b = __ldg(cellStart + g.cellBase + iz * g.ny + iy1 + 1);
@@ -67,9 +68,11 @@ __device__ int search_row(const RowGrid& g, int npads, const int* __restrict__ c
       if (best < 0 || chi < bchi || (chi == bchi && h < best)) {
         best = h;
         bchi = chi;
+        bp = p;
       }
     }
   }
+  *pbest = bp;
   return best;
 }
 
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, int* __restrict__
 #pragma unroll
     for (int j = 0; j < 15; ++j) q.C[j] = s_last[6 + j][threadIdx.x];
   };
-  const float zunit = G->zunit, bzc = G->bzc;
+  const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
   // phases: 0 chain fit, 1 outward following, 2 inward refit, 3 inward
   // following, 5 take the next tracklet
   int phase = 5, k = 0, r0 = 0, Rs = 0, zref = 0, yref = 0;
@@ -192,7 +195,8 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, int* __restrict__
       phase = 0;
       continue;
     }
-    int row, hit = -1;
+    int row, hit = -1, nextChain = -1;
+    int2 hp = make_int2(0, 0);  // coordinates of the hit to add
     bool search = false;
     if (phase == 0) {
       if (chainHit < 0 || nc >= kNRow - r0) {
@@ -206,6 +210,9 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, int* __restrict__
       }
       row = r0 + nc;
       hit = chainHit;
+      // both loads in flight during the transport
+      hp = syz[hit];
+      nextChain = up[hit];
     } else if (phase == 1) {
       if (r >= kNRow) {
         begin_refit();
@@ -223,6 +230,7 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, int* __restrict__
       }
       row = Rw[i];
       hit = H[i];
+      hp = syz[hit];
     } else {
       if (r < 0) {
         finish(false);
@@ -234,7 +242,7 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, int* __restrict__
     bool stop = kf_prop<float>(st, G->rowx[row], bzc) != 0;
     if (!stop && search) {
       stop = fabsf(st.p[2]) > kSinFollow;
-      if (!stop) hit = search_row(grid[Rs + row], G->npads[row], cellStart, syz, st, yref, zref, zunit);
+      if (!stop) hit = search_row(grid[Rs + row], G->npads[row], cellStart, syz, st, yref, zref, zunit, izunit, &hp);
     }
     if (stop) {
       if (phase == 0) finish(true);
@@ -244,13 +252,12 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, int* __restrict__
       continue;
     }
     if (hit >= 0) {
-      const int2 p = syz[hit];
-      kf_update<float>(st, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
+      kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr);
       if (phase == 0) {
         H[nc] = hit;
         Rw[nc] = (uint8_t)row;
         ++nc;
-        chainHit = up[hit];
+        chainHit = nextChain;
       } else if (phase == 1) {
         H[na] = hit;
         Rw[na] = (uint8_t)row;
@@ -389,7 +396,7 @@ __global__ void __launch_bounds__(128) k_sector_fit(int nSt, TrackletBufs tb, co
                                                     const GeomConst* __restrict__ G, SectorTrackBufs sb) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= nSt) return;
-  const float zunit = G->zunit, bzc = G->bzc;
+  const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
   const int b = sb.off[id], m = sb.off[id + 1] - b;
   const int* H = sb.hits + b;
   const uint8_t* Rw = sb.rows + b;

@@ -114,6 +114,19 @@ uint64_t input_bytes(const o2tpc_tf& t) {
   return t.format == O2TPC_FMT_FIXED ? 12ull * t.n : 10ull * t.n + 64;
 }
 
+// A batch whose results are being copied to the host on the download stream.
+struct Pending {
+  std::vector<std::shared_ptr<Job>> jobs;
+  std::shared_ptr<BatchMem> out;  // device result arrays, freed once copied
+  cudaEvent_t dl0 = nullptr, dl1 = nullptr;
+  float stageMs[16] = {};
+  double hostPrepMs = 0;
+  ~Pending() {
+    if (dl0) cudaEventDestroy(dl0);
+    if (dl1) cudaEventDestroy(dl1);
+  }
+};
+
 struct Ctx {
   o2tpc_config cfg{};
   cudaStream_t stream = nullptr;
@@ -138,8 +151,15 @@ struct Ctx {
   uint64_t upAheadBytes = 0, upAheadLimit = 0;
   // the library's own stream-ordered pool (no user allocator)
   cudaMemPool_t pool = nullptr;
-  bool traceCopies = false;  // O2TPC_TRACE_COPIES=1: time every result copy (stderr); =2: the
-  int traceMode = 0;         // download phases without extra synchronisation
+  // result download: a third stream and the thread that completes batches
+  // once their copies have landed (the worker starts the next batch meanwhile)
+  cudaStream_t dlStream = nullptr;
+  std::thread finisher;
+  std::condition_variable cvFin;
+  std::deque<std::shared_ptr<Pending>> finQueue;
+  bool finStop = false;
+  bool traceCopies = false;  // O2TPC_TRACE_COPIES=1: time every result copy (stderr)
+  int traceMode = 0;
   // pinned staging for descriptors and results
   void* hStage = nullptr;
   size_t hStageBytes = 0;
@@ -517,19 +537,24 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   // ---- A11: final refit and output
   CK(cudaEventRecord(c->evs[8], st));
   int* trkNcl = dalloc<int>(M, nHeads + 1);
+  // result arrays live apart from the batch's other buffers: they stay until
+  // the download stream has copied them out
+  auto outMem = std::make_shared<BatchMem>();
+  outMem->ctx = c;
+  BatchMem& OM = *outMem;
   OutBufs ob;
-  ob.off = dalloc<int>(M, nHeads + 1);
-  ob.cl = dalloc<int>(M, nStHits);
-  ob.x = dalloc<float>(M, nHeads);
-  ob.alpha = dalloc<float>(M, nHeads);
-  ob.par = dalloc<float>(M, (size_t)nHeads * 5);
-  ob.cov = dalloc<float>(M, (size_t)nHeads * 15);
-  ob.chi2 = dalloc<float>(M, nHeads);
-  ob.ndf = dalloc<int>(M, nHeads);
-  ob.sector = dalloc<uint8_t>(M, nHeads);
-  ob.flags = dalloc<uint8_t>(M, nHeads);
-  ob.zref = dalloc<int>(M, nHeads);
-  ob.nFallback = dalloc<int>(M, 1);
+  ob.off = dalloc<int>(OM, nHeads + 1);
+  ob.cl = dalloc<int>(OM, nStHits);
+  ob.x = dalloc<float>(OM, nHeads);
+  ob.alpha = dalloc<float>(OM, nHeads);
+  ob.par = dalloc<float>(OM, (size_t)nHeads * 5);
+  ob.cov = dalloc<float>(OM, (size_t)nHeads * 15);
+  ob.chi2 = dalloc<float>(OM, nHeads);
+  ob.ndf = dalloc<int>(OM, nHeads);
+  ob.sector = dalloc<uint8_t>(OM, nHeads);
+  ob.flags = dalloc<uint8_t>(OM, nHeads);
+  ob.zref = dalloc<int>(OM, nHeads);
+  ob.nFallback = dalloc<int>(OM, 1);
   CK(cudaMemsetAsync(ob.nFallback, 0, sizeof(int), st));
   launch_chain_counts(nHeads, heads, sb, mb, trkNcl, st);
   CKL();
@@ -544,8 +569,9 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CK(cudaEventRecord(c->ev1, st));
   CK(cudaEventRecord(c->evs[9], st));
 
-  // ---- A12: download: sizes first, then every TF's arrays straight into
-  // its own pinned result block
+  // ---- A12: download.  Sizes first (synchronously), then every TF's arrays
+  // straight into its own pinned result block on the download stream, which
+  // the finisher thread waits for while the worker starts the next batch.
   const size_t nT = (size_t)nHeads;
   int* hSmall = static_cast<int*>(c->stage(sizeof(int) * (nT + 1 + 3 * (B + 1) + 8)));
   int* hOff = hSmall;
@@ -562,8 +588,24 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   for (int i = 0; i < B; ++i) CK(cudaMemcpyAsync(&tfFirstRow[i], grid + (size_t)i * kRowsPerTF, sizeof(RowGrid),
                                                  cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(c->evs[10], st));
-  const double tSizes = now_ms();
   CK(cudaStreamSynchronize(st));
+
+  auto P = std::make_shared<Pending>();
+  P->jobs = jobs;
+  P->out = outMem;
+  for (int k = 0; k < 10; ++k) cudaEventElapsedTime(&P->stageMs[k], c->evs[k], c->evs[k + 1]);
+  cudaEventElapsedTime(&P->stageMs[12], c->evWait, c->evs[0]);
+  cudaEventElapsedTime(&P->stageMs[13], c->ev0, c->evWait);
+  float devMs = 0.f;
+  cudaEventElapsedTime(&devMs, c->ev0, c->ev1);
+  const long long nLaunch = g_launch_count;
+  const bool inputBad = (*hErr & kErrInput) != 0;
+  cudaStream_t dl = c->dlStream;
+  CK(cudaEventCreate(&P->dl0));
+  CK(cudaEventCreate(&P->dl1));
+  CK(cudaStreamWaitEvent(dl, c->evs[10], 0));
+  CK(cudaEventRecord(P->dl0, dl));
+
   auto r16 = [](size_t x) { return (x + 15) / 16 * 16; };
   const double tPrep = now_ms();
   for (int i = 0; i < B; ++i) {
@@ -582,21 +624,17 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
           cudaEvent_t a, b;
           cudaEventCreate(&a);
           cudaEventCreate(&b);
-          cudaEventRecord(a, st);
-          CK(cudaMemcpyAsync(dst, dsrc, nb, cudaMemcpyDeviceToHost, st));
-          cudaEventRecord(b, st);
+          cudaEventRecord(a, dl);
+          CK(cudaMemcpyAsync(dst, dsrc, nb, cudaMemcpyDeviceToHost, dl));
+          cudaEventRecord(b, dl);
           cudaEventSynchronize(b);
           float ms = 0.f;
           cudaEventElapsedTime(&ms, a, b);
-          cudaPointerAttributes pa{}, pb{};
-          cudaPointerGetAttributes(&pa, dst);
-          cudaPointerGetAttributes(&pb, dsrc);
-          std::fprintf(stderr, "o2tpc copy %zu bytes %.3f ms %.1f GB/s dst type %d src type %d\n", nb, ms,
-                       nb / (ms * 1e6), (int)pa.type, (int)pb.type);
+          std::fprintf(stderr, "o2tpc copy %zu bytes %.3f ms %.1f GB/s\n", nb, ms, nb / (ms * 1e6));
           cudaEventDestroy(a);
           cudaEventDestroy(b);
         } else {
-          CK(cudaMemcpyAsync(dst, dsrc, nb, cudaMemcpyDeviceToHost, st));
+          CK(cudaMemcpyAsync(dst, dsrc, nb, cudaMemcpyDeviceToHost, dl));
         }
       }
       q += r16(nb);
@@ -618,31 +656,22 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     R.sector = reinterpret_cast<const uint8_t*>(take(ob.sector + t0, nt));
     R.flags = reinterpret_cast<const uint8_t*>(take(ob.flags + t0, nt));
     for (size_t k = 0; k <= nt; ++k) off64[k] = (uint64_t)(hOff[t0 + k] - hOff[t0]);
+    R.user_tag = J.tf.user_tag;
+    R.stats.n_clusters = J.tf.n;
+    R.stats.n_tracklets = (uint64_t)(hTlTf[i + 1] - hTlTf[i]);
+    R.stats.n_sector_tracks = (uint64_t)(hStTf[i + 1] - hStTf[i]);
+    R.stats.n_tracks = R.n_tracks;
+    R.stats.batch_size = (uint32_t)B;
+    R.stats.ms_queue = (float)(J.t_start - J.t_submit);
+    R.stats.ms_device = devMs;
+    R.stats.n_launches = (uint64_t)nLaunch;
+    J.status = inputBad ? O2TPC_EINVAL : O2TPC_OK;
+    R.status = J.status;
+    J.tfIndex = i;
   }
-  const double hostPrepMs = now_ms() - tPrep;
-  CK(cudaEventRecord(c->evs[11], st));
-  const double tWait = now_ms();
-  CK(cudaStreamSynchronize(st));
-  if (c->traceCopies && c->traceMode == 2) {
-    float msCopy = 0.f;
-    cudaEventElapsedTime(&msCopy, c->evs[10], c->evs[11]);
-    std::fprintf(stderr, "o2tpc download: host prep %.3f ms, final wait %.3f ms, device %.3f ms, sizes sync at %.3f\n",
-                 hostPrepMs, now_ms() - tWait, msCopy, tPrep - tSizes);
-  }
-  float devMs = 0.f;
-  float stageMs[16] = {};
-  for (int k = 0; k < 11; ++k) {
-    stageMs[k] = 0.f;
-    cudaEventElapsedTime(&stageMs[k], c->evs[k], c->evs[k + 1]);
-  }
-  stageMs[11] = (float)hostPrepMs;
-  cudaEventElapsedTime(&stageMs[12], c->evWait, c->evs[0]);
-  cudaEventElapsedTime(&stageMs[13], c->ev0, c->evWait);
-  const long long nLaunch = g_launch_count;
-  cudaEventElapsedTime(&devMs, c->ev0, c->ev1);
-  const bool inputBad = (*hErr & kErrInput) != 0;
+  CK(cudaEventRecord(P->dl1, dl));
+  P->hostPrepMs = now_ms() - tPrep;
 
-  const double tEnd = now_ms();
   M.tfHitBase.resize(B);
   M.tfHitEnd.resize(B);
   M.tfInBase.resize(B);
@@ -652,27 +681,6 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     M.tfHitBase[i] = tfFirstRow[i].start;
     M.tfHitEnd[i] = (i + 1 < B) ? tfFirstRow[i + 1].start : n;
     M.tfInBase[i] = tfd[i].inBase;
-  }
-  for (int i = 0; i < B; ++i) {
-    Job& J = *jobs[i];
-    o2tpc_result& R = J.res;
-    uint64_t fb = 0;
-    for (uint64_t k = 0; k < R.n_tracks; ++k) fb += (R.flags[k] & 1) ? 1 : 0;
-    R.user_tag = J.tf.user_tag;
-    R.stats.n_clusters = J.tf.n;
-    R.stats.n_tracklets = (uint64_t)(hTlTf[i + 1] - hTlTf[i]);
-    R.stats.n_sector_tracks = (uint64_t)(hStTf[i + 1] - hStTf[i]);
-    R.stats.n_tracks = R.n_tracks;
-    R.stats.n_fp64_fallback = fb;
-    R.stats.batch_size = (uint32_t)B;
-    R.stats.ms_queue = (float)(J.t_start - J.t_submit);
-    R.stats.ms_batch = (float)(tEnd - J.t_start);
-    R.stats.ms_device = devMs;
-    R.stats.n_launches = (uint64_t)nLaunch;
-    for (int k = 0; k < 16; ++k) R.stats.ms_stage[k] = stageMs[k];
-    J.status = inputBad ? O2TPC_EINVAL : O2TPC_OK;
-    R.status = J.status;
-    J.tfIndex = i;
   }
   if (keep) {
     M.grid = grid;
@@ -690,6 +698,12 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     M.refs = B;
     for (int i = 0; i < B; ++i) jobs[i]->mem = mem;
   }
+  // hand the batch to the finisher; nothing below may throw
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->finQueue.push_back(P);
+  }
+  c->cvFin.notify_one();
   // without kept stages the batch memory is freed here (stream-ordered)
 }
 
@@ -814,19 +828,67 @@ void worker_main(Ctx* c) {
       }
     }
     for (auto& j : batch) release_upload(c, *j);
+    if (status == O2TPC_OK) continue;  // the finisher completes the batch
     {
       std::lock_guard<std::mutex> lk(c->mu);
       for (auto& j : batch) {
-        if (status != O2TPC_OK) {
-          j->status = status;
-          j->res = o2tpc_result{};
-          j->res.status = status;
-          j->res.user_tag = j->tf.user_tag;
-          j->emptyOffset = 0;
-          j->res.offsets = &j->emptyOffset;
-        }
+        j->status = status;
+        j->res = o2tpc_result{};
+        j->res.status = status;
+        j->res.user_tag = j->tf.user_tag;
+        j->emptyOffset = 0;
+        j->res.offsets = &j->emptyOffset;
         j->t_end = now_ms();
         j->done = true;
+      }
+    }
+    c->cvDone.notify_all();
+  }
+}
+
+// Finisher: completes batches in order once their download has landed, then
+// frees their device result arrays.
+void finisher_main(Ctx* c) {
+  cudaSetDevice(c->cfg.device);
+  for (;;) {
+    std::shared_ptr<Pending> P;
+    {
+      std::unique_lock<std::mutex> lk(c->mu);
+      c->cvFin.wait(lk, [&] { return c->finStop || !c->finQueue.empty(); });
+      if (c->finQueue.empty()) return;
+      P = c->finQueue.front();
+      c->finQueue.pop_front();
+    }
+    const cudaError_t e = cudaEventSynchronize(P->dl1);
+    float dlMs = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&dlMs, P->dl0, P->dl1);
+    const double tEnd = now_ms();
+    P->out.reset();
+    if (e == cudaSuccess) {
+      for (auto& jp : P->jobs) {
+        o2tpc_result& R = jp->res;
+        uint64_t fb = 0;
+        for (uint64_t k = 0; k < R.n_tracks; ++k) fb += (R.flags[k] & 1) ? 1 : 0;
+        R.stats.n_fp64_fallback = fb;
+        for (int k = 0; k < 16; ++k) R.stats.ms_stage[k] = P->stageMs[k];
+        R.stats.ms_stage[10] = dlMs;
+        R.stats.ms_stage[11] = (float)P->hostPrepMs;
+        R.stats.ms_batch = (float)(tEnd - jp->t_start);
+      }
+    } else {
+      std::fprintf(stderr, "o2tpc: CUDA error %s in the result download\n", cudaGetErrorString(e));
+      cudaGetLastError();
+    }
+    {
+      std::lock_guard<std::mutex> lk(c->mu);
+      if (e != cudaSuccess) c->fatal = O2TPC_ECUDA;
+      for (auto& jp : P->jobs) {
+        if (e != cudaSuccess) {
+          jp->status = O2TPC_ECUDA;
+          jp->res.status = O2TPC_ECUDA;
+        }
+        jp->t_end = tEnd;
+        jp->done = true;
       }
     }
     c->cvDone.notify_all();
@@ -888,6 +950,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
     CK(cudaEventCreate(&x->ev1));
     CK(cudaEventCreate(&x->evWait));
     CK(cudaStreamCreateWithFlags(&x->upStream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&x->dlStream, cudaStreamNonBlocking));
     if (!c.dev_alloc) {
       cudaMemPoolProps props{};
       props.allocType = cudaMemAllocationTypePinned;
@@ -917,6 +980,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
     return O2TPC_ENOMEM;
   }
   x->worker = std::thread(worker_main, x);
+  x->finisher = std::thread(finisher_main, x);
   if (x->pool) x->uploader = std::thread(uploader_main, x);
   *out = reinterpret_cast<o2tpc_ctx*>(x);
   return O2TPC_OK;
@@ -1020,6 +1084,12 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
   c->cvUp.notify_all();
   if (c->worker.joinable()) c->worker.join();
   if (c->uploader.joinable()) c->uploader.join();
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->finStop = true;
+  }
+  c->cvFin.notify_all();
+  if (c->finisher.joinable()) c->finisher.join();
   int rc = c->fatal;
   cudaSetDevice(c->cfg.device);
   {
@@ -1044,6 +1114,10 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
   if (c->upStream) {
     cudaStreamSynchronize(c->upStream);
     cudaStreamDestroy(c->upStream);
+  }
+  if (c->dlStream) {
+    cudaStreamSynchronize(c->dlStream);
+    cudaStreamDestroy(c->dlStream);
   }
   if (c->ownStream) cudaStreamDestroy(c->stream);
   if (c->pool) cudaMemPoolDestroy(c->pool);

@@ -82,36 +82,45 @@ struct TFDesc {
 enum : unsigned { kErrInput = 1u, kErrOverflow = 2u, kErrTimeout = 4u };
 
 // ------------------------------------------------------------ helpers
-__host__ __device__ inline int floordiv_i64(long long a, long long b) {
-  long long q = a / b;
-  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
-  return (int)q;
+// floor(a / b) for b > 0 in 32-bit arithmetic.
+__host__ __device__ inline int floordiv_i32(int a, int b) {
+  const int q = a / b;
+  return (q * b > a) ? q - 1 : q;
 }
 
 __device__ inline int cell_iy(const RowGrid& g, int npads, int yu) {
   int half = 32 * npads;
-  int iy = floordiv_i64((long long)yu + half, kCellY);
+  int iy = floordiv_i32(yu + half, kCellY);
   return iy < 0 ? 0 : (iy > g.ny - 1 ? g.ny - 1 : iy);
 }
 
+// Cell row of a drift coordinate: floor((v - zmin) / cz), -1 below the row's
+// range.  v - zmin can exceed the int32 range (|v|, |zmin| < 2^31), so the
+// difference and the division are unsigned.
+__device__ inline int cell_iz_floor(int v, const RowGrid& g) {
+  if (v < g.zmin) return -1;
+  const unsigned q = ((unsigned)v - (unsigned)g.zmin) / (unsigned)g.cz;
+  return q > 0x3FFFFFFFu ? 0x3FFFFFFF : (int)q;
+}
+
 // Cell rectangle of row g overlapping [ylo,yhi] x [zlo,zhi]; false if empty.
-__device__ inline bool cell_range(const RowGrid& g, int npads, long long ylo, long long yhi, long long zlo,
-                                  long long zhi, int& iy0, int& iy1, int& iz0, int& iz1) {
+// Coordinates are integer units inside the int32 range (y windows within a
+// few 10^6, z windows within +-2.1e9), so 32-bit arithmetic suffices.
+__device__ inline bool cell_range(const RowGrid& g, int npads, int ylo, int yhi, int zlo, int zhi, int& iy0,
+                                  int& iy1, int& iz0, int& iz1) {
   if (g.count == 0) return false;
-  long long half = 32 * npads;
-  long long a = ylo + half, b = yhi + half;
-  long long qa = a >= 0 ? a / kCellY : -((-a + kCellY - 1) / kCellY);
-  long long qb = b >= 0 ? b / kCellY : -((-b + kCellY - 1) / kCellY);
-  iy0 = (int)(qa < 0 ? 0 : (qa > g.ny - 1 ? g.ny - 1 : qa));
-  iy1 = (int)(qb < 0 ? 0 : (qb > g.ny - 1 ? g.ny - 1 : qb));
-  long long za = zlo - g.zmin, zb = zhi - g.zmin;
-  long long qza = za >= 0 ? za / g.cz : -((-za + g.cz - 1) / g.cz);
-  long long qzb = zb >= 0 ? zb / g.cz : -((-zb + g.cz - 1) / g.cz);
+  const int half = 32 * npads;
+  const int qa = floordiv_i32(ylo + half, kCellY);
+  const int qb = floordiv_i32(yhi + half, kCellY);
+  iy0 = qa < 0 ? 0 : (qa > g.ny - 1 ? g.ny - 1 : qa);
+  iy1 = qb < 0 ? 0 : (qb > g.ny - 1 ? g.ny - 1 : qb);
+  int qza = cell_iz_floor(zlo, g);
+  int qzb = cell_iz_floor(zhi, g);
   if (qza < 0) qza = 0;
   if (qzb > g.nz - 1) qzb = g.nz - 1;
   if (qza > qzb) return false;
-  iz0 = (int)qza;
-  iz1 = (int)qzb;
+  iz0 = qza;
+  iz1 = qzb;
   return true;
 }
 
