@@ -95,6 +95,15 @@ __device__ inline void store_state(float* dst, const KState<float>& s, int yref)
 #pragma unroll
   for (int i = 0; i < 15; ++i) dst[6 + i] = s.C[i];
 }
+// Stores a state as it is (y relative to the fit's origin): the hand-over
+// between the passes of the tracklet constructor.
+__device__ inline void store_raw(float* dst, const KState<float>& s) {
+  dst[0] = s.x;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) dst[1 + i] = s.p[i];
+#pragma unroll
+  for (int i = 0; i < 15; ++i) dst[6 + i] = s.C[i];
+}
 __device__ inline void load_state(KState<float>& s, const float* src) {
   s.x = src[0];
 #pragma unroll
@@ -103,23 +112,79 @@ __device__ inline void load_state(KState<float>& s, const float* src) {
   for (int i = 0; i < 15; ++i) s.C[i] = src[6 + i];
 }
 
-// K7: persistent threads, one tracklet at a time each, taking the next start
-// hit from a global counter as soon as the previous tracklet is done (no lane
-// idles until the longest tracklet of its warp ends).  The passes of a
-// tracklet (chain fit, outward following, inward refit of the attached hits,
-// inward following below the chain) are phases of one loop whose body holds a
-// single transport, search and update: threads of a warp in different phases
-// still issue the same instructions.  Results do not depend on which thread
-// builds which tracklet.
-__global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, int* __restrict__ workCounter,
-                                                      const int* __restrict__ starts,
-                                                      const int* __restrict__ up, const RowGrid* __restrict__ grid,
-                                                      int nRows, const int* __restrict__ cellStart,
-                                                      const int2* __restrict__ syz, const GeomConst* __restrict__ G,
-                                                      TrackletBufs tb) {
-  // the state after the last accepted hit lives in shared memory (one column
-  // per thread) rather than in registers
-  __shared__ float s_last[21][128];
+// K7: the TrackletConstructor in four passes, one persistent kernel each:
+// (a) chain fit, (b) outward following, (c) inward refit of the attached
+// hits, (d) inward following below the chain start.  Within a pass every
+// lane runs the same loop body (transport, then either the next known hit or
+// a row search, then the update), so a warp stays converged; lanes take the
+// next tracklet from a global counter as soon as theirs is done.  Between the
+// passes a tracklet's state waits in tb.state (21 floats), its hit count in
+// tb.nasc and its row base in tb.rbase; tb.nhits is written by the last pass
+// (0: dropped).  Results do not depend on which thread builds which tracklet.
+
+// (a) chain fit: seed from the first and third chain hits, then one update
+// per chain hit.  A transport failure drops the tracklet.
+__global__ void __launch_bounds__(128) k_tl_chain(int nTl, int* __restrict__ counter, const int* __restrict__ starts,
+                                                  const int* __restrict__ up, const RowGrid* __restrict__ grid,
+                                                  int nRows, const int2* __restrict__ syz,
+                                                  const GeomConst* __restrict__ G, TrackletBufs tb) {
+  const float zunit = G->zunit, bzc = G->bzc;
+  for (;;) {
+    const int k = atomicAdd(counter, 1);
+    if (k >= nTl) return;
+    const int h0 = starts[k];
+    const int R0 = find_row(grid, nRows, h0);
+    const int r0 = (R0 % kRowsPerTF) % kNRow;
+    int* H = tb.hits + (size_t)k * kMaxTlHits;
+    uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
+    const int2 a0 = syz[h0];
+    const int zref = a0.y, yref = a0.x;
+    tb.zref[k] = zref;
+    tb.rbase[k] = R0 - r0;
+    const int h1 = up[h0];
+    const int2 a2 = syz[up[h1]];
+    const float x0 = G->rowx[r0], x2 = G->rowx[r0 + 2];
+    const float dx = x2 - x0, dy = hit_y(a2.x, yref) - hit_y(a0.x, yref);
+    const float tphi = dy / dx;
+    const float s0 = tphi / sqrtf(1.f + tphi * tphi);
+    const float t0 = (hit_z(a2.y, zref, zunit) - hit_z(a0.y, zref, zunit)) / sqrtf(dx * dx + dy * dy);
+    KState<float> st;
+    kf_reset<float>(st, x0, hit_y(a0.x, yref), hit_z(a0.y, zref, zunit), s0, t0, 0.f);
+    H[0] = h0;
+    Rw[0] = (uint8_t)r0;
+    int nc = 1, hit = h1;
+    bool dropped = false;
+    while (hit >= 0 && nc < kNRow - r0) {
+      const int row = r0 + nc;
+      const int2 hp = syz[hit];  // both loads in flight during the transport
+      const int next = up[hit];
+      if (kf_prop<float>(st, G->rowx[row], bzc) != 0) {
+        dropped = true;
+        break;
+      }
+      kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr);
+      H[nc] = hit;
+      Rw[nc] = (uint8_t)row;
+      ++nc;
+      hit = next;
+    }
+    tb.nasc[k] = dropped ? 0 : nc;
+    if (dropped) tb.nhits[k] = 0;
+    else store_raw(tb.state + (size_t)k * 21, st);
+  }
+}
+
+// Following (passes b and d): from row r in steps of dir, transport, search
+// the +-3 sigma window, update with the best hit; stop after kMaxMiss rows
+// without a hit, at the row range end, on a transport failure or when
+// |sin phi| > kSinFollow.  The state after the last accepted hit is kept in
+// shared memory (one column per thread) and returned in st.  Appends the
+// hits at H[n..]; returns the new count.
+template <int kDir>
+__device__ inline int follow(KState<float>& st, float (*s_last)[128], int r, int n, int* H, uint8_t* Rw, int* top,
+                             int Rs, int yref, int zref, const RowGrid* __restrict__ grid,
+                             const int* __restrict__ cellStart, const int2* __restrict__ syz,
+                             const GeomConst* __restrict__ G, float zunit, float izunit, float bzc) {
   auto save_last = [&](const KState<float>& q) {
     s_last[0][threadIdx.x] = q.x;
 #pragma unroll
@@ -127,159 +192,114 @@ __global__ void __launch_bounds__(128, 6) k_tracklets(int nTl, int* __restrict__
 #pragma unroll
     for (int j = 0; j < 15; ++j) s_last[6 + j][threadIdx.x] = q.C[j];
   };
-  auto load_last = [&](KState<float>& q) {
-    q.x = s_last[0][threadIdx.x];
+  save_last(st);
+  int misses = 0;
+  for (; kDir > 0 ? r < kNRow : r >= 0; r += kDir) {
+    if (kf_prop<float>(st, G->rowx[r], bzc) != 0 || fabsf(st.p[2]) > kSinFollow) break;
+    int2 hp;
+    const int hit = search_row(grid[Rs + r], G->npads[r], cellStart, syz, st, yref, zref, zunit, izunit, &hp);
+    if (hit >= 0) {
+      kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr);
+      H[n] = hit;
+      Rw[n] = (uint8_t)r;
+      ++n;
+      *top = hit;
+      save_last(st);
+      misses = 0;
+    } else if (++misses >= kMaxMiss) {
+      break;
+    }
+  }
+  st.x = s_last[0][threadIdx.x];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) q.p[j] = s_last[1 + j][threadIdx.x];
+  for (int j = 0; j < 5; ++j) st.p[j] = s_last[1 + j][threadIdx.x];
 #pragma unroll
-    for (int j = 0; j < 15; ++j) q.C[j] = s_last[6 + j][threadIdx.x];
-  };
+  for (int j = 0; j < 15; ++j) st.C[j] = s_last[6 + j][threadIdx.x];
+  return n;
+}
+
+// (b) outward following above the chain; then the refit's starting state:
+// the last accepted state with the position of the top hit and a fresh
+// covariance.
+__global__ void __launch_bounds__(128) k_tl_out(int nTl, int* __restrict__ counter, const RowGrid* __restrict__ grid,
+                                                const int* __restrict__ cellStart, const int2* __restrict__ syz,
+                                                const GeomConst* __restrict__ G, TrackletBufs tb) {
+  __shared__ float s_last[21][128];
   const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
-  // phases: 0 chain fit, 1 outward following, 2 inward refit, 3 inward
-  // following, 5 take the next tracklet
-  int phase = 5, k = 0, r0 = 0, Rs = 0, zref = 0, yref = 0;
-  int i = 0, r = 0, nc = 0, na = 0, nd = 0, misses = 0, top = 0, chainHit = -1;
-  int* H = nullptr;
-  uint8_t* Rw = nullptr;
-  KState<float> st;
-  // end of the outward following: restart at the top hit, fresh covariance
-  auto begin_refit = [&]() {
-    load_last(st);
+  for (;;) {
+    const int k = atomicAdd(counter, 1);
+    if (k >= nTl) return;
+    const int nc = tb.nasc[k];
+    if (nc == 0) continue;
+    int* H = tb.hits + (size_t)k * kMaxTlHits;
+    uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
+    const int r0 = Rw[0], Rs = tb.rbase[k], zref = tb.zref[k];
+    const int yref = syz[H[0]].x;
+    KState<float> st;
+    float* S = tb.state + (size_t)k * 21;
+    load_state(st, S);
+    int top = H[nc - 1];
+    const int na = follow<1>(st, s_last, r0 + nc, nc, H, Rw, &top, Rs, yref, zref, grid, cellStart, syz, G, zunit,
+                             izunit, bzc);
     const int2 p = syz[top];
     st.p[0] = hit_y(p.x, yref);
     st.p[1] = hit_z(p.y, zref, zunit);
     reset_cov(st);
-    i = na - 2;
-    phase = 2;
-  };
-  auto finish = [&](bool dropped) {
-    if (dropped) {
-      tb.nhits[k] = 0;
-      tb.nasc[k] = 0;
-    } else {
-      tb.nhits[k] = na + nd;
-      tb.nasc[k] = na;
-      load_last(st);
-      store_state(tb.state + (size_t)k * 21, st, yref);
-    }
-    phase = 5;
-  };
+    tb.nasc[k] = na;
+    store_raw(S, st);
+  }
+}
+
+// (c) inward refit from the top hit through every attached hit; a hit whose
+// transport fails is skipped.
+__global__ void __launch_bounds__(128) k_tl_refit(int nTl, int* __restrict__ counter, const int2* __restrict__ syz,
+                                                  const GeomConst* __restrict__ G, TrackletBufs tb) {
+  const float zunit = G->zunit, bzc = G->bzc;
   for (;;) {
-    if (phase == 5) {
-      k = atomicAdd(workCounter, 1);
-      if (k >= nTl) break;
-      const int h0 = starts[k];
-      const int R0 = find_row(grid, nRows, h0);
-      r0 = (R0 % kRowsPerTF) % kNRow;
-      Rs = R0 - r0;
-      H = tb.hits + (size_t)k * kMaxTlHits;
-      Rw = tb.rows + (size_t)k * kMaxTlHits;
-      const int2 a0 = syz[h0];
-      zref = a0.y;
-      yref = a0.x;
-      tb.zref[k] = zref;
-      const int h1 = up[h0];
-      const int2 a2 = syz[up[h1]];
-      const float x0 = G->rowx[r0], x2 = G->rowx[r0 + 2];
-      const float dx = x2 - x0, dy = hit_y(a2.x, yref) - hit_y(a0.x, yref);
-      const float tphi = dy / dx;
-      const float s0 = tphi / sqrtf(1.f + tphi * tphi);
-      const float t0 = (hit_z(a2.y, zref, zunit) - hit_z(a0.y, zref, zunit)) / sqrtf(dx * dx + dy * dy);
-      kf_reset<float>(st, x0, hit_y(a0.x, yref), hit_z(a0.y, zref, zunit), s0, t0, 0.f);
-      H[0] = h0;
-      Rw[0] = (uint8_t)r0;
-      nc = 1;
-      chainHit = h1;
-      nd = 0;
-      misses = 0;
-      phase = 0;
-      continue;
-    }
-    int row, hit = -1, nextChain = -1;
-    int2 hp = make_int2(0, 0);  // coordinates of the hit to add
-    bool search = false;
-    if (phase == 0) {
-      if (chainHit < 0 || nc >= kNRow - r0) {
-        na = nc;
-        top = H[nc - 1];
-        save_last(st);
-        r = r0 + nc;
-        misses = 0;
-        phase = 1;
-        continue;
-      }
-      row = r0 + nc;
-      hit = chainHit;
-      // both loads in flight during the transport
-      hp = syz[hit];
-      nextChain = up[hit];
-    } else if (phase == 1) {
-      if (r >= kNRow) {
-        begin_refit();
-        continue;
-      }
-      row = r;
-      search = true;
-    } else if (phase == 2) {
-      if (i < 0) {
-        save_last(st);
-        r = r0 - 1;
-        misses = 0;
-        phase = 3;
-        continue;
-      }
-      row = Rw[i];
-      hit = H[i];
-      hp = syz[hit];
-    } else {
-      if (r < 0) {
-        finish(false);
-        continue;
-      }
-      row = r;
-      search = true;
-    }
-    bool stop = kf_prop<float>(st, G->rowx[row], bzc) != 0;
-    if (!stop && search) {
-      stop = fabsf(st.p[2]) > kSinFollow;
-      if (!stop) hit = search_row(grid[Rs + row], G->npads[row], cellStart, syz, st, yref, zref, zunit, izunit, &hp);
-    }
-    if (stop) {
-      if (phase == 0) finish(true);
-      else if (phase == 2) --i;
-      else if (phase == 1) begin_refit();
-      else finish(false);
-      continue;
-    }
-    if (hit >= 0) {
+    const int k = atomicAdd(counter, 1);
+    if (k >= nTl) return;
+    const int na = tb.nasc[k];
+    if (na == 0) continue;
+    const int* H = tb.hits + (size_t)k * kMaxTlHits;
+    const uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
+    const int zref = tb.zref[k];
+    const int yref = syz[H[0]].x;
+    KState<float> st;
+    float* S = tb.state + (size_t)k * 21;
+    load_state(st, S);
+    for (int i = na - 2; i >= 0; --i) {
+      const int2 hp = syz[H[i]];
+      if (kf_prop<float>(st, G->rowx[Rw[i]], bzc) != 0) continue;
       kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr);
-      if (phase == 0) {
-        H[nc] = hit;
-        Rw[nc] = (uint8_t)row;
-        ++nc;
-        chainHit = nextChain;
-      } else if (phase == 1) {
-        H[na] = hit;
-        Rw[na] = (uint8_t)row;
-        ++na;
-        top = hit;
-        save_last(st);
-        misses = 0;
-      } else if (phase == 3) {
-        H[na + nd] = hit;
-        Rw[na + nd] = (uint8_t)row;
-        ++nd;
-        save_last(st);
-        misses = 0;
-      }
-    } else if (search && ++misses >= kMaxMiss) {
-      if (phase == 1) begin_refit();
-      else finish(false);
-      continue;
     }
-    if (phase == 1) ++r;
-    else if (phase == 2) --i;
-    else if (phase == 3) --r;
+    store_raw(S, st);
+  }
+}
+
+// (d) inward following below the chain start; the state kept is the one at
+// the innermost accepted hit.
+__global__ void __launch_bounds__(128) k_tl_in(int nTl, int* __restrict__ counter, const RowGrid* __restrict__ grid,
+                                               const int* __restrict__ cellStart, const int2* __restrict__ syz,
+                                               const GeomConst* __restrict__ G, TrackletBufs tb) {
+  __shared__ float s_last[21][128];
+  const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
+  for (;;) {
+    const int k = atomicAdd(counter, 1);
+    if (k >= nTl) return;
+    const int na = tb.nasc[k];
+    if (na == 0) continue;
+    int* H = tb.hits + (size_t)k * kMaxTlHits;
+    uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
+    const int r0 = Rw[0], Rs = tb.rbase[k], zref = tb.zref[k];
+    const int yref = syz[H[0]].x;
+    KState<float> st;
+    float* S = tb.state + (size_t)k * 21;
+    load_state(st, S);
+    int top = -1;
+    const int n = follow<-1>(st, s_last, r0 - 1, na, H, Rw, &top, Rs, yref, zref, grid, cellStart, syz, G, zunit,
+                             izunit, bzc);
+    tb.nhits[k] = n;
+    store_state(S, st, yref);
   }
 }
 
@@ -430,21 +450,36 @@ __global__ void __launch_bounds__(128) k_sector_fit(int nSt, TrackletBufs tb, co
 }
 
 // ------------------------------------------------------------- launchers
+namespace {
+struct PassGrid {
+  int sms = 0, chain = 0, out = 0, refit = 0, in = 0;
+};
+PassGrid pass_grid() {
+  static PassGrid g;
+  if (g.sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.chain, k_tl_chain, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.out, k_tl_out, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.refit, k_tl_refit, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.in, k_tl_in, 128, 0);
+  }
+  return g;
+}
+}  // namespace
+
 void launch_tracklets(int nTl, int* workCounter, const int* starts, const int* up, const RowGrid* grid, int nRows,
                       const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st) {
   if (nTl <= 0) return;
-  static int sms = 0, perSm = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perSm, k_tracklets, 128, 0);
-    if (perSm < 1) perSm = 1;
-  }
-  const int blocks = std::min((nTl + 127) / 128, sms * perSm);
-  cudaMemsetAsync(workCounter, 0, sizeof(int), st);
-  k_tracklets<<<blocks, 128, 0, st>>>(nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb);
-  ++g_launch_count;
+  const PassGrid g = pass_grid();
+  auto blocks = [&](int perSm) { return std::min((nTl + 127) / 128, g.sms * std::max(perSm, 1)); };
+  cudaMemsetAsync(workCounter, 0, 4 * sizeof(int), st);
+  k_tl_chain<<<blocks(g.chain), 128, 0, st>>>(nTl, workCounter, starts, up, grid, nRows, syz, G, tb);
+  k_tl_out<<<blocks(g.out), 128, 0, st>>>(nTl, workCounter + 1, grid, cellStart, syz, G, tb);
+  k_tl_refit<<<blocks(g.refit), 128, 0, st>>>(nTl, workCounter + 2, syz, G, tb);
+  k_tl_in<<<blocks(g.in), 128, 0, st>>>(nTl, workCounter + 3, grid, cellStart, syz, G, tb);
+  g_launch_count += 4;
 }
 
 void launch_ownership(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, unsigned long long* w, cudaStream_t st) {

@@ -435,6 +435,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   tb.rows = dalloc<uint8_t>(M, (size_t)nTl * kMaxTlHits);
   tb.state = dalloc<float>(M, (size_t)nTl * 21);
   tb.zref = dalloc<int>(M, nTl);
+  tb.rbase = dalloc<int>(M, nTl);
   int* workCounter = dalloc<int>(M, 4);
   launch_tracklets(nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st);
   CKL();

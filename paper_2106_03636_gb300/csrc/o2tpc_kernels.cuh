@@ -44,6 +44,7 @@ struct TrackletBufs {
   uint8_t* rows; // [nTl * kMaxTlHits]
   float* state;  // [nTl * 21]  x, par[5], cov[15] at the innermost hit
   int* zref;     // [nTl]
+  int* rbase;    // [nTl]  batch-global row of pad row 0 of the tracklet's sector
 };
 void launch_tracklets(int nTl, int* workCounter, const int* starts, const int* up, const RowGrid* grid, int nRows,
                       const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st);
