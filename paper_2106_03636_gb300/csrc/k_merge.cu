@@ -220,46 +220,57 @@ __global__ void k_pair_group(MergeBufs mb, int* __restrict__ cursor) {
   mb.pairsSorted[mb.edgeStart[e] + atomicAdd(&cursor[e], 1)] = p;
 }
 
-// (chi2, a, b) order; chi2 >= 0 so its float bits order like the value.
-__device__ inline bool pair_less(const float4& x, const float4& y) {
-  const int cx = __float_as_int(x.x), cy = __float_as_int(y.x);
-  if (cx != cy) return cx < cy;
-  const int ax = __float_as_int(x.y), ay = __float_as_int(y.y);
-  if (ax != ay) return ax < ay;
-  return __float_as_int(x.z) < __float_as_int(y.z);
-}
-
-constexpr int kSelSmem = 8192;  // pairs sorted in shared memory (128 KB), a power of two
-
-struct PairLess {
-  __device__ bool operator()(const float4& x, const float4& y) const { return pair_less(x, y); }
-};
-
-// One CTA per directed edge: order its pairs (bitonic, in shared memory up to
-// kSelSmem pairs, else in the global scratch at 2 * edgeStart), then the
-// greedy selection.
-__global__ void __launch_bounds__(512) k_merge_select(MergeBufs mb, float4* __restrict__ scratch) {
-  extern __shared__ float4 sp[];
+// One CTA per directed edge: the greedy matching in ascending (chi2, a, b),
+// each track end used once, computed without ordering the pairs.  A pair
+// that is the smallest among the still-free pairs at both of its ends would
+// be taken by the sequential greedy pass as well (every smaller pair at its
+// ends lost an end to a pair taken before it), so taking all such pairs at
+// once, and repeating on the pairs whose ends are both still free, yields
+// exactly the greedy result; the smallest free pair of the edge qualifies in
+// every round, so the rounds end.  The minima use 64-bit keys: for pairs
+// sharing end a, (chi2 bits, b); for pairs sharing b, (chi2 bits, a)
+// (chi2 >= 0, so its float bits order like the value).  minA / minB are
+// indexed by track; every track end belongs to a single edge.
+__global__ void __launch_bounds__(512) k_merge_select(MergeBufs mb, unsigned long long* __restrict__ minA,
+                                                      unsigned long long* __restrict__ minB) {
   const int e = blockIdx.x;
-  const int b = mb.edgeStart[e], P = mb.edgeStart[e + 1] - b;
-  if (P == 0) return;
-  const float4* src = mb.pairsSorted + b;
-  int n2 = 1;
-  while (n2 < P) n2 <<= 1;
-  float4* buf = (n2 <= kSelSmem) ? sp : scratch + 2 * (size_t)b;
-  for (int i = threadIdx.x; i < n2; i += blockDim.x)
-    buf[i] = (i < P) ? src[i]
-                     : make_float4(__int_as_float(0x7f800000), __int_as_float(INT_MAX), __int_as_float(INT_MAX), 0.f);
-  __syncthreads();
-  cta_bitonic(buf, n2, PairLess());
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < P; ++i) {
-      const float4 p = buf[i];
-      const int a = __float_as_int(p.y), bb = __float_as_int(p.z);
-      if (mb.next[a] >= 0 || mb.prev[bb] >= 0) continue;
-      mb.next[a] = bb;
-      mb.prev[bb] = a;
+  const int b0 = mb.edgeStart[e], b1 = mb.edgeStart[e + 1];
+  if (b0 == b1) return;
+  const float4* P = mb.pairsSorted;
+  for (int round = 0; round <= b1 - b0; ++round) {
+    int alive = 0;
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+      const float4 p = P[i];
+      const int a = __float_as_int(p.y), b = __float_as_int(p.z);
+      if (mb.next[a] < 0 && mb.prev[b] < 0) {
+        minA[a] = ~0ull;
+        minB[b] = ~0ull;
+        alive = 1;
+      }
     }
+    if (!__syncthreads_or(alive)) break;
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+      const float4 p = P[i];
+      const int a = __float_as_int(p.y), b = __float_as_int(p.z);
+      if (mb.next[a] < 0 && mb.prev[b] < 0) {
+        const unsigned long long c = (unsigned long long)(unsigned)__float_as_int(p.x) << 32;
+        atomicMin(&minA[a], c | (unsigned)b);
+        atomicMin(&minB[b], c | (unsigned)a);
+      }
+    }
+    __syncthreads();
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+      const float4 p = P[i];
+      const int a = __float_as_int(p.y), b = __float_as_int(p.z);
+      if (mb.next[a] < 0 && mb.prev[b] < 0) {
+        const unsigned long long c = (unsigned long long)(unsigned)__float_as_int(p.x) << 32;
+        if (minA[a] == (c | (unsigned)b) && minB[b] == (c | (unsigned)a)) {
+          mb.next[a] = b;
+          mb.prev[b] = a;
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -473,10 +484,9 @@ void launch_merge_select(int nPairs, int nKeys, MergeBufs mb, int* scratch, cuda
     k_pair_group<<<(nPairs + 255) / 256, 256, 0, st>>>(mb, mb.edgeCnt);
     ++g_launch_count;
   }
-  size_t smem = kSelSmem * sizeof(float4);
-  cudaFuncSetAttribute(k_merge_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (nKeys > 0) {
-    k_merge_select<<<nKeys, 512, smem, st>>>(mb, mb.sortScratch);
+    auto* minA = reinterpret_cast<unsigned long long*>(mb.sortScratch);
+    k_merge_select<<<nKeys, 512, 0, st>>>(mb, minA, minA + mb.nSt);
     ++g_launch_count;
   }
 }

@@ -493,6 +493,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CK(cudaEventRecord(c->evs[7], st));
   const int nKeys = B * kNSec * 2;
   MergeBufs mb;
+  mb.nSt = nSt;
   mb.keyIn = dalloc<int>(M, nSt);
   mb.keyOut = dalloc<int>(M, nSt);
   mb.listCnt = dalloc<int>(M, nKeys + 1);

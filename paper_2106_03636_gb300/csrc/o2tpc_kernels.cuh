@@ -81,7 +81,9 @@ struct MergeBufs {
   int* pairCount;    // [1]
   int pairCap;
   float4* pairsSorted;  // [cap]
-  float4* sortScratch;  // [2 * max(cap, nSt)] padded bitonic buffers (also used as int2)
+  float4* sortScratch;  // [2 * max(cap, nSt)] padded bitonic buffers of the lists (int2);
+                        // then the per-track minima of the pair selection (2 * nSt u64)
+  int nSt;
   int* edgeCnt;      // [nKeys + 1]
   int* edgeStart;    // [nKeys + 1]
   int* next;         // [nSt]
