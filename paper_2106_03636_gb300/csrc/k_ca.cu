@@ -14,15 +14,53 @@ namespace o2tpc {
 
 constexpr int kNFCand = 4;  // candidates per side held in registers by the NeighboursFinder
 
+// Candidate residuals of one side, packed: (y_h - y_c + 1024) << 16 |
+// (z_h - z_c + 1024).  Inside the windows both halves stay in [776, 1272], so
+// the sum of an up and a down residual adds the halves without carries and
+// unpacks to (2 y_h - y_u - y_d + 2048, 2 z_h - z_u - z_d + 2048).
+__device__ inline unsigned pack_res(int dy, int dz) { return ((unsigned)(dy + 1024) << 16) | (unsigned)(dz + 1024); }
+
+// Appends the in-window candidates of one side (cells [iy0, iy1] of cell
+// rows iz0..iz1 of row g, visited in ascending sorted index) to the register
+// slots: the newest goes to slot kNFCand-1, older ones move down, so slots
+// [kNFCand - n, kNFCand) hold them in ascending index order.  Returns the
+// number found (more than kNFCand: the caller takes the general path).
+__device__ inline int nf_collect(const RowGrid& g, int iy0, int iy1, int iz0, int iz1,
+                                 const int* __restrict__ cellStart, const int2* __restrict__ syz, int2 hh,
+                                 int (&idx)[kNFCand], unsigned (&res)[kNFCand]) {
+  int n = 0;
+  for (int iz = iz0; iz <= iz1; ++iz) {
+    const int a = __ldg(cellStart + g.cellBase + iz * g.ny + iy0);
+    const int b = __ldg(cellStart + g.cellBase + iz * g.ny + iy1 + 1);
+    for (int c = a; c < b; ++c) {
+      const int2 p = __ldg(syz + c);
+      const int dy = hh.x - p.x, dz = hh.y - p.y;
+      if (abs(dy) > kWinY || abs(dz) > kWinZ) continue;
+#pragma unroll
+      for (int q = 0; q < kNFCand - 1; ++q) {
+        idx[q] = idx[q + 1];
+        res[q] = res[q + 1];
+      }
+      idx[kNFCand - 1] = c;
+      res[kNFCand - 1] = pack_res(dy, dz);
+      ++n;
+    }
+  }
+  return n;
+}
+
 // K4: one thread per hit; blocks tile the rows (nfBlockStart maps a block to
-// its row).
+// its row, looked up once per block).
 __global__ void __launch_bounds__(kNFBlock) k_neighbours(const RowGrid* __restrict__ grid,
                                                          const int* __restrict__ nfBlockStart, int nRows,
                                                          const int* __restrict__ cellStart,
                                                          const int2* __restrict__ syz, const GeomConst* __restrict__ G,
                                                          int* __restrict__ upRaw, int* __restrict__ dnRaw) {
   if ((int)blockIdx.x >= nfBlockStart[nRows]) return;  // launched with an upper bound of blocks
-  const int R = upper_bound_i32(nfBlockStart, nRows + 1, blockIdx.x) - 1;
+  __shared__ int s_row;
+  if (threadIdx.x == 0) s_row = upper_bound_i32(nfBlockStart, nRows + 1, blockIdx.x) - 1;
+  __syncthreads();
+  const int R = s_row;
   const RowGrid g = grid[R];
   const int h = g.start + (blockIdx.x - nfBlockStart[R]) * kNFBlock + threadIdx.x;
   if (h >= g.start + g.count) return;
@@ -36,81 +74,45 @@ __global__ void __launch_bounds__(kNFBlock) k_neighbours(const RowGrid* __restri
     int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
     if (cell_range(gu, npu, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, uy0, uy1, uz0, uz1) &&
         cell_range(gd, npd, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, dy0, dy1, dz0, dz1)) {
-      // Collect the in-window candidates of each side into registers (up to
-      // kNFCand each), then evaluate the pairs in one fixed, predicated loop:
-      // every lane of the warp runs the same iterations.  Lanes with more
-      // candidates take the general nested loop.  The result is the
-      // lexicographic minimum of (D, u, d) either way.
-      int ui[kNFCand], di[kNFCand];
-      int2 up_[kNFCand], dp_[kNFCand];
-      int nu = 0, nd = 0;
-      for (int izu = uz0; izu <= uz1; ++izu) {
-        const int ua = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy0);
-        const int ub = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy1 + 1);
-        for (int u = ua; u < ub; ++u) {
-          const int2 pu = __ldg(syz + u);
-          if (abs(pu.x - hh.x) > kWinY || abs(pu.y - hh.y) > kWinZ) continue;
-#pragma unroll
-          for (int q = 0; q < kNFCand; ++q)
-            if (q == nu) {
-              ui[q] = u;
-              up_[q] = pu;
-            }
-          ++nu;
-        }
-      }
-      if (nu > 0) {
-        for (int izd = dz0; izd <= dz1; ++izd) {
-          const int da = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy0);
-          const int db = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy1 + 1);
-          for (int d = da; d < db; ++d) {
-            const int2 pd = __ldg(syz + d);
-            if (abs(pd.x - hh.x) > kWinY || abs(pd.y - hh.y) > kWinZ) continue;
-#pragma unroll
-            for (int q = 0; q < kNFCand; ++q)
-              if (q == nd) {
-                di[q] = d;
-                dp_[q] = pd;
-              }
-            ++nd;
-          }
-        }
-      }
-      int bestD = INT_MAX;
-      const int y2 = 2 * hh.x, z2 = 2 * hh.y;
+      int ui[kNFCand] = {}, di[kNFCand] = {};
+      unsigned ur[kNFCand] = {}, dr[kNFCand] = {};
+      const int nu = nf_collect(gu, uy0, uy1, uz0, uz1, cellStart, syz, hh, ui, ur);
+      const int nd = nu > 0 ? nf_collect(gd, dy0, dy1, dz0, dz1, cellStart, syz, hh, di, dr) : 0;
+      // bestD starts one above the cut, so "D < bestD" also applies the cut
+      int bestD = kMaxMetric + 1;
       if (nu <= kNFCand && nd <= kNFCand) {
+        // pairs in ascending (u, d): a strict "<" keeps the first minimum,
+        // which is the lexicographic minimum of (D, u, d)
 #pragma unroll
         for (int a = 0; a < kNFCand; ++a)
 #pragma unroll
           for (int b = 0; b < kNFCand; ++b) {
-            if (a < nu && b < nd) {
-              const int ey = y2 - up_[a].x - dp_[b].x, ez = z2 - up_[a].y - dp_[b].y;
-              const int D = kWeightY * ey * ey + kWeightZ * ez * ez;
-              const int u = ui[a], d = di[b];
-              if (D <= kMaxMetric && (D < bestD || (D == bestD && (u < bu || (u == bu && d < bd))))) {
-                bestD = D;
-                bu = u;
-                bd = d;
-              }
+            const unsigned sres = ur[a] + dr[b];
+            const int ey = (int)(sres >> 16) - 2048, ez = (int)(sres & 0xFFFFu) - 2048;
+            const int D = kWeightY * ey * ey + kWeightZ * ez * ez;
+            if (a >= kNFCand - nu && b >= kNFCand - nd && D < bestD) {
+              bestD = D;
+              bu = ui[a];
+              bd = di[b];
             }
           }
       } else {
+        const int y2 = 2 * yh, z2 = 2 * zh;
         for (int izu = uz0; izu <= uz1; ++izu) {
           const int ua = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy0);
           const int ub = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy1 + 1);
           for (int u = ua; u < ub; ++u) {
             const int2 pu = __ldg(syz + u);
-            if (abs(pu.x - hh.x) > kWinY || abs(pu.y - hh.y) > kWinZ) continue;
+            if (abs(pu.x - yh) > kWinY || abs(pu.y - zh) > kWinZ) continue;
             for (int izd = dz0; izd <= dz1; ++izd) {
               const int da = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy0);
               const int db = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy1 + 1);
               for (int d = da; d < db; ++d) {
                 const int2 pd = __ldg(syz + d);
-                if (abs(pd.x - hh.x) > kWinY || abs(pd.y - hh.y) > kWinZ) continue;
+                if (abs(pd.x - yh) > kWinY || abs(pd.y - zh) > kWinZ) continue;
                 const int ey = y2 - pu.x - pd.x, ez = z2 - pu.y - pd.y;
                 const int D = kWeightY * ey * ey + kWeightZ * ez * ez;
-                if (D > kMaxMetric) continue;
-                if (D < bestD || (D == bestD && (u < bu || (u == bu && d < bd)))) {
+                if (D < bestD) {  // (u, d) visited in ascending order
                   bestD = D;
                   bu = u;
                   bd = d;

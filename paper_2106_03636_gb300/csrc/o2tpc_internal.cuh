@@ -97,10 +97,18 @@ __device__ inline int cell_iy(const RowGrid& g, int npads, int yu) {
 // Cell row of a drift coordinate: floor((v - zmin) / cz), -1 below the row's
 // range.  v - zmin can exceed the int32 range (|v|, |zmin| < 2^31), so the
 // difference and the division are unsigned.
+// The quotient is estimated in single precision and corrected by one step:
+// the estimate is within one of the true quotient for quotients up to 2^20
+// (nz never exceeds that); larger ones are clamped to nz, which callers clamp
+// further.
 __device__ inline int cell_iz_floor(int v, const RowGrid& g) {
   if (v < g.zmin) return -1;
-  const unsigned q = ((unsigned)v - (unsigned)g.zmin) / (unsigned)g.cz;
-  return q > 0x3FFFFFFFu ? 0x3FFFFFFF : (int)q;
+  const unsigned x = (unsigned)v - (unsigned)g.zmin, cz = (unsigned)g.cz, nz = (unsigned)g.nz;
+  const float qe = __fdividef((float)x, (float)cz);
+  unsigned q = qe >= (float)nz ? nz : (unsigned)qe;
+  if ((unsigned long long)q * cz > x) --q;
+  else if (q < nz && (unsigned long long)(q + 1) * cz <= x) ++q;
+  return (int)q;
 }
 
 // Cell rectangle of row g overlapping [ylo,yhi] x [zlo,zhi]; false if empty.
