@@ -54,7 +54,38 @@ STAGE_BYTES = {
     "sizes": 0.0,
     "download": 0.0,
     "host_prep": 0.0,
+    # the two following passes of the tracklet constructor (single kernels,
+    # timed apart): read the coordinates of the clusters they attach and
+    # write their indices, >= 8 + 4 bytes per cluster
+    "tl_out": 12.0,
+    "tl_in": 12.0,
 }
+# DRAM bytes (read + write) per launch that ncu measured for a kernel on a
+# workload (the launch list in profiles/launches_full_tf.md), valid while the
+# kernel's sources hash to the recorded value; otherwise the line says null.
+MEASURED_TRAFFIC = {
+    ("k_tl_out", "full_tf"): {"bytes": 7219.3e6 + 3275.5e6, "sources_sha256_16": "98cc15abef21df10",
+                              "sources": ["k_track.cu", "o2tpc_internal.cuh", "o2tpc_kernels.cuh"]},
+}
+
+
+def measured_traffic(kernel: str, workload: str):
+    import hashlib
+
+    rec = MEASURED_TRAFFIC.get((kernel, workload))
+    if rec is None:
+        return None
+    h = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, "paper_2106_03636_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes"] if h.hexdigest()[:16] == rec["sources_sha256_16"] else None
+
+
+# kernels (or single-kernel steps) the roofline line can name
+ROOF_KERNELS = {"tl_out": "k_tl_out", "tl_in": "k_tl_in", "neighbours": "k_neighbours",
+                "refit": "k_final_refit", "sort": "k_row_scatter+k_cell_sort", "selection": "k_ownership+k_segments",
+                "sector_fit": "k_sector_fit", "merge": "k_merge_*"}
 PATH_BYTES = 64.0
 
 
@@ -166,6 +197,23 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def dominant_kernel(stage, names):
+    """The longest single kernel (or single-kernel step) of a step."""
+    idx = {nm: i for i, nm in enumerate(names)}
+    cand = [(float(stage[idx[k]]), k) for k in ROOF_KERNELS]
+    ms, k = max(cand)
+    return k, ms
+
+
+def roofline(stage, names, n, peak, peak_kind, workload=None):
+    k, ms = dominant_kernel(stage, names)
+    achieved = STAGE_BYTES[k] * n / (ms / 1e3) / 1e9
+    traffic = measured_traffic(ROOF_KERNELS[k], workload) if workload else None
+    return {"bound": "hbm", "kernel": ROOF_KERNELS[k], "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+            "bytes_per_cluster": STAGE_BYTES[k], "ms_per_launch": ms}
+
+
 def device_max(ms, world, local):
     """Max over ranks of a duration (replicas; the only collective)."""
     if world == 1:
@@ -248,8 +296,6 @@ def run_chunks(args, rank, world, local):
                "mode": "batched from pinned host memory"}
     peak, peak_kind = peaks()
     names = o2tpc.STAGES
-    k = int(np.argmax(stage_b[:11]))
-    achieved = STAGE_BYTES[names[k]] * n / (stage_b[k] / 1e3) / 1e9
     line = {"metric": METRIC, "value": world * n / (ms_b / 1e3), "unit": "clusters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -260,11 +306,10 @@ def run_chunks(args, rank, world, local):
             "batched": {"value": world * n / (ms_b / 1e3), "ms_per_step": ms_b, "batch_sizes": sizes_b,
                         "gpu_launches": l_b},
             "plain": {"value": world * n / (ms_p / 1e3), "ms_per_step": ms_p, "gpu_launches": l_p,
-                      "stage_ms": {names[i]: round(float(stage_p[i]), 3) for i in range(14)}},
+                      "stage_ms": {names[i]: round(float(stage_p[i]), 3) for i in range(16)}},
             "speedup_batched_vs_plain": ms_p / ms_b,
-            "stage_ms": {names[i]: round(float(stage_b[i]), 3) for i in range(14)},
-            "roofline": {"bound": "hbm", "kernel": names[k], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind},
+            "stage_ms": {names[i]: round(float(stage_b[i]), 3) for i in range(16)},
+            "roofline": roofline(stage_b, names, n, peak, peak_kind),
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "peak": peak,
                               "frac": n / (ms_b / 1e3) * PATH_BYTES / 1e9 / peak},
             "cpu_baseline": None, "e2e": e2e, "gpu_launches": l_b, "clocks": clk.summary()}
@@ -417,7 +462,7 @@ def main():
         if args.trace:
             st = r["stats"]["ms_stage"]
             print(f"{tag}: batch {r['stats']['batch_size']} device {r['stats']['ms_device']:.2f} ms, "
-                  + ", ".join(f"{o2tpc.STAGES[i]} {st[i]:.2f}" for i in range(14)), file=sys.stderr, flush=True)
+                  + ", ".join(f"{o2tpc.STAGES[i]} {st[i]:.2f}" for i in range(16)), file=sys.stderr, flush=True)
 
     def step(location, arrays):
         r = trk.wait(trk.submit(tf, location=location, arrays=arrays))
@@ -523,16 +568,11 @@ def main():
                "p99_ms": float(np.percentile(lat_hs, 99)), "batch_sizes": sizes_hs,
                "plain": {"value": world * n / (ms_h / args.steps / 1e3), "ms_per_step": ms_h / args.steps,
                          "p50_ms": float(np.percentile(lat_h, 50)), "p99_ms": float(np.percentile(lat_h, 99)),
-                         "stage_ms": {o2tpc.STAGES[i]: round(float(stage_h[i]), 3) for i in range(14)}}}
+                         "stage_ms": {o2tpc.STAGES[i]: round(float(stage_h[i]), 3) for i in range(16)}}}
 
     peak, peak_kind = peaks()
     names = o2tpc.STAGES
-    k = int(np.argmax(stage[:11]))
-    dom = names[k]
-    achieved = STAGE_BYTES[dom] * n / (stage[k] / 1e3) / 1e9
-    roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-            "bytes_per_cluster": STAGE_BYTES[dom], "ms_per_launch": float(stage[k])}
+    roof = roofline(stage, names, n, peak, peak_kind, args.workload)
     path_frac = plain_value / world * PATH_BYTES / 1e9 / peak
 
     cpu = None
@@ -555,7 +595,7 @@ def main():
             "plain": {"value": plain_value, "tf_per_s": world / (ms_step / 1e3), "ms_per_step": ms_step,
                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                       "steps": args.steps},
-            "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(14)},
+            "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(16)},
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "frac": path_frac, "peak": peak},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_s, "clocks": clocks}
     if rank == 0:

@@ -149,8 +149,8 @@ typedef struct {
    * result copies (pinned blocks, offsets) inside step 10; 12 upload: from
    * the batch start to the start of step 0 (host-resident inputs copied in
    * the batch's own stream, descriptor tables); 13 time the batch waited for
-   * inputs that were uploaded ahead on the context's copy stream; 14-15 are
-   * reserved (zero) */
+   * inputs that were uploaded ahead on the context's copy stream; 14 and 15
+   * the outward and the inward following passes inside step 4 */
   float ms_stage[16];
 } o2tpc_stats;
 

@@ -470,15 +470,26 @@ PassGrid pass_grid() {
 }  // namespace
 
 void launch_tracklets(int nTl, int* workCounter, const int* starts, const int* up, const RowGrid* grid, int nRows,
-                      const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st) {
-  if (nTl <= 0) return;
+                      const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st,
+                      cudaEvent_t* passEnd) {
+  auto mark = [&](int i) {
+    if (passEnd) cudaEventRecord(passEnd[i], st);
+  };
+  if (nTl <= 0) {
+    for (int i = 0; i < 4; ++i) mark(i);
+    return;
+  }
   const PassGrid g = pass_grid();
   auto blocks = [&](int perSm) { return std::min((nTl + 127) / 128, g.sms * std::max(perSm, 1)); };
   cudaMemsetAsync(workCounter, 0, 4 * sizeof(int), st);
   k_tl_chain<<<blocks(g.chain), 128, 0, st>>>(nTl, workCounter, starts, up, grid, nRows, syz, G, tb);
+  mark(0);
   k_tl_out<<<blocks(g.out), 128, 0, st>>>(nTl, workCounter + 1, grid, cellStart, syz, G, tb);
+  mark(1);
   k_tl_refit<<<blocks(g.refit), 128, 0, st>>>(nTl, workCounter + 2, syz, G, tb);
+  mark(2);
   k_tl_in<<<blocks(g.in), 128, 0, st>>>(nTl, workCounter + 3, grid, cellStart, syz, G, tb);
+  mark(3);
   g_launch_count += 4;
 }
 

@@ -144,6 +144,7 @@ struct Ctx {
   int fatal = O2TPC_OK;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evWait = nullptr;
   cudaEvent_t evs[12] = {};
+  cudaEvent_t evTl[4] = {};  // ends of the four tracklet passes
   // copy stream, its thread and the bytes uploaded ahead of their batch
   cudaStream_t upStream = nullptr;
   std::thread uploader;
@@ -437,7 +438,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   tb.zref = dalloc<int>(M, nTl);
   tb.rbase = dalloc<int>(M, nTl);
   int* workCounter = dalloc<int>(M, 4);
-  launch_tracklets(nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st);
+  launch_tracklets(nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st, c->evTl);
   CKL();
 
   // ---- A9: selection
@@ -598,6 +599,8 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   for (int k = 0; k < 10; ++k) cudaEventElapsedTime(&P->stageMs[k], c->evs[k], c->evs[k + 1]);
   cudaEventElapsedTime(&P->stageMs[12], c->evWait, c->evs[0]);
   cudaEventElapsedTime(&P->stageMs[13], c->ev0, c->evWait);
+  cudaEventElapsedTime(&P->stageMs[14], c->evTl[0], c->evTl[1]);
+  cudaEventElapsedTime(&P->stageMs[15], c->evTl[2], c->evTl[3]);
   float devMs = 0.f;
   cudaEventElapsedTime(&devMs, c->ev0, c->ev1);
   const long long nLaunch = g_launch_count;
@@ -969,6 +972,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
       x->upAheadLimit = c.mem_budget / 8;
     }
     for (auto& e : x->evs) CK(cudaEventCreate(&e));
+    for (auto& e : x->evTl) CK(cudaEventCreate(&e));
     fill_geom(x->hGeom, c.bz_tesla, c.vdrift_cm_us);
     x->dGeom = static_cast<GeomConst*>(x->dev_alloc(sizeof(GeomConst)));
     CK(cudaMemcpyAsync(x->dGeom, &x->hGeom, sizeof(GeomConst), cudaMemcpyHostToDevice, x->stream));
@@ -1109,6 +1113,8 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
   cudaStreamSynchronize(c->stream);
   if (c->hStage) cudaFreeHost(c->hStage);
   for (auto& e : c->evs)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->evTl)
     if (e) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);

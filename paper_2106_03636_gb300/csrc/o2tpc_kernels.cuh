@@ -46,8 +46,11 @@ struct TrackletBufs {
   int* zref;     // [nTl]
   int* rbase;    // [nTl]  batch-global row of pad row 0 of the tracklet's sector
 };
+// passEnd: optional 4 events recorded after the chain-fit, outward, refit and
+// inward passes.
 void launch_tracklets(int nTl, int* workCounter, const int* starts, const int* up, const RowGrid* grid, int nRows,
-                      const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st);
+                      const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st,
+                      cudaEvent_t* passEnd = nullptr);
 
 struct SectorTrackBufs {
   int* tl;        // [nSt] tracklet of the sector track

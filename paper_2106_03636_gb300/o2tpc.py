@@ -86,7 +86,7 @@ class o2tpc_stats(ctypes.Structure):
     ]
 
 STAGES = ("ingest", "sort", "neighbours", "clean_starts", "tracklets", "selection", "sector_fit", "merge",
-          "refit", "sizes", "download", "host_prep", "upload", "upload_wait", "reserved14", "reserved15")
+          "refit", "sizes", "download", "host_prep", "upload", "upload_wait", "tl_out", "tl_in")
 
 
 class o2tpc_result(ctypes.Structure):
