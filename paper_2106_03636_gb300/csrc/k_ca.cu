@@ -290,9 +290,10 @@ void launch_lower_bounds(const int* list, int nList, const int* keys, int nKeys,
 
 void launch_neighbours(int nfBlocks, const RowGrid* grid, const int* nfBlockStart, int nRows, const int* cellStart,
                        const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw, cudaStream_t st) {
-  if (nfBlocks > 0)
+  if (nfBlocks > 0) {
     k_neighbours<<<nfBlocks, kNFBlock, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw);
     ++g_launch_count;
+  }
 }
 
 void launch_clean(int n, const int* upRaw, const int* dnRaw, int* up, int* dn, int* startFlag, cudaStream_t st) {

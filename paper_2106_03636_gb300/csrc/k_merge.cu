@@ -519,9 +519,10 @@ void launch_chain_counts(int nHeads, const int* heads, const SectorTrackBufs sb,
 void launch_final_refit(int nHeads, const int* heads, const SectorTrackBufs sb, MergeBufs mb, const int2* syz,
                         const int* sorig, const TFDesc* tfs, const GeomConst* G, int forceFp64, OutBufs ob,
                         cudaStream_t st) {
-  if (nHeads > 0)
+  if (nHeads > 0) {
     k_final_refit<<<(nHeads + 127) / 128, 128, 0, st>>>(nHeads, heads, sb, mb, syz, sorig, tfs, G, forceFp64, ob);
     ++g_launch_count;
+  }
 }
 
 }  // namespace o2tpc

@@ -303,46 +303,104 @@ __global__ void __launch_bounds__(128) k_tl_in(int nTl, int* __restrict__ counte
   }
 }
 
-__device__ inline int tf_of(const int* __restrict__ begin, int nTF, int k) {
-  return upper_bound_i32(begin, nTF + 1, k) - 1;
+
+// Ownership keys.  Only tracklets of the same sector can share a hit, so the
+// tie-break id is the tracklet's index within its sector (same order as the
+// index within the TF): (nHits << 24 | 2^24-1-id) in 32 bits, or the 64-bit
+// (nHits << 32 | 2^32-1-id) when a sector holds 2^24 tracklets or more.
+__device__ inline unsigned own_key32(int nh, int lid) { return ((unsigned)nh << 24) | (0xFFFFFFu - (unsigned)lid); }
+__device__ inline unsigned long long own_key64(int nh, int lid) {
+  return ((unsigned long long)(unsigned)nh << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)lid);
 }
 
-__device__ inline unsigned long long own_key(int nh, int kl) {
-  return ((unsigned long long)(unsigned)nh << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)kl);
+// First tracklet of every (TF, sector) (start hits are sorted by hit index);
+// *wide = 1 when a sector holds 2^24 tracklets or more.
+__global__ void k_sector_ranges(int nSec, const RowGrid* __restrict__ grid, const int* __restrict__ starts, int nTl,
+                                int* __restrict__ secBegin, int* __restrict__ wide) {
+  const int ts = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ts > nSec) return;
+  auto lower = [&](int key) {
+    int lo = 0, hi = nTl;
+    while (lo < hi) {
+      const int m = (lo + hi) >> 1;
+      if (starts[m] < key) lo = m + 1;
+      else hi = m;
+    }
+    return lo;
+  };
+  const int b = (ts == nSec) ? nTl : lower(grid[ts * kNRow].start);
+  secBegin[ts] = b;
+  if (ts < nSec) {
+    const int e = (ts + 1 == nSec) ? nTl : lower(grid[(ts + 1) * kNRow].start);
+    if (e - b >= (1 << 24)) atomicOr(wide, 1);
+  }
 }
 
-// K8a: hit ownership.
-__global__ void k_ownership(int nTl, const int* __restrict__ tlTfBegin, int nTF, TrackletBufs tb,
-                            unsigned long long* __restrict__ w) {
+struct OwnCtx {
+  const int* secBegin;
+  const int* wide;
+  void* w;  // unsigned[n] or unsigned long long[n]
+};
+
+// Key of tracklet k and whether hit h is owned by it.
+struct TlKey {
+  bool wide;
+  unsigned k32;
+  unsigned long long k64;
+  __device__ bool owns(const OwnCtx& o, int h) const {
+    return wide ? static_cast<const unsigned long long*>(o.w)[h] == k64 : static_cast<const unsigned*>(o.w)[h] == k32;
+  }
+};
+__device__ inline TlKey tl_key(const OwnCtx& o, const TrackletBufs& tb, int k, int nh) {
+  const int lid = k - o.secBegin[tb.rbase[k] / kNRow];
+  TlKey t;
+  t.wide = *o.wide != 0;
+  t.k32 = own_key32(nh, lid);
+  t.k64 = own_key64(nh, lid);
+  return t;
+}
+
+// K8a: hit ownership (atomicMax of the key; a hit already holding a larger
+// key is skipped without an atomic).
+__global__ void k_ownership(int nTl, OwnCtx o, TrackletBufs tb) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nTl) return;
   const int nh = tb.nhits[k];
   if (nh < kMinHits) return;
-  const int tf = tf_of(tlTfBegin, nTF, k);
-  const unsigned long long key = own_key(nh, k - tlTfBegin[tf]);
+  const TlKey key = tl_key(o, tb, k, nh);
   const int* H = tb.hits + (size_t)k * kMaxTlHits;
-  for (int i = 0; i < nh; ++i) atomicMax(&w[H[i]], key);
+  if (key.wide) {
+    auto* w = static_cast<unsigned long long*>(o.w);
+    for (int i = 0; i < nh; ++i) {
+      const int h = H[i];
+      if (w[h] < key.k64) atomicMax(&w[h], key.k64);
+    }
+  } else {
+    auto* w = static_cast<unsigned*>(o.w);
+    for (int i = 0; i < nh; ++i) {
+      const int h = H[i];
+      if (w[h] < key.k32) atomicMax(&w[h], key.k32);
+    }
+  }
 }
 
-// K8b: segments per tracklet (count pass).  Segment buffers live in local
-// memory (at most one hit per row).
-__global__ void __launch_bounds__(128) k_segments_count(int nTl, const int* __restrict__ tlTfBegin, int nTF,
-                                                        TrackletBufs tb, const unsigned long long* __restrict__ w,
-                                                        int* __restrict__ nSeg, int* __restrict__ nSegHits) {
+// K8b: segments per tracklet (count pass): owned hits in row order, split at
+// gaps of more than kMaxMiss rows, segments of >= kMinHits kept.
+__global__ void __launch_bounds__(128) k_segments_count(int nTl, OwnCtx o, TrackletBufs tb, int* __restrict__ nSeg,
+                                                        int* __restrict__ nSegHits) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nTl) return;
   const int nh = tb.nhits[k];
   int cs = 0, ch = 0;
   if (nh >= kMinHits) {
-    const int tf = tf_of(tlTfBegin, nTF, k);
-    const unsigned long long key = own_key(nh, k - tlTfBegin[tf]);
+    const TlKey key = tl_key(o, tb, k, nh);
     const int nasc = tb.nasc[k], nd = nh - nasc;
     const int* H = tb.hits + (size_t)k * kMaxTlHits;
     const uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
     int m = 0, prev = -1000;
     for (int j = 0; j < nh; ++j) {
       const int i = (j < nd) ? (nh - 1 - j) : (j - nd);
-      if (w[H[i]] != key) continue;
+      if (!key.owns(o, H[i])) continue;
       const int row = Rw[i];
       if (m > 0 && row - prev - 1 > kMaxMiss) {
         if (m >= kMinHits) { ++cs; ch += m; }
@@ -358,38 +416,33 @@ __global__ void __launch_bounds__(128) k_segments_count(int nTl, const int* __re
 }
 
 // K8c: write the sector tracks of each tracklet (ids in tracklet order).
-// A segment is staged in local memory and written only if it is kept.
-__global__ void __launch_bounds__(128) k_segments_write(int nTl, const int* __restrict__ tlTfBegin, int nTF,
-                                                        TrackletBufs tb, const unsigned long long* __restrict__ w,
+// Hits go straight to their output slots: a segment that turns out too short
+// is overwritten by the next kept one, or lies past the tracklet's last kept
+// hit and is not written (the slots of a tracklet are exactly its kept hits).
+__global__ void __launch_bounds__(128) k_segments_write(int nTl, OwnCtx o, TrackletBufs tb,
                                                         const int* __restrict__ segPos,
                                                         const int* __restrict__ segHitPos,
-                                                        const int2* __restrict__ syz, const RowGrid* __restrict__ grid,
-                                                        int nRows, SectorTrackBufs sb) {
+                                                        const int2* __restrict__ syz, SectorTrackBufs sb) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nTl) return;
   const int nh = tb.nhits[k];
   if (nh < kMinHits || segPos[k + 1] == segPos[k]) return;
-  const int tf = tf_of(tlTfBegin, nTF, k);
-  const unsigned long long key = own_key(nh, k - tlTfBegin[tf]);
+  const TlKey key = tl_key(o, tb, k, nh);
   const int nasc = tb.nasc[k], nd = nh - nasc;
   const int* H = tb.hits + (size_t)k * kMaxTlHits;
   const uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
-  const int sector = (find_row(grid, nRows, H[0]) % kRowsPerTF) / kNRow;
-  int seg[kNRow];
-  uint8_t segRow[kNRow];
+  const int ts = tb.rbase[k] / kNRow;
+  const int tf = ts / kNSec, sector = ts % kNSec;
+  const int hoEnd = segHitPos[k + 1];
   int id = segPos[k], ho = segHitPos[k];
-  int m = 0, prev = -1000;
+  int m = 0, prev = -1000, first = -1;
   auto flush = [&](void) {
     if (m >= kMinHits) {
-      for (int q = 0; q < m; ++q) {
-        sb.hits[ho + q] = seg[q];
-        sb.rows[ho + q] = segRow[q];
-      }
       sb.tl[id] = k;
       sb.tf[id] = tf;
       sb.sector[id] = sector;
       sb.off[id] = ho;
-      sb.zref[id] = syz[seg[0]].y;
+      sb.zref[id] = syz[first].y;
       ++id;
       ho += m;
     }
@@ -398,20 +451,20 @@ __global__ void __launch_bounds__(128) k_segments_write(int nTl, const int* __re
   for (int j = 0; j < nh; ++j) {
     const int i = (j < nd) ? (nh - 1 - j) : (j - nd);
     const int h = H[i];
-    if (w[h] != key) continue;
+    if (!key.owns(o, h)) continue;
     const int row = Rw[i];
     if (m > 0 && row - prev - 1 > kMaxMiss) flush();
-    seg[m] = h;
-    segRow[m] = (uint8_t)row;
+    if (m == 0) first = h;
+    if (ho + m < hoEnd) {
+      sb.hits[ho + m] = h;
+      sb.rows[ho + m] = (uint8_t)row;
+    }
     ++m;
     prev = row;
   }
   flush();
 }
 
-// K8d: outward then inward fit of every sector track.  The outward fit seeds
-// (sin phi, t, q/pT) from the tracklet's state moved to the first hit; the
-// inward fit seeds them from the outward result.
 __global__ void __launch_bounds__(128) k_sector_fit(int nSt, TrackletBufs tb, const int2* __restrict__ syz,
                                                     const GeomConst* __restrict__ G, SectorTrackBufs sb) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -493,28 +546,34 @@ void launch_tracklets(int nTl, int* workCounter, const int* starts, const int* u
   g_launch_count += 4;
 }
 
-void launch_ownership(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, unsigned long long* w, cudaStream_t st) {
+void launch_ownership(int nTl, int nSec, const RowGrid* grid, const int* starts, TrackletBufs tb, void* w,
+                      int* secBegin, int* wide, cudaStream_t st) {
+  cudaMemsetAsync(wide, 0, sizeof(int), st);
+  k_sector_ranges<<<(nSec + 1 + 127) / 128, 128, 0, st>>>(nSec, grid, starts, nTl, secBegin, wide);
+  ++g_launch_count;
   if (nTl > 0) {
-    k_ownership<<<(nTl + 127) / 128, 128, 0, st>>>(nTl, tlTfBegin, nTF, tb, w);
+    k_ownership<<<(nTl + 127) / 128, 128, 0, st>>>(nTl, OwnCtx{secBegin, wide, w}, tb);
     ++g_launch_count;
   }
 }
 
-void launch_segments_count(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, const unsigned long long* w,
-                           int* nSeg, int* nSegHits, cudaStream_t st) {
+void launch_segments_count(int nTl, const int* secBegin, const int* wide, const void* w, TrackletBufs tb, int* nSeg,
+                           int* nSegHits, cudaStream_t st) {
   if (nTl > 0) {
-    k_segments_count<<<(nTl + 127) / 128, 128, 0, st>>>(nTl, tlTfBegin, nTF, tb, w, nSeg, nSegHits);
+    k_segments_count<<<(nTl + 127) / 128, 128, 0, st>>>(nTl, OwnCtx{secBegin, wide, const_cast<void*>(w)}, tb,
+                                                         nSeg, nSegHits);
     ++g_launch_count;
   }
 }
 
-void launch_segments_write(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, const unsigned long long* w,
-                           const int* segPos, const int* segHitPos, const int2* syz, const RowGrid* grid, int nRows,
-                           SectorTrackBufs sb, cudaStream_t st) {
-  if (nTl > 0)
-    k_segments_write<<<(nTl + 127) / 128, 128, 0, st>>>(nTl, tlTfBegin, nTF, tb, w, segPos, segHitPos, syz, grid,
-                                                        nRows, sb);
+void launch_segments_write(int nTl, const int* secBegin, const int* wide, const void* w, TrackletBufs tb,
+                           const int* segPos, const int* segHitPos, const int2* syz, SectorTrackBufs sb,
+                           cudaStream_t st) {
+  if (nTl > 0) {
+    k_segments_write<<<(nTl + 127) / 128, 128, 0, st>>>(nTl, OwnCtx{secBegin, wide, const_cast<void*>(w)}, tb,
+                                                         segPos, segHitPos, syz, sb);
     ++g_launch_count;
+  }
 }
 
 void launch_sector_fit(int nSt, const TrackletBufs tb, const int2* syz, const GeomConst* G, SectorTrackBufs sb,

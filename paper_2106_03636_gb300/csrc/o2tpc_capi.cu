@@ -445,13 +445,15 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CK(cudaEventRecord(c->evs[5], st));
   unsigned long long* w = dalloc<unsigned long long>(M, n);
   CK(cudaMemsetAsync(w, 0, sizeof(unsigned long long) * std::max(n, 1), st));
-  launch_ownership(nTl, tlTfBegin, B, tb, w, st);
+  int* secBegin = dalloc<int>(M, B * kNSec + 1);
+  int* wide = dalloc<int>(M, 1);
+  launch_ownership(nTl, B * kNSec, grid, starts, tb, w, secBegin, wide, st);
   CKL();
   int* nSeg = dalloc<int>(M, nTl + 1);
   int* nSegHits = dalloc<int>(M, nTl + 1);
   int* segPos = dalloc<int>(M, nTl + 1);
   int* segHitPos = dalloc<int>(M, nTl + 1);
-  launch_segments_count(nTl, tlTfBegin, B, tb, w, nSeg, nSegHits, st);
+  launch_segments_count(nTl, secBegin, wide, w, tb, nSeg, nSegHits, st);
   CKL();
   scan_exclusive(nSeg, segPos, nTl, scratch, st);
   CKL();
@@ -473,7 +475,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   sb.rows = dalloc<uint8_t>(M, nStHits);
   sb.in = dalloc<float>(M, (size_t)nSt * 21);
   sb.out = dalloc<float>(M, (size_t)nSt * 21);
-  launch_segments_write(nTl, tlTfBegin, B, tb, w, segPos, segHitPos, syz, grid, nRows, sb, st);
+  launch_segments_write(nTl, secBegin, wide, w, tb, segPos, segHitPos, syz, sb, st);
   CKL();
   CK(cudaMemcpyAsync(sb.off + nSt, segHitPos + nTl, sizeof(int), cudaMemcpyDeviceToDevice, st));
   CK(cudaEventRecord(c->evs[6], st));

@@ -263,7 +263,20 @@ __device__ inline int kf_prop(KState<T>& s, T x2, T bzc) {
   T dy = dx * (s1 + s2) * icc;
   T chord = kf_sqrt<T>(dx * dx + dy * dy);
   T ak = fabs(k) * chord;
-  T ds = (ak < T(1e-6)) ? chord : T(2) * kf_asin<T>(T(0.5) * ak) / fabs(k);
+  // arc length 2 asin(ak/2)/|k|.  In single precision, for ak/2 = h < 0.05
+  // the Taylor series asin(h)/h = 1 + h^2/6 + 3h^4/40 + ... truncated after
+  // the h^4 term is exact to 7e-10 relative (next term 5h^6/112), below the
+  // precision of the result.  Double precision keeps asin.
+  const T h = T(0.5) * ak;
+  T ds;
+  if (sizeof(T) == 4 && h < T(0.05)) {
+    const T h2 = h * h;
+    ds = chord * (T(1) + h2 * (T(1.0 / 6.0) + h2 * T(3.0 / 40.0)));
+  } else if (ak < T(1e-6)) {
+    ds = chord;
+  } else {
+    ds = T(2) * kf_asin<T>(h) / fabs(k);
+  }
   if (dx < T(0)) ds = -ds;
   T sm = s1 + T(0.5) * k * dx;
   T cm = kf_sqrt<T>((T(1) - sm) * (T(1) + sm));

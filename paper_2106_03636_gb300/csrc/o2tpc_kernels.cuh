@@ -63,12 +63,15 @@ struct SectorTrackBufs {
   float* in;      // [nSt * 21] state at the innermost hit (inward fit)
   float* out;     // [nSt * 21] state at the outermost hit (outward fit)
 };
-void launch_ownership(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, unsigned long long* w, cudaStream_t st);
-void launch_segments_count(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, const unsigned long long* w,
-                           int* nSeg, int* nSegHits, cudaStream_t st);
-void launch_segments_write(int nTl, const int* tlTfBegin, int nTF, TrackletBufs tb, const unsigned long long* w,
-                           const int* segPos, const int* segHitPos, const int2* syz, const RowGrid* grid, int nRows,
-                           SectorTrackBufs sb, cudaStream_t st);
+// Ownership over w (n words: 32-bit keys, or 64-bit when *wide is set by the
+// sector ranges; w must hold 8 bytes per hit and start at zero).
+void launch_ownership(int nTl, int nSec, const RowGrid* grid, const int* starts, TrackletBufs tb, void* w,
+                      int* secBegin, int* wide, cudaStream_t st);
+void launch_segments_count(int nTl, const int* secBegin, const int* wide, const void* w, TrackletBufs tb, int* nSeg,
+                           int* nSegHits, cudaStream_t st);
+void launch_segments_write(int nTl, const int* secBegin, const int* wide, const void* w, TrackletBufs tb,
+                           const int* segPos, const int* segHitPos, const int2* syz, SectorTrackBufs sb,
+                           cudaStream_t st);
 void launch_sector_fit(int nSt, const TrackletBufs tb, const int2* syz, const GeomConst* G, SectorTrackBufs sb,
                        cudaStream_t st);
 
