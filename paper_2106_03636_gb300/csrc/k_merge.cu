@@ -12,6 +12,8 @@
 // final refit runs inward over each chain's clusters, rotating at sector
 // boundaries, in FP32; a track whose FP32 covariance stops being positive
 // definite after an update is redone with an FP64 covariance and counted.
+#include <algorithm>
+
 #include "o2tpc_kernels.cuh"
 
 namespace o2tpc {
@@ -319,22 +321,23 @@ __global__ void k_chain_counts(int nHeads, const int* __restrict__ heads, Sector
   trkNcl[t] = n;
 }
 
-// Inward refit over a chain (segments segs[0..nseg), hits of each ascending
-// in rows), in precision T.  y is kept relative to the origin yref (integer
-// units, the first hit fitted in the current sector frame); at a sector
-// boundary the state is made absolute, rotated, and re-referenced to the next
-// hit.  Returns flags bits 2 (stopped at a boundary) and 8 (FP32 covariance
-// lost positive definiteness); yref of the final state in *yrefOut.
+// Inward refit over a chain of sector tracks from its tail (the last of at
+// most kMaxChain segments) back to its head through the prev links, hits of
+// each segment descending in rows, in precision T.  y is kept relative to
+// the origin yref (integer units, the first hit fitted in the current sector
+// frame); at a sector boundary the state is made absolute, rotated, and
+// re-referenced to the next hit.  Returns flags bits 2 (stopped at a
+// boundary) and 8 (FP32 covariance lost positive definiteness); yref of the
+// final state in *yrefOut.
 template <typename T>
-__device__ int refit_chain(const int* segs, int nseg, const SectorTrackBufs& sb, const int2* __restrict__ syz,
-                           const GeomConst* __restrict__ G, int zref, KState<T>& t, T& chi2, int& used,
-                           int& frame, int* yrefOut) {
+__device__ int refit_chain(int head, int tail, const SectorTrackBufs& sb, const int* __restrict__ prev,
+                           const int2* __restrict__ syz, const GeomConst* __restrict__ G, int zref, KState<T>& t,
+                           T& chi2, int& used, int& frame, int* yrefOut) {
   const T zunit = sizeof(T) == 8 ? (T)G->zunit_d : (T)G->zunit;
   const T bzc = sizeof(T) == 8 ? (T)G->bzc_d : (T)G->bzc;
   const T rc = sizeof(T) == 8 ? (T)G->rot_cos_d : (T)G->rot_cos;
   const T rs = sizeof(T) == 8 ? (T)G->rot_sin_d : (T)G->rot_sin;
   const T yunit = T(1) / T(160);
-  const int tail = segs[nseg - 1];
   frame = sb.sector[tail];
   const int hl = sb.off[tail + 1] - 1;
   const float* so = sb.out + (size_t)tail * 21;
@@ -346,8 +349,7 @@ __device__ int refit_chain(const int* segs, int nseg, const SectorTrackBufs& sb,
   used = 1;
   int flags = 0;
   bool first = true;
-  for (int j = nseg - 1; j >= 0; --j) {
-    const int sg = segs[j];
+  for (int sg = tail;; sg = prev[sg]) {
     const int sec = sb.sector[sg];
     for (int i = sb.off[sg + 1] - 1; i >= sb.off[sg]; --i) {
       if (first) { first = false; continue; }
@@ -373,74 +375,95 @@ __device__ int refit_chain(const int* segs, int nseg, const SectorTrackBufs& sb,
       ++used;
       if (!kf_cov_ok<T>(t.C)) flags |= 8;
     }
+    if (sg == head) break;
   }
   *yrefOut = yref;
   return flags;
 }
 
+// Output row t of a track: state at the innermost cluster in the frame of
+// its sector, tan(lambda) = dz/ds = -side * dzeta/ds.
+template <typename T>
+__device__ void write_track(int t, const KState<T>& s, int yref, T chi2, int used, int frame, int flags, int zref,
+                            const GeomConst* __restrict__ G, OutBufs& ob) {
+  float par[5], cov[15];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) par[k] = (float)s.p[k];
+  par[0] = (float)((double)s.p[0] + (double)yref / 160.0);
+#pragma unroll
+  for (int k = 0; k < 15; ++k) cov[k] = (float)s.C[k];
+  const float sg = (frame < 18) ? -1.f : 1.f;
+  par[3] *= sg;
+#pragma unroll
+  for (int k = 0; k < 5; ++k)
+    if (k != 3) cov[ix(3, k)] *= sg;
+  ob.x[t] = (float)s.x;
+  ob.alpha[t] = G->sec_alpha[frame % 18];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) ob.par[(size_t)t * 5 + k] = par[k];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) ob.cov[(size_t)t * 15 + k] = cov[k];
+  ob.chi2[t] = (float)chi2;
+  ob.ndf[t] = 2 * used - 5;
+  ob.sector[t] = (uint8_t)frame;
+  ob.flags[t] = (uint8_t)flags;
+  ob.zref[t] = zref;
+}
+
+// Tail of a chain: the last of at most kMaxChain segments from its head.
+__device__ inline int chain_tail(int head, const int* __restrict__ next, int* nseg) {
+  int tail = head, n = 1;
+  for (int c = next[head]; c >= 0 && n < kMaxChain; c = next[c], ++n) tail = c;
+  *nseg = n;
+  return tail;
+}
+
+// K11: final refit in FP32, one thread per track; cluster list in chain
+// order, ascending rows inside each segment, as indices into the TF's
+// submitted order.  A track whose FP32 covariance stops being positive
+// definite (or every track with forceFp64) is queued for k_final_refit64.
 __global__ void __launch_bounds__(128) k_final_refit(int nHeads, const int* __restrict__ heads, SectorTrackBufs sb,
                                                      MergeBufs mb, const int2* __restrict__ syz,
                                                      const int* __restrict__ sorig, const TFDesc* __restrict__ tfs,
                                                      const GeomConst* __restrict__ G, int forceFp64, OutBufs ob) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nHeads) return;
-  int segs[kMaxChain];
-  int nseg = 0;
-  for (int c = heads[t]; c >= 0 && nseg < kMaxChain; c = mb.next[c]) segs[nseg++] = c;
-  // cluster list: segments in chain order, ascending rows inside each, as
-  // indices into the TF's submitted order
-  const int inBase = tfs[sb.tf[segs[0]]].inBase;
+  const int head = heads[t];
+  int nseg;
+  const int tail = chain_tail(head, mb.next, &nseg);
+  const int inBase = tfs[sb.tf[head]].inBase;
   int o = ob.off[t];
-  for (int j = 0; j < nseg; ++j)
-    for (int i = sb.off[segs[j]]; i < sb.off[segs[j] + 1]; ++i) ob.cl[o++] = sorig[sb.hits[i]] - inBase;
-  const int zref = syz[sb.hits[sb.off[segs[0]]]].y;
-  int flags = nseg > 1 ? 2 : 0;
-  float par[5], cov[15], x, chi2;
-  int used, frame;
+  for (int c = head, j = 0; j < nseg; c = mb.next[c], ++j)
+    for (int i = sb.off[c]; i < sb.off[c + 1]; ++i) ob.cl[o++] = sorig[sb.hits[i]] - inBase;
+  const int zref = syz[sb.hits[sb.off[head]]].y;
   KState<float> sf;
   float c2f;
-  int yref;
-  int fl = refit_chain<float>(segs, nseg, sb, syz, G, zref, sf, c2f, used, frame, &yref);
+  int used, frame, yref;
+  const int fl = refit_chain<float>(head, tail, sb, mb.prev, syz, G, zref, sf, c2f, used, frame, &yref);
   if ((fl & 8) || forceFp64) {
+    ob.fallback[atomicAdd(ob.nFallback, 1)] = t;
+    return;
+  }
+  write_track<float>(t, sf, yref, c2f, used, frame, (nseg > 1 ? 2 : 0) | (fl & 4), zref, G, ob);
+}
+
+// K11b: the queued tracks again with an FP64 covariance (flag bit 1).
+__global__ void __launch_bounds__(128) k_final_refit64(const int* __restrict__ heads, SectorTrackBufs sb, MergeBufs mb,
+                                                       const int2* __restrict__ syz, const GeomConst* __restrict__ G,
+                                                       OutBufs ob) {
+  const int nf = *ob.nFallback;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nf; q += gridDim.x * blockDim.x) {
+    const int t = ob.fallback[q];
+    const int head = heads[t];
+    int nseg;
+    const int tail = chain_tail(head, mb.next, &nseg);
+    const int zref = syz[sb.hits[sb.off[head]]].y;
     KState<double> sd;
     double c2d;
-    fl = refit_chain<double>(segs, nseg, sb, syz, G, zref, sd, c2d, used, frame, &yref);
-    x = (float)sd.x;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) par[k] = (float)sd.p[k];
-    par[0] = (float)(sd.p[0] + (double)yref / 160.0);
-#pragma unroll
-    for (int k = 0; k < 15; ++k) cov[k] = (float)sd.C[k];
-    chi2 = (float)c2d;
-    flags |= 1;
-    atomicAdd(ob.nFallback, 1);
-  } else {
-    x = sf.x;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) par[k] = sf.p[k];
-    par[0] = (float)((double)sf.p[0] + (double)yref / 160.0);
-#pragma unroll
-    for (int k = 0; k < 15; ++k) cov[k] = sf.C[k];
-    chi2 = c2f;
+    int used, frame, yref;
+    const int fl = refit_chain<double>(head, tail, sb, mb.prev, syz, G, zref, sd, c2d, used, frame, &yref);
+    write_track<double>(t, sd, yref, c2d, used, frame, 1 | (nseg > 1 ? 2 : 0) | (fl & 4), zref, G, ob);
   }
-  flags |= fl & 4;
-  // tan(lambda) = dz/ds = -side * dzeta/ds
-  const float sg = (frame < 18) ? -1.f : 1.f;
-  par[3] *= sg;
-#pragma unroll
-  for (int k = 0; k < 5; ++k)
-    if (k != 3) cov[ix(3, k)] *= sg;
-  ob.x[t] = x;
-  ob.alpha[t] = G->sec_alpha[frame % 18];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) ob.par[(size_t)t * 5 + k] = par[k];
-#pragma unroll
-  for (int k = 0; k < 15; ++k) ob.cov[(size_t)t * 15 + k] = cov[k];
-  ob.chi2[t] = chi2;
-  ob.ndf[t] = 2 * used - 5;
-  ob.sector[t] = (uint8_t)frame;
-  ob.flags[t] = (uint8_t)flags;
-  ob.zref[t] = zref;
 }
 
 // ------------------------------------------------------------- launchers
@@ -521,7 +544,14 @@ void launch_final_refit(int nHeads, const int* heads, const SectorTrackBufs sb, 
                         cudaStream_t st) {
   if (nHeads > 0) {
     k_final_refit<<<(nHeads + 127) / 128, 128, 0, st>>>(nHeads, heads, sb, mb, syz, sorig, tfs, G, forceFp64, ob);
-    ++g_launch_count;
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    k_final_refit64<<<std::min((nHeads + 127) / 128, sms * 4), 128, 0, st>>>(heads, sb, mb, syz, G, ob);
+    g_launch_count += 2;
   }
 }
 

@@ -560,6 +560,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   ob.flags = dalloc<uint8_t>(OM, nHeads);
   ob.zref = dalloc<int>(OM, nHeads);
   ob.nFallback = dalloc<int>(OM, 1);
+  ob.fallback = dalloc<int>(M, nHeads);
   CK(cudaMemsetAsync(ob.nFallback, 0, sizeof(int), st));
   launch_chain_counts(nHeads, heads, sb, mb, trkNcl, st);
   CKL();

@@ -118,6 +118,7 @@ struct OutBufs {
   uint8_t* flags;
   int* zref;
   int* nFallback;   // [1]
+  int* fallback;    // [nTrk] tracks queued for the FP64 refit
 };
 void launch_final_refit(int nHeads, const int* heads, const SectorTrackBufs sb, MergeBufs mb, const int2* syz,
                         const int* sorig, const TFDesc* tfs, const GeomConst* G, int forceFp64, OutBufs ob,
