@@ -172,6 +172,60 @@ def cpu_baseline(tf, sector: int = 0):
     return sub.n, dt
 
 
+def _oracle_sector_job(packed, bz, vdrift):
+    """One process of the multi-core oracle run: one sector's clusters."""
+    from types import SimpleNamespace
+
+    import oracle
+
+    sub = SimpleNamespace(n=len(packed), fmt=1, packed=packed, sector=None, row=None, y=None, z=None, bz=bz,
+                          vdrift=vdrift)
+    t0 = time.perf_counter()
+    oracle.run(sub, fields=["trk_off"])
+    return len(packed), time.perf_counter() - t0
+
+
+def oracle_baselines(tf):
+    """The oracle as it stands, on the GPU machine's host cores: single-threaded
+    on the single-sector frame (whole), on one sector of the 1 ms frame and on
+    one sector of the benchmark's TF; and the TF's sectors as independent
+    processes on all cores at once (one sector per process, as many sectors
+    as cores)."""
+    import multiprocessing as mp
+    from types import SimpleNamespace
+
+    import oracle
+    from paper_2106_03636_gb300 import synth
+
+    oracle.build()
+    out = {}
+    c0 = synth.single_sector()
+    t0 = time.perf_counter()
+    oracle.run(c0, fields=["trk_off"])
+    out["single_sector_whole"] = {"clusters": c0.n, "s": time.perf_counter() - t0}
+    c1 = synth.full_tpc_1ms()
+    sel = c1.sector == 0
+    sub = SimpleNamespace(n=int(sel.sum()), fmt=0, packed=None, sector=np.ascontiguousarray(c1.sector[sel]),
+                          row=np.ascontiguousarray(c1.row[sel]), y=np.ascontiguousarray(c1.y[sel]),
+                          z=np.ascontiguousarray(c1.z[sel]), bz=c1.bz, vdrift=c1.vdrift)
+    t0 = time.perf_counter()
+    oracle.run(sub, fields=["trk_off"])
+    out["full_tpc_1ms_sector0"] = {"clusters": sub.n, "s": time.perf_counter() - t0}
+    nc, dt = cpu_baseline(tf)
+    out["full_tf_sector0"] = {"clusters": nc, "s": dt}
+    cores = min(os.cpu_count() or 1, 36)
+    jobs = [np.ascontiguousarray(tf.packed[tf.packed[:, 9] == s]) for s in range(cores)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_sector_job, [(j, tf.bz, tf.vdrift) for j in jobs])
+    wall = time.perf_counter() - t0
+    out["full_tf_all_cores"] = {"clusters": int(sum(r[0] for r in res)), "s": wall, "cores": cores,
+                                "sectors": cores}
+    for v in out.values():
+        v["clusters_per_s"] = v["clusters"] / v["s"]
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -324,46 +378,60 @@ def run_serving(args, rank, world, local):
     10..570 collisions, half pp-like ~3 M clusters) arrive as a Poisson
     process from pinned host memory; at most --max-queue are admitted at
     once (an arrival that finds the server full is dropped and counted).
-    Latency = arrival -> result polled on the host."""
+    Latency = arrival -> result polled on the host.  The same arrival
+    sequence is then replayed 'plain': one TF at a time, submitted and
+    waited for, no batching and no overlap."""
     import torch
 
     from paper_2106_03636_gb300 import o2tpc, synth
 
     pool = synth.serving_pool(seed=20210611 + 1000 * rank)
     pin = [{"packed": torch.from_numpy(t.packed).pin_memory()} for t in pool]
-    trk = o2tpc.Tracker(device=local, max_inflight=args.max_queue)
-    for i in range(min(len(pool), max(args.warmup, 3))):  # warm the pools (device memory, pinned results)
-        trk.wait(trk.submit(pool[i], location=o2tpc.O2TPC_LOC_HOST, arrays=pin[i]))
     rng = np.random.default_rng(20210611 + rank)
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate_hz, int(args.rate_hz * args.serve_seconds * 2) + 10))
     arrivals = arrivals[arrivals < args.serve_seconds]
     picks = rng.integers(0, len(pool), len(arrivals))
 
-    done = collections.deque()
-    pending = collections.deque()
-    cv = threading.Condition()
-    state = {"closed": False}
+    def warm(trk):
+        for i in range(min(len(pool), max(args.warmup, 3))):  # device memory pool, pinned result blocks
+            trk.wait(trk.submit(pool[i], location=o2tpc.O2TPC_LOC_HOST, arrays=pin[i]))
 
-    def poller():
-        while True:
-            with cv:
-                cv.wait_for(lambda: pending or state["closed"])
-                if not pending:
-                    return
-                tk, t_arr, i = pending.popleft()
-            r = trk.wait(tk)
-            done.append((t_arr, time.perf_counter(), i, r["status"], r["stats"]["batch_size"]))
+    def summary(done, dropped, t0):
+        lat = np.array([1e3 * (b - a) for a, b, _, _ in done])
+        ncl = sum(pool[d[2]].n for d in done)
+        wall = max(d[1] for d in done) - t0
+        sizes = np.array([d[3] for d in done])
+        return {"value": ncl / wall, "tf_per_s": len(done) / wall, "served": int(len(done)), "dropped": int(dropped),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_batch": float(sizes.mean()), "wall_s": wall}
 
-    th = threading.Thread(target=poller, daemon=True)
-    dropped = 0
-    with ClockSampler(local) as clk:
+    def served_run():
+        trk = o2tpc.Tracker(device=local, max_inflight=args.max_queue)
+        warm(trk)
+        done, pending = [], collections.deque()
+        cv = threading.Condition()
+        state = {"closed": False}
+
+        def poller():
+            while True:
+                with cv:
+                    cv.wait_for(lambda: pending or state["closed"])
+                    if not pending:
+                        return
+                    tk, t_arr, i = pending.popleft()
+                r = trk.wait(tk)
+                if r["status"] != 0:
+                    raise RuntimeError(o2tpc.o2tpc_strerror(r["status"]))
+                done.append((t_arr, time.perf_counter(), i, r["stats"]["batch_size"]))
+
+        th = threading.Thread(target=poller, daemon=True)
         th.start()
+        dropped = 0
         t0 = time.perf_counter()
         for t_a, i in zip(arrivals, picks):
             now = time.perf_counter() - t0
             if t_a > now:
                 time.sleep(t_a - now)
-            t_arr = t0 + t_a
             try:
                 tk = trk.submit(pool[i], location=o2tpc.O2TPC_LOC_HOST, arrays=pin[i])
             except o2tpc.O2TPCError as e:
@@ -372,34 +440,54 @@ def run_serving(args, rank, world, local):
                 dropped += 1
                 continue
             with cv:
-                pending.append((tk, t_arr, i))
+                pending.append((tk, t0 + t_a, i))
                 cv.notify()
         with cv:
             state["closed"] = True
             cv.notify()
         th.join()
-    lat = np.array([1e3 * (b - a) for a, b, _, _, _ in done])
-    bad = sum(1 for d in done if d[3] != 0)
-    if bad:
-        raise RuntimeError(f"{bad} TFs failed")
-    ncl = sum(pool[d[2]].n for d in done)
-    t_end = max(d[1] for d in done)
-    wall = t_end - t0
-    sizes = np.array([d[4] for d in done])
-    line = {"metric": METRIC, "value": ncl / wall, "unit": "clusters/s", "n_gpus": world, "steps": len(done),
-            "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, len(done)), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        trk.close()
+        return summary(done, dropped, t0)
+
+    def plain_run():
+        trk = o2tpc.Tracker(device=local, flags=o2tpc.O2TPC_FLAG_NO_BATCHING)
+        warm(trk)
+        done, q = [], collections.deque()
+        dropped, j = 0, 0
+        t0 = time.perf_counter()
+        while j < len(arrivals) or q:
+            now = time.perf_counter() - t0
+            while j < len(arrivals) and arrivals[j] <= now:
+                if len(q) < args.max_queue:
+                    q.append(j)
+                else:
+                    dropped += 1
+                j += 1
+            if not q:
+                time.sleep(max(0.0, arrivals[j] - now))
+                continue
+            a = q.popleft()
+            r = trk.wait(trk.submit(pool[picks[a]], location=o2tpc.O2TPC_LOC_HOST, arrays=pin[picks[a]]))
+            if r["status"] != 0:
+                raise RuntimeError(o2tpc.o2tpc_strerror(r["status"]))
+            done.append((t0 + arrivals[a], time.perf_counter(), picks[a], 1))
+        trk.close()
+        return summary(done, dropped, t0)
+
+    with ClockSampler(local) as clk:
+        srv = served_run()
+        pln = plain_run()
+    line = {"metric": METRIC, "value": srv["value"], "unit": "clusters/s", "n_gpus": world, "steps": srv["served"],
+            "warmup": args.warmup, "ms_per_step": 1e3 * srv["wall_s"] / max(1, srv["served"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving_pool24_poisson", "rate_hz": args.rate_hz,
                        "arrival_window_s": args.serve_seconds, "max_queue": args.max_queue,
                        "pool_clusters": [int(t.n) for t in pool], "format": "fixed12",
                        "input": "pinned host memory", "parallelism": f"replicas x{world}"},
-            "offered": int(len(arrivals)), "served": int(len(done)), "dropped": int(dropped),
-            "tf_per_s": len(done) / wall, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_batch": float(sizes.mean()),
-            "wall_s": wall, "clocks": clk.summary()}
+            "offered": int(len(arrivals)), "tf_per_s": srv["tf_per_s"], "p50_ms": srv["p50_ms"],
+            "p99_ms": srv["p99_ms"], "served": srv, "plain": pln, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    trk.close()
 
 
 def main():
@@ -577,9 +665,11 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and tf.fmt == 1:
-        nc, dt = cpu_baseline(tf)
-        cpu = {"value": nc / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
-               "sample": f"sector 0 of the same TF: {nc} clusters, {dt:.1f} s"}
+        ob = oracle_baselines(tf)
+        s0 = ob["full_tf_sector0"]
+        cpu = {"value": s0["clusters_per_s"], "unit": "clusters/s", "cores": 1, "kind": "oracle",
+               "sample": f"sector 0 of the same TF: {s0['clusters']} clusters, {s0['s']:.1f} s",
+               "configs": ob}
 
     cfg.update({"clusters": int(n), "tracks": int(r["n_tracks"]), "l2": "inputs larger than L2 (no flush)",
                 "mode": f"served: continuous batching, {args.inflight} TFs in flight (TF replayed from memory)",

@@ -107,8 +107,9 @@ typedef struct {
   void (*dev_free)(void* ptr, void* user);
   void* alloc_user;
   void* stream;            /* cudaStream_t to run on, or NULL for a library stream    */
-  uint64_t batch_full_clusters; /* clusters that fill the GPU: a batch holding this
-                              many takes no further TF (0: 2^25; UINT64_MAX: only
+  uint64_t batch_full_clusters; /* clusters that fill the GPU: a TF joins a batch
+                              only if the batch stays within this many clusters (a
+                              larger TF runs alone) (0: 2^25; UINT64_MAX: only
                               max_batch and mem_budget limit a batch)                 */
 } o2tpc_config;
 

@@ -35,9 +35,9 @@ namespace {
 constexpr int kTileMin = 65536;           // clusters per ingest tile, at least
 constexpr int kTilesPerTFMax = 4096;
 constexpr uint64_t kMaxBatchHits = 2000000000ull;
-// Default for o2tpc_config::batch_full_clusters: a batch that already holds
-// this many clusters fills the GPU, more TFs would only add latency, so it
-// stops taking them (they wait, uploaded ahead).
+// Default for o2tpc_config::batch_full_clusters: this many clusters fill the
+// GPU; larger batches would only add latency (the TFs left out wait, uploaded
+// ahead).
 constexpr uint64_t kBatchFullHits = 1ull << 25;
 
 struct CudaError {
@@ -795,8 +795,11 @@ void worker_main(Ctx* c) {
       const int maxB = (c->cfg.flags & O2TPC_FLAG_NO_BATCHING) ? 1 : c->cfg.max_batch;
       while (!c->queue.empty() && (int)batch.size() < maxB) {
         auto& j = c->queue.front();
+        // a TF joins only if the batch stays within the size that fills the
+        // GPU: small TFs share batches, a large one runs alone and never
+        // holds small ones back (FIFO order kept: stop at the first misfit)
         if (!batch.empty() && (fp + j->footprint > c->cfg.mem_budget || hits + j->tf.n > kMaxBatchHits ||
-                               hits >= c->cfg.batch_full_clusters))
+                               hits + j->tf.n > c->cfg.batch_full_clusters))
           break;
         fp += j->footprint;
         hits += j->tf.n;
