@@ -294,8 +294,9 @@ def run_chunks(args, rank, world, local):
     n = sum(c.n for c in chunks)
     dev = [{"packed": torch.from_numpy(c.packed).to(f"cuda:{local}")} for c in chunks]
     torch.cuda.synchronize()
-    plain = o2tpc.Tracker(device=local, flags=o2tpc.O2TPC_FLAG_NO_BATCHING)
-    batched = o2tpc.Tracker(device=local, max_batch=len(chunks), batch_full_clusters=2**64 - 1)
+    tune = 0 if args.no_autotune else o2tpc.O2TPC_FLAG_AUTOTUNE
+    plain = o2tpc.Tracker(device=local, flags=o2tpc.O2TPC_FLAG_NO_BATCHING | tune)
+    batched = o2tpc.Tracker(device=local, max_batch=len(chunks), batch_full_clusters=2**64 - 1, flags=tune)
 
     def pass_plain(loc=o2tpc.O2TPC_LOC_DEVICE, arrays=dev):
         out = []
@@ -366,7 +367,8 @@ def run_chunks(args, rank, world, local):
             "roofline": roofline(stage_b, names, n, peak, peak_kind),
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "peak": peak,
                               "frac": n / (ms_b / 1e3) * PATH_BYTES / 1e9 / peak},
-            "cpu_baseline": None, "e2e": e2e, "gpu_launches": l_b, "clocks": clk.summary()}
+            "cpu_baseline": None, "e2e": e2e, "gpu_launches": l_b, "clocks": clk.summary(),
+            "autotune": {"batched": batched.tuning(), "plain": plain.tuning()}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plain.close()
@@ -504,6 +506,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--trace", action="store_true", help="per-TF stage times on stderr")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
     ap.add_argument("--torch-memory", action="store_true",
                     help="device buffers from PyTorch's caching allocator (no uploads ahead)")
     ap.add_argument("--inflight", type=int, default=3, help="TFs kept in flight in the served measurement")
@@ -543,7 +546,8 @@ def main():
             dev[k] = torch.from_numpy(getattr(tf, k)).to(f"cuda:{local}")
     torch.cuda.synchronize()
 
-    trk = o2tpc.Tracker(device=local, torch_memory=args.torch_memory)
+    tune = 0 if args.no_autotune else o2tpc.O2TPC_FLAG_AUTOTUNE
+    trk = o2tpc.Tracker(device=local, torch_memory=args.torch_memory, flags=tune)
     st = trk.stream
 
     def trace(tag, r):
@@ -687,7 +691,8 @@ def main():
                       "steps": args.steps},
             "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(16)},
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "frac": path_frac, "peak": peak},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_s, "clocks": clocks}
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_s, "clocks": clocks,
+            "autotune": trk.tuning()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     trk.close()

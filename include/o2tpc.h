@@ -81,8 +81,12 @@ enum {
   O2TPC_FLAG_KEEP_STAGES = 1u << 0, /* keep per-step device arrays until release,
                                        readable with o2tpc_get_stage          */
   O2TPC_FLAG_NO_BATCHING = 1u << 1, /* run every TF alone (one TF per batch)  */
-  O2TPC_FLAG_FORCE_FP64 = 1u << 2   /* take the FP64 covariance path in the final
+  O2TPC_FLAG_FORCE_FP64 = 1u << 2,  /* take the FP64 covariance path in the final
                                        refit for every track (testing aid)     */
+  O2TPC_FLAG_AUTOTUNE = 1u << 3     /* on the first batch of >= 2^20 clusters,
+                                       time the launch shapes of the tunable
+                                       steps on that batch and keep the fastest
+                                       (see o2tpc_get_tuning)                  */
 };
 
 typedef struct {
@@ -111,7 +115,25 @@ typedef struct {
                               only if the batch stays within this many clusters (a
                               larger TF runs alone) (0: 2^25; UINT64_MAX: only
                               max_batch and mem_budget limit a batch)                 */
+  /* Launch shapes (0: default, or the autotuner's choice with
+   * O2TPC_FLAG_AUTOTUNE).  Results never depend on them. */
+  int32_t nf_hits_per_block;     /* NeighboursFinder: hits (threads) per block of a
+                                    pad row: 64, 128 (default) or 256             */
+  int32_t sort_threads_per_row;  /* cell sort: threads per pad row: 128, 256
+                                    (default) or 512                              */
 } o2tpc_config;
+
+/* Launch shapes in use and, once the autotuner has run, its timings (device
+ * ms of each candidate on the batch it tuned on; candidates in the order
+ * listed above). */
+typedef struct {
+  int32_t tuned;                 /* 1 once the autotuner has chosen               */
+  int32_t nf_hits_per_block;
+  int32_t sort_threads_per_row;
+  int32_t tuned_on_clusters;     /* size of the batch it tuned on                 */
+  float nf_ms[3];
+  float sort_ms[3];
+} o2tpc_tuning;
 
 typedef struct {
   uint64_t n;              /* clusters (may be 0)                                      */
@@ -236,6 +258,11 @@ const char* o2tpc_strerror(int32_t status);
  */
 int o2tpc_get_stage(o2tpc_ctx* ctx, uint64_t ticket, const char* name, void* dst, uint64_t capacity,
                     uint64_t* needed);
+
+/* Current launch shapes and autotuner timings (see o2tpc_tuning).  The paper
+ * has no counterpart: its block shapes are fixed per GPU model.  Returns
+ * O2TPC_OK or O2TPC_EINVAL. */
+int o2tpc_get_tuning(o2tpc_ctx* ctx, o2tpc_tuning* out);
 
 /* Allocation-free grid binning and stable sort of one TF.
  *

@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(512) k_row_scatter(const TFDesc* __restrict__ 
 // most kSmemCells cells, else in the global scratch (cellStart itself).
 constexpr int kSmemCells = 12288;
 
-__global__ void __launch_bounds__(256) k_cell_sort(const RowGrid* __restrict__ grid, const int4* __restrict__ bucket,
+template <int kT>
+__global__ void __launch_bounds__(kT) k_cell_sort(const RowGrid* __restrict__ grid, const int4* __restrict__ bucket,
                                                    int* __restrict__ cellStart, int2* __restrict__ syz,
                                                    int* __restrict__ sorig, int* __restrict__ gscratch) {
   __shared__ int s_cnt[kSmemCells];
@@ -243,8 +244,8 @@ __global__ void __launch_bounds__(256) k_cell_sort(const RowGrid* __restrict__ g
   for (int c0 = 0; c0 < nc; c0 += blockDim.x) {
     int c = c0 + threadIdx.x;
     int v = (c < nc) ? cnt[c] : 0;
-    // warp + block scan for 256 threads
-    __shared__ int ws[8];
+    // warp + block scan (up to 1024 threads)
+    __shared__ int ws[32];
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int x = v;
 #pragma unroll
@@ -325,9 +326,14 @@ void launch_row_scatter(const TFDesc* tfs, const int2* tiles, int nTiles, int ti
 }
 
 void launch_cell_sort(int nRows, const RowGrid* grid, const int4* bucket, int* cellStart, int2* syz, int* sorig,
-                      int* gscratch, const int* totals, cudaStream_t st) {
+                      int* gscratch, const int* totals, cudaStream_t st, int threadsPerRow) {
   if (nRows > 0) {
-    k_cell_sort<<<nRows, 256, 0, st>>>(grid, bucket, cellStart, syz, sorig, gscratch);
+    if (threadsPerRow == 128)
+      k_cell_sort<128><<<nRows, 128, 0, st>>>(grid, bucket, cellStart, syz, sorig, gscratch);
+    else if (threadsPerRow == 512)
+      k_cell_sort<512><<<nRows, 512, 0, st>>>(grid, bucket, cellStart, syz, sorig, gscratch);
+    else
+      k_cell_sort<256><<<nRows, 256, 0, st>>>(grid, bucket, cellStart, syz, sorig, gscratch);
     ++g_launch_count;
   }
   k_cell_sentinel<<<1, 1, 0, st>>>(cellStart, totals);

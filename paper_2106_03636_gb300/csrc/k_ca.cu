@@ -49,9 +49,11 @@ __device__ inline int nf_collect(const RowGrid& g, int iy0, int iy1, int iz0, in
   return n;
 }
 
-// K4: one thread per hit; blocks tile the rows (nfBlockStart maps a block to
-// its row, looked up once per block).
-__global__ void __launch_bounds__(kNFBlock) k_neighbours(const RowGrid* __restrict__ grid,
+// K4: one thread per hit; blocks of kB hits tile the rows
+// (nfBlockStart, built for the same block size, maps a block to its row,
+// looked up once per block).
+template <int kB>
+__global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ grid,
                                                          const int* __restrict__ nfBlockStart, int nRows,
                                                          const int* __restrict__ cellStart,
                                                          const int2* __restrict__ syz, const GeomConst* __restrict__ G,
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(kNFBlock) k_neighbours(const RowGrid* __restri
   __syncthreads();
   const int R = s_row;
   const RowGrid g = grid[R];
-  const int h = g.start + (blockIdx.x - nfBlockStart[R]) * kNFBlock + threadIdx.x;
+  const int h = g.start + (blockIdx.x - nfBlockStart[R]) * kB + threadIdx.x;
   if (h >= g.start + g.count) return;
   const int r = (R % kRowsPerTF) % kNRow;
   int bu = -1, bd = -1;
@@ -288,10 +290,16 @@ void launch_lower_bounds(const int* list, int nList, const int* keys, int nKeys,
   }
 }
 
-void launch_neighbours(int nfBlocks, const RowGrid* grid, const int* nfBlockStart, int nRows, const int* cellStart,
-                       const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw, cudaStream_t st) {
+void launch_neighbours(int nfBlocks, int hitsPerBlock, const RowGrid* grid, const int* nfBlockStart, int nRows,
+                       const int* cellStart, const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw,
+                       cudaStream_t st) {
   if (nfBlocks > 0) {
-    k_neighbours<<<nfBlocks, kNFBlock, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw);
+    if (hitsPerBlock == 64)
+      k_neighbours<64><<<nfBlocks, 64, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw);
+    else if (hitsPerBlock == 256)
+      k_neighbours<256><<<nfBlocks, 256, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw);
+    else
+      k_neighbours<128><<<nfBlocks, 128, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw);
     ++g_launch_count;
   }
 }

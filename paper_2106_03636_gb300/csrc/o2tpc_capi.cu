@@ -145,6 +145,7 @@ struct Ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evWait = nullptr;
   cudaEvent_t evs[12] = {};
   cudaEvent_t evTl[4] = {};  // ends of the four tracklet passes
+  o2tpc_tuning tune{};       // launch shapes in use (autotuner results)
   // copy stream, its thread and the bytes uploaded ahead of their batch
   cudaStream_t upStream = nullptr;
   std::thread uploader;
@@ -296,6 +297,64 @@ void fill_geom(GeomConst& g, double bz, double vd) {
 }
 
 // ------------------------------------------------------------ the batch
+// Autotuner: the cell sort and the NeighboursFinder are pure functions of
+// their inputs, so every candidate launch shape is timed on the batch at hand
+// (cell sort: best of two runs; CUDA events on the compute stream) and the fastest
+// is kept for this and later batches.  The last cell-sort run leaves the same
+// arrays as any other; the grid's block map is rebuilt for the chosen NF
+// shape before the real NeighboursFinder launch.
+void autotune(Ctx* c, int n, int nRows, const int* rowCnt, const int* rowMin, const int* rowMax, RowGrid* grid,
+              int* nfBlockStart, int* totals, const int4* bucket, int* cellStart, int2* syz, int* sorig,
+              int* gscratch) {
+  cudaStream_t st = c->stream;
+  const GeomConst* G = c->dGeom;
+  static const int kSort[3] = {128, 256, 512};
+  static const int kNF[3] = {64, 128, 256};
+  cudaEvent_t es[3][3], en[3][2];
+  for (auto& r : es)
+    for (auto& e : r) CK(cudaEventCreate(&e));
+  for (auto& r : en)
+    for (auto& e : r) CK(cudaEventCreate(&e));
+  // scratch links for the timing runs of the NeighboursFinder
+  int* up = static_cast<int*>(c->dev_alloc(sizeof(int) * (size_t)n * 2));
+  for (int i = 0; i < 3; ++i) {
+    CK(cudaEventRecord(es[i][0], st));
+    launch_cell_sort(nRows, grid, bucket, cellStart, syz, sorig, gscratch, totals, st, kSort[i]);
+    CK(cudaEventRecord(es[i][1], st));
+    launch_cell_sort(nRows, grid, bucket, cellStart, syz, sorig, gscratch, totals, st, kSort[i]);
+    CK(cudaEventRecord(es[i][2], st));
+  }
+  for (int i = 0; i < 3; ++i) {
+    launch_grid(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, kNF[i], totals, st);
+    const int blocks = n / kNF[i] + nRows + 1;
+    CK(cudaEventRecord(en[i][0], st));
+    launch_neighbours(blocks, kNF[i], grid, nfBlockStart, nRows, cellStart, syz, G, up, up + n, st);
+    CK(cudaEventRecord(en[i][1], st));
+  }
+  CK(cudaEventSynchronize(en[2][1]));
+  c->dev_free(up);
+  int bs = 0, bn = 0;
+  for (int i = 0; i < 3; ++i) {
+    float a = 0.f, b = 0.f, m = 0.f;
+    cudaEventElapsedTime(&a, es[i][0], es[i][1]);
+    cudaEventElapsedTime(&b, es[i][1], es[i][2]);
+    c->tune.sort_ms[i] = std::min(a, b);
+    cudaEventElapsedTime(&m, en[i][0], en[i][1]);
+    c->tune.nf_ms[i] = m;
+    if (c->tune.sort_ms[i] < c->tune.sort_ms[bs]) bs = i;
+    if (c->tune.nf_ms[i] < c->tune.nf_ms[bn]) bn = i;
+  }
+  for (auto& r : es)
+    for (auto& e : r) cudaEventDestroy(e);
+  for (auto& r : en)
+    for (auto& e : r) cudaEventDestroy(e);
+  c->tune.sort_threads_per_row = kSort[bs];
+  c->tune.nf_hits_per_block = kNF[bn];
+  c->tune.tuned = 1;
+  c->tune.tuned_on_clusters = n;
+  launch_grid(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, c->tune.nf_hits_per_block, totals, st);
+}
+
 void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   cudaStream_t st = c->stream;
   const bool keep = (c->cfg.flags & O2TPC_FLAG_KEEP_STAGES) != 0;
@@ -387,7 +446,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CKL();
   launch_row_reduce(dTF, B, tileStats, rowCnt, rowMin, rowMax, st);
   CKL();
-  launch_grid(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, kNFBlock, totals, st);
+  launch_grid(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, c->tune.nf_hits_per_block, totals, st);
   CKL();
   const long long cellsMax = (long long)n / kHitsPerCell + 46ll * nRows + 1;
   CK(cudaEventRecord(c->evs[1], st));
@@ -398,7 +457,9 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   int* sorig = dalloc<int>(M, n);
   launch_row_scatter(dTF, dTiles, nTiles, tileSize, G, tileStats, grid, bucket, st);
   CKL();
-  launch_cell_sort(nRows, grid, bucket, cellStart, syz, sorig, gscratch, totals, st);
+  launch_cell_sort(nRows, grid, bucket, cellStart, syz, sorig, gscratch, totals, st, c->tune.sort_threads_per_row);
+  if ((c->cfg.flags & O2TPC_FLAG_AUTOTUNE) && !c->tune.tuned && n >= (1 << 20))
+    autotune(c, n, nRows, rowCnt, rowMin, rowMax, grid, nfBlockStart, totals, bucket, cellStart, syz, sorig, gscratch);
   CKL();
 
   // ---- A5-A7: neighbours, cleaner, start hits
@@ -410,8 +471,9 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   int* flag = dalloc<int>(M, n + 1);
   int* pos = dalloc<int>(M, n + 1);
   int* scratch = dalloc<int>(M, scan_scratch_ints((long long)n + 8) + (nRows + 8) * 2 / 4096 + 64);
-  const int nfBlocksMax = n / kNFBlock + nRows + 1;
-  launch_neighbours(nfBlocksMax, grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw, st);
+  const int nfB = c->tune.nf_hits_per_block;
+  const int nfBlocksMax = n / nfB + nRows + 1;
+  launch_neighbours(nfBlocksMax, nfB, grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw, st);
   CKL();
   CK(cudaEventRecord(c->evs[3], st));
   launch_clean(n, upRaw, dnRaw, up, dn, flag, st);
@@ -937,6 +999,11 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
   if (c.max_inflight <= 0) c.max_inflight = 64;
   if (c.max_batch <= 0) c.max_batch = 64;
   if (c.batch_full_clusters == 0) c.batch_full_clusters = kBatchFullHits;
+  if (c.nf_hits_per_block == 0) c.nf_hits_per_block = kNFBlock;
+  if (c.sort_threads_per_row == 0) c.sort_threads_per_row = 256;
+  if ((c.nf_hits_per_block != 64 && c.nf_hits_per_block != 128 && c.nf_hits_per_block != 256) ||
+      (c.sort_threads_per_row != 128 && c.sort_threads_per_row != 256 && c.sort_threads_per_row != 512))
+    return O2TPC_EINVAL;
   if (!(c.vdrift_cm_us > 0.0) || !std::isfinite(c.bz_tesla)) return O2TPC_EINVAL;
   if ((c.dev_alloc == nullptr) != (c.dev_free == nullptr)) return O2TPC_EINVAL;
   int ndev = 0;
@@ -947,6 +1014,8 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
   auto* x = new (std::nothrow) Ctx();
   if (!x) return O2TPC_ENOMEM;
   x->cfg = c;
+  x->tune.nf_hits_per_block = c.nf_hits_per_block;
+  x->tune.sort_threads_per_row = c.sort_threads_per_row;
   x->traceCopies = std::getenv("O2TPC_TRACE_COPIES") != nullptr;
   x->traceMode = x->traceCopies ? std::atoi(std::getenv("O2TPC_TRACE_COPIES")) : 0;
   try {
@@ -1043,6 +1112,14 @@ int o2tpc_submit_many(o2tpc_ctx* ctx, const o2tpc_tf* tfs, uint32_t n, uint64_t*
 int o2tpc_submit_tf(o2tpc_ctx* ctx, const o2tpc_tf* tf, uint64_t* ticket) {
   if (!ctx || !tf || !ticket) return O2TPC_EINVAL;
   return o2tpc_submit_many(ctx, tf, 1, ticket);
+}
+
+int o2tpc_get_tuning(o2tpc_ctx* ctx, o2tpc_tuning* out) {
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  if (!c || !out) return O2TPC_EINVAL;
+  std::lock_guard<std::mutex> lk(c->mu);
+  *out = c->tune;
+  return O2TPC_OK;
 }
 
 int o2tpc_poll(o2tpc_ctx* ctx, uint64_t ticket, int32_t timeout_ms, const o2tpc_result** out) {

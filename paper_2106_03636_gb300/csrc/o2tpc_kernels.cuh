@@ -11,7 +11,7 @@ namespace o2tpc {
 // Kernels launched by the calling host thread (each launcher adds its own).
 extern thread_local long long g_launch_count;
 
-constexpr int kNFBlock = 128;      // hits per NeighboursFinder block
+constexpr int kNFBlock = 128;      // default hits per NeighboursFinder block
 constexpr int kMaxTlHits = kNRow;  // hit slots per tracklet
 
 // k_bin.cu
@@ -24,10 +24,11 @@ void launch_grid(int nRows, const int* rowCnt, const int* rowMin, const int* row
 void launch_row_scatter(const TFDesc* tfs, const int2* tiles, int nTiles, int tileSize, const GeomConst* G,
                         const int* tileStats, const RowGrid* grid, int4* bucket, cudaStream_t st);
 void launch_cell_sort(int nRows, const RowGrid* grid, const int4* bucket, int* cellStart, int2* syz, int* sorig,
-                      int* gscratch, const int* totals, cudaStream_t st);
+                      int* gscratch, const int* totals, cudaStream_t st,
+                      int threadsPerRow = 256);
 
 // k_ca.cu
-void launch_neighbours(int nfBlocks, const RowGrid* grid, const int* nfBlockStart, int nRows, const int* cellStart,
+void launch_neighbours(int nfBlocks, int hitsPerBlock, const RowGrid* grid, const int* nfBlockStart, int nRows, const int* cellStart,
                        const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw, cudaStream_t st);
 void launch_clean(int n, const int* upRaw, const int* dnRaw, int* up, int* dn, int* startFlag, cudaStream_t st);
 int scan_scratch_ints(long long n);

@@ -32,6 +32,7 @@ O2TPC_LOC_HOST = 0
 O2TPC_LOC_DEVICE = 1
 
 O2TPC_FLAG_KEEP_STAGES = 1 << 0
+O2TPC_FLAG_AUTOTUNE = 1 << 3
 O2TPC_FLAG_NO_BATCHING = 1 << 1
 O2TPC_FLAG_FORCE_FP64 = 1 << 2
 
@@ -53,6 +54,19 @@ class o2tpc_config(ctypes.Structure):
         ("alloc_user", ctypes.c_void_p),
         ("stream", ctypes.c_void_p),
         ("batch_full_clusters", ctypes.c_uint64),
+        ("nf_hits_per_block", ctypes.c_int32),
+        ("sort_threads_per_row", ctypes.c_int32),
+    ]
+
+
+class o2tpc_tuning(ctypes.Structure):
+    _fields_ = [
+        ("tuned", ctypes.c_int32),
+        ("nf_hits_per_block", ctypes.c_int32),
+        ("sort_threads_per_row", ctypes.c_int32),
+        ("tuned_on_clusters", ctypes.c_int32),
+        ("nf_ms", ctypes.c_float * 3),
+        ("sort_ms", ctypes.c_float * 3),
     ]
 
 
@@ -145,6 +159,8 @@ def load(build: bool = True) -> ctypes.CDLL:
         lib.o2tpc_sort_tf_static.restype = ctypes.c_int
         lib.o2tpc_sort_tf_static.argtypes = [ctypes.POINTER(o2tpc_tf), ctypes.c_double, vp, vp, vp, vp,
                                              ctypes.c_uint64, vp]
+        lib.o2tpc_get_tuning.restype = ctypes.c_int
+        lib.o2tpc_get_tuning.argtypes = [vp, ctypes.POINTER(o2tpc_tuning)]
         lib.o2tpc_get_stage.restype = ctypes.c_int
         lib.o2tpc_get_stage.argtypes = [vp, ctypes.c_uint64, ctypes.c_char_p, vp, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_uint64)]
@@ -170,6 +186,12 @@ def o2tpc_submit_many(ctx, tfs: list):
     t = (ctypes.c_uint64 * len(tfs))()
     rc = load().o2tpc_submit_many(ctx, arr, len(tfs), t)
     return rc, list(t)
+
+
+def o2tpc_get_tuning(ctx):
+    t = o2tpc_tuning()
+    rc = load().o2tpc_get_tuning(ctx, ctypes.byref(t))
+    return rc, t
 
 
 def o2tpc_poll(ctx, ticket: int, timeout_ms: int):
@@ -266,7 +288,7 @@ class Tracker:
 
     def __init__(self, device: int = 0, bz: float = 0.5, vdrift: float = 2.58, flags: int = 0,
                  mem_budget: int = 0, max_inflight: int = 0, max_batch: int = 0, torch_memory: bool = False,
-                 batch_full_clusters: int = 0):
+                 batch_full_clusters: int = 0, nf_hits_per_block: int = 0, sort_threads_per_row: int = 0):
         self.cfg = o2tpc_config()
         self.cfg.device = device
         self.cfg.bz_tesla = bz
@@ -276,6 +298,8 @@ class Tracker:
         self.cfg.max_inflight = max_inflight
         self.cfg.max_batch = max_batch
         self.cfg.batch_full_clusters = batch_full_clusters
+        self.cfg.nf_hits_per_block = nf_hits_per_block
+        self.cfg.sort_threads_per_row = sort_threads_per_row
         self._keep = []
         import torch
 
@@ -359,6 +383,14 @@ class Tracker:
     def release(self, ticket: int, result: dict) -> None:
         o2tpc_result_release(self.ctx, result["_res"])
         self._pending.pop(ticket, None)
+
+    def tuning(self) -> dict:
+        rc, t = o2tpc_get_tuning(self.ctx)
+        if rc != O2TPC_OK:
+            raise O2TPCError(rc, "o2tpc_get_tuning")
+        return {"tuned": bool(t.tuned), "nf_hits_per_block": t.nf_hits_per_block,
+                "sort_threads_per_row": t.sort_threads_per_row, "tuned_on_clusters": t.tuned_on_clusters,
+                "nf_ms": list(t.nf_ms), "sort_ms": list(t.sort_ms)}
 
     def stage(self, ticket: int, name: str) -> np.ndarray:
         rc, need = o2tpc_get_stage(self.ctx, ticket, name, None, 0)

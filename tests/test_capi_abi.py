@@ -18,7 +18,7 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for n in ("o2tpc_create", "o2tpc_submit_tf", "o2tpc_submit_many", "o2tpc_poll", "o2tpc_destroy", "o2tpc_result_release",
-              "o2tpc_strerror", "o2tpc_get_stage"):
+              "o2tpc_strerror", "o2tpc_get_stage", "o2tpc_get_tuning"):
         assert n in names
 
 
@@ -37,5 +37,7 @@ def test_binding_structures_match_header_sizes():
     # 64-bit layout of the C structs as the header defines them
     assert ctypes.sizeof(o2tpc.o2tpc_tf) == 8 + 4 + 4 + 5 * 8 + 8
     assert ctypes.sizeof(o2tpc.o2tpc_stats) == 5 * 8 + 4 * 4 + 8 + 16 * 4
-    # device, budget, inflight, batch, bz, vdrift, flags(+pad), 2 callbacks, user, stream, batch_full
-    assert ctypes.sizeof(o2tpc.o2tpc_config) == 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 * 4 + 8
+    # device, budget, inflight, batch, bz, vdrift, flags(+pad), 2 callbacks, user, stream, batch_full,
+    # two launch shapes
+    assert ctypes.sizeof(o2tpc.o2tpc_config) == 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 * 4 + 8 + 4 + 4
+    assert ctypes.sizeof(o2tpc.o2tpc_tuning) == 4 * 4 + 6 * 4

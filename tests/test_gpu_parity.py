@@ -175,3 +175,27 @@ def test_submit_many_is_all_or_nothing():
         tickets = t.submit_many(tfs[:2])
         rs = [t.wait(k) for k in tickets]
         assert all(r["status"] == 0 and r["n_tracks"] > 10 for r in rs)
+
+
+def test_launch_shapes_and_autotuner_leave_results_unchanged():
+    """The tunable launch shapes (NeighboursFinder hits per block, cell-sort
+    threads per row) and the autotuner's choice change no result bit."""
+    tf = synth.full_tpc_1ms(seed=21, n_coll=3)
+    assert tf.n >= 1 << 20
+    keys = ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref")
+    with o2tpc.Tracker() as a:
+        ref = a.track(tf)
+        assert a.tuning()["tuned"] is False
+    with o2tpc.Tracker(nf_hits_per_block=64, sort_threads_per_row=512) as b:
+        other = b.track(tf)
+    with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_AUTOTUNE) as c:
+        tuned = c.track(tf)
+        t = c.tuning()
+    assert t["tuned"] and t["tuned_on_clusters"] == tf.n
+    assert t["nf_hits_per_block"] in (64, 128, 256) and t["sort_threads_per_row"] in (128, 256, 512)
+    assert all(v > 0 for v in t["nf_ms"] + t["sort_ms"])
+    for r in (other, tuned):
+        for k in keys:
+            assert np.array_equal(ref[k], r[k]), k
+    with pytest.raises(o2tpc.O2TPCError):
+        o2tpc.Tracker(nf_hits_per_block=100)
