@@ -132,10 +132,10 @@ __global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ g
 
 // K5 + K6a: reciprocity filter on the raw (snapshot) links and the chain-head
 // flag: dn < 0, up >= 0, up[up] >= 0 (chains of at least three hits).
-__global__ void k_clean(int n, const int* __restrict__ upRaw, const int* __restrict__ dnRaw, int* __restrict__ up,
-                        int* __restrict__ dn, int* __restrict__ startFlag) {
+__global__ void k_clean(const int* __restrict__ nDev, const int* __restrict__ upRaw, const int* __restrict__ dnRaw,
+                        int* __restrict__ up, int* __restrict__ dn, int* __restrict__ startFlag) {
   int h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= n) return;
+  if (h >= *nDev) return;
   int u = upRaw[h], d = dnRaw[h];
   int uc = (u >= 0 && dnRaw[u] == h) ? u : -1;
   int dc = (d >= 0 && upRaw[d] == h) ? d : -1;
@@ -180,7 +180,9 @@ __device__ inline int block_excl(int v, int* total) {
   return incl - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int* __restrict__ in, int n, int* __restrict__ sums) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int* __restrict__ in, const int* __restrict__ nDev,
+                                                            int* __restrict__ sums) {
+  const int n = *nDev;
   long long base = (long long)blockIdx.x * kScanTile;
   int s = 0;
 #pragma unroll
@@ -206,8 +208,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_mid(int* __restrict__ sum
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restrict__ in, int n,
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restrict__ in, const int* __restrict__ nDev,
                                                              const int* __restrict__ sums, int* __restrict__ out) {
+  const int n = *nDev;
   long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
   int v[kScanItems];
   int s = 0;
@@ -228,35 +231,68 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restri
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = off;
 }
 
-// out[0..n] = exclusive scan of in[0..n-1], out[n] = total; out may alias in.
+// out[0..m] = exclusive scan of in[0..m-1], out[m] = total, m = *nDev <= n
+// (the grid covers n; tiles past m add zeros); out may alias in.
 // scratch: >= scan_scratch_ints(n) ints.
 int scan_scratch_ints(long long n) { return (int)((n + kScanTile - 1) / kScanTile) + 1; }
 
-void scan_exclusive(const int* in, int* out, int n, int* scratch, cudaStream_t st) {
+__global__ void k_store_zero_at(int* __restrict__ out, const int* __restrict__ nDev) { out[*nDev] = 0; }
+
+void scan_exclusive(const int* in, int* out, int n, const int* nDev, int* scratch, cudaStream_t st) {
   int nb = (n + kScanTile - 1) / kScanTile;
   if (nb == 0) {
-    cudaMemsetAsync(out, 0, sizeof(int), st);
+    k_store_zero_at<<<1, 1, 0, st>>>(out, nDev);
+    ++g_launch_count;
     return;
   }
-  k_scan_sums<<<nb, kScanThreads, 0, st>>>(in, n, scratch);
+  k_scan_sums<<<nb, kScanThreads, 0, st>>>(in, nDev, scratch);
   ++g_launch_count;
   k_scan_mid<<<1, kScanThreads, 0, st>>>(scratch, nb);
   ++g_launch_count;
-  k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, n, scratch, out);
+  k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, nDev, scratch, out);
   ++g_launch_count;
 }
 
-// ordered compaction: out[pos[i]] = i for flag[i] != 0 (pos = exclusive scan)
-__global__ void k_compact(int n, const int* __restrict__ flag, const int* __restrict__ pos, int* __restrict__ out) {
+// ordered compaction: out[pos[i]] = i for flag[i] != 0 (pos = exclusive
+// scan), i < *nDev; entries past the capacity are dropped and flagged
+__global__ void k_compact(const int* __restrict__ nDev, const int* __restrict__ flag, const int* __restrict__ pos,
+                          int* __restrict__ out, int cap, int* __restrict__ overflow) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && flag[i]) out[pos[i]] = i;
+  if (i < *nDev && flag[i]) {
+    const int p = pos[i];
+    if (p < cap) out[p] = i;
+    else *overflow = 1;
+  }
+}
+
+// *dst = min(arr[*idx], cap) (a count read off the end of a scan), flagging
+// an overflow; optionally also writes the count at base[*dst] (CSR end).
+__global__ void k_count_at(const int* __restrict__ arr, const int* __restrict__ idx, int* __restrict__ dst, int cap,
+                           int* __restrict__ overflow, const int* __restrict__ arr2, int* __restrict__ dst2, int cap2,
+                           int* __restrict__ endBase) {
+  int v = arr[*idx];
+  if (v > cap) {
+    v = cap;
+    *overflow = 1;
+  }
+  *dst = v;
+  if (arr2) {
+    int v2 = arr2[*idx];
+    if (v2 > cap2) {
+      v2 = cap2;
+      *overflow = 1;
+    }
+    *dst2 = v2;
+    if (endBase) endBase[v] = v2;
+  }
 }
 
 // first entry of a sorted list that is >= each TF's first sorted hit
-__global__ void k_tf_ranges(int nTF, const RowGrid* __restrict__ grid, const int* __restrict__ list, int nList,
-                            int* __restrict__ tfBegin) {
+__global__ void k_tf_ranges(int nTF, const RowGrid* __restrict__ grid, const int* __restrict__ list,
+                            const int* __restrict__ nListDev, int* __restrict__ tfBegin) {
   int tf = blockIdx.x * blockDim.x + threadIdx.x;
   if (tf > nTF) return;
+  const int nList = *nListDev;
   int key = (tf == nTF) ? INT_MAX : grid[tf * kRowsPerTF].start;
   int lo = 0, hi = nList;
   while (lo < hi) {
@@ -268,10 +304,11 @@ __global__ void k_tf_ranges(int nTF, const RowGrid* __restrict__ grid, const int
 }
 
 // out[i] = first index of the sorted list with list[j] >= keys[i]
-__global__ void k_lower_bounds(const int* __restrict__ list, int nList, const int* __restrict__ keys, int nKeys,
-                               int* __restrict__ out) {
+__global__ void k_lower_bounds(const int* __restrict__ list, const int* __restrict__ nListDev,
+                               const int* __restrict__ keys, int nKeys, int* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nKeys) return;
+  const int nList = *nListDev;
   const int key = keys[i];
   int lo = 0, hi = nList;
   while (lo < hi) {
@@ -283,9 +320,10 @@ __global__ void k_lower_bounds(const int* __restrict__ list, int nList, const in
 }
 
 // ------------------------------------------------------------- launchers
-void launch_lower_bounds(const int* list, int nList, const int* keys, int nKeys, int* out, cudaStream_t st) {
+void launch_lower_bounds(const int* list, const int* nListDev, const int* keys, int nKeys, int* out,
+                         cudaStream_t st) {
   if (nKeys > 0) {
-    k_lower_bounds<<<(nKeys + 127) / 128, 128, 0, st>>>(list, nList, keys, nKeys, out);
+    k_lower_bounds<<<(nKeys + 127) / 128, 128, 0, st>>>(list, nListDev, keys, nKeys, out);
     ++g_launch_count;
   }
 }
@@ -304,22 +342,43 @@ void launch_neighbours(int nfBlocks, int hitsPerBlock, const RowGrid* grid, cons
   }
 }
 
-void launch_clean(int n, const int* upRaw, const int* dnRaw, int* up, int* dn, int* startFlag, cudaStream_t st) {
+void launch_clean(int n, const int* nDev, const int* upRaw, const int* dnRaw, int* up, int* dn, int* startFlag,
+                  cudaStream_t st) {
   if (n > 0) {
-    k_clean<<<(n + 255) / 256, 256, 0, st>>>(n, upRaw, dnRaw, up, dn, startFlag);
+    k_clean<<<(n + 255) / 256, 256, 0, st>>>(nDev, upRaw, dnRaw, up, dn, startFlag);
     ++g_launch_count;
   }
 }
 
-void launch_compact(int n, const int* flag, const int* pos, int* out, cudaStream_t st) {
+void launch_compact(int n, const int* nDev, const int* flag, const int* pos, int* out, int cap, int* overflow,
+                    cudaStream_t st) {
   if (n > 0) {
-    k_compact<<<(n + 255) / 256, 256, 0, st>>>(n, flag, pos, out);
+    k_compact<<<(n + 255) / 256, 256, 0, st>>>(nDev, flag, pos, out, cap, overflow);
     ++g_launch_count;
   }
 }
 
-void launch_tf_ranges(int nTF, const RowGrid* grid, const int* list, int nList, int* tfBegin, cudaStream_t st) {
-  k_tf_ranges<<<(nTF + 1 + 63) / 64, 64, 0, st>>>(nTF, grid, list, nList, tfBegin);
+__global__ void k_iota(int* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = i;
+}
+
+void launch_iota(int* out, int n, cudaStream_t st) {
+  if (n > 0) {
+    k_iota<<<(n + 255) / 256, 256, 0, st>>>(out, n);
+    ++g_launch_count;
+  }
+}
+
+void launch_count_at(const int* arr, const int* idx, int* dst, int cap, int* overflow, cudaStream_t st,
+                     const int* arr2, int* dst2, int cap2, int* endBase) {
+  k_count_at<<<1, 1, 0, st>>>(arr, idx, dst, cap, overflow, arr2, dst2, cap2, endBase);
+  ++g_launch_count;
+}
+
+void launch_tf_ranges(int nTF, const RowGrid* grid, const int* list, const int* nListDev, int* tfBegin,
+                      cudaStream_t st) {
+  k_tf_ranges<<<(nTF + 1 + 63) / 64, 64, 0, st>>>(nTF, grid, list, nListDev, tfBegin);
   ++g_launch_count;
 }
 

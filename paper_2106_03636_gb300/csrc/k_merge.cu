@@ -22,9 +22,9 @@ __device__ inline int nb_sector(int s, int d) { return (s / 18) * 18 + (s % 18 +
 
 // Keys: inner end of a border track -> B-list key (tf*36 + sector)*2 + (dir>0);
 // outer end -> the edge key of the same form for its own sector.
-__global__ void k_merge_keys(int nSt, SectorTrackBufs sb, const GeomConst* __restrict__ G, MergeBufs mb) {
+__global__ void k_merge_keys(SectorTrackBufs sb, const GeomConst* __restrict__ G, MergeBufs mb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nSt) return;
+  if (i >= mb.cnt->nSt) return;
   const float tn = G->tan10;
   const float* so = sb.out + (size_t)i * 21;
   const float* si = sb.in + (size_t)i * 21;
@@ -48,10 +48,10 @@ __device__ inline int zeta_units(int zref, float zrel, float zunit) {
   return zref + (int)lrintf(fminf(fmaxf(zrel / zunit, -1.0e9f), 1.0e9f));
 }
 
-__global__ void k_merge_list_fill(int nSt, SectorTrackBufs sb, const GeomConst* __restrict__ G, MergeBufs mb,
+__global__ void k_merge_list_fill(SectorTrackBufs sb, const GeomConst* __restrict__ G, MergeBufs mb,
                                   int* __restrict__ cursor) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nSt) return;
+  if (i >= mb.cnt->nSt) return;
   const int k = mb.keyIn[i];
   if (k < 0) return;
   const int slot = mb.listStart[k] + atomicAdd(&cursor[k], 1);
@@ -137,10 +137,10 @@ __device__ inline bool chi2_5(const float* d, const float* M, float& out) {
 }
 
 // One thread per outer border end A: all B candidates of the neighbour edge.
-__global__ void __launch_bounds__(128) k_merge_pairs(int nSt, SectorTrackBufs sb, const GeomConst* __restrict__ G,
+__global__ void __launch_bounds__(128) k_merge_pairs(SectorTrackBufs sb, const GeomConst* __restrict__ G,
                                                      MergeBufs mb, unsigned* __restrict__ err) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= nSt) return;
+  if (a >= mb.cnt->nSt) return;
   const int ko = mb.keyOut[a];
   if (ko < 0) return;
   const int d = (ko & 1) ? 1 : -1;
@@ -277,7 +277,8 @@ __global__ void __launch_bounds__(512) k_merge_select(MergeBufs mb, unsigned lon
 }
 
 // Chains: mark every track reachable from a head (prev < 0).
-__global__ void k_chain_reach(int nSt, MergeBufs mb) {
+__global__ void k_chain_reach(MergeBufs mb) {
+  const int nSt = mb.cnt->nSt;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nSt || mb.prev[i] >= 0) return;
   int guard = 0;
@@ -289,7 +290,8 @@ __global__ void k_chain_reach(int nSt, MergeBufs mb) {
 // kernel) finds whether it is the loop's smallest member, which marks itself.
 // The next kernel cuts the link into every marked track, so each loop is cut
 // exactly once, whatever the thread order.
-__global__ void k_chain_loops(int nSt, MergeBufs mb) {
+__global__ void k_chain_loops(MergeBufs mb) {
+  const int nSt = mb.cnt->nSt;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nSt || mb.reached[i]) return;
   int mn = i, guard = 0;
@@ -297,7 +299,8 @@ __global__ void k_chain_loops(int nSt, MergeBufs mb) {
   if (mn == i) mb.reached[i] = 2;
 }
 
-__global__ void k_chain_loops_fix(int nSt, MergeBufs mb) {
+__global__ void k_chain_loops_fix(MergeBufs mb) {
+  const int nSt = mb.cnt->nSt;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nSt || mb.reached[i] != 2) return;
   const int p = mb.prev[i];
@@ -305,17 +308,19 @@ __global__ void k_chain_loops_fix(int nSt, MergeBufs mb) {
   mb.prev[i] = -1;
 }
 
-__global__ void k_head_flags(int nSt, MergeBufs mb, int* __restrict__ headFlag) {
+__global__ void k_head_flags(MergeBufs mb, int* __restrict__ headFlag) {
+  const int nSt = mb.cnt->nSt;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nSt) headFlag[i] = mb.prev[i] < 0;
 }
 
 constexpr int kMaxChain = 64;  // segments per chain, at most
 
-__global__ void k_chain_counts(int nHeads, const int* __restrict__ heads, SectorTrackBufs sb, MergeBufs mb,
+__global__ void k_chain_counts(const int* __restrict__ nHeadsDev, const int* __restrict__ heads, SectorTrackBufs sb,
+                               MergeBufs mb,
                                int* __restrict__ trkNcl) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nHeads) return;
+  if (t >= *nHeadsDev) return;
   int n = 0, nseg = 0;
   for (int c = heads[t]; c >= 0 && nseg < kMaxChain; c = mb.next[c], ++nseg) n += sb.off[c + 1] - sb.off[c];
   trkNcl[t] = n;
@@ -422,12 +427,13 @@ __device__ inline int chain_tail(int head, const int* __restrict__ next, int* ns
 // order, ascending rows inside each segment, as indices into the TF's
 // submitted order.  A track whose FP32 covariance stops being positive
 // definite (or every track with forceFp64) is queued for k_final_refit64.
-__global__ void __launch_bounds__(128) k_final_refit(int nHeads, const int* __restrict__ heads, SectorTrackBufs sb,
+__global__ void __launch_bounds__(128) k_final_refit(const int* __restrict__ nHeadsDev, const int* __restrict__ heads,
+                                                     SectorTrackBufs sb,
                                                      MergeBufs mb, const int2* __restrict__ syz,
                                                      const int* __restrict__ sorig, const TFDesc* __restrict__ tfs,
                                                      const GeomConst* __restrict__ G, int forceFp64, OutBufs ob) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nHeads) return;
+  if (t >= *nHeadsDev) return;
   const int head = heads[t];
   int nseg;
   const int tail = chain_tail(head, mb.next, &nseg);
@@ -467,17 +473,19 @@ __global__ void __launch_bounds__(128) k_final_refit64(const int* __restrict__ h
 }
 
 // ------------------------------------------------------------- launchers
+// nSt, nKeys, nPairs, nHeads below size the grids (exact or capacities); the
+// kernels read the sizes from mb.cnt / nHeadsDev.
 void launch_merge_keys(int nSt, const SectorTrackBufs sb, const GeomConst* G, MergeBufs mb, int nKeys, int* scratch,
                        cudaStream_t st) {
   cudaMemsetAsync(mb.listCnt, 0, sizeof(int) * (nKeys + 1), st);
   if (nSt > 0) {
-    k_merge_keys<<<(nSt + 255) / 256, 256, 0, st>>>(nSt, sb, G, mb);
+    k_merge_keys<<<(nSt + 255) / 256, 256, 0, st>>>(sb, G, mb);
     ++g_launch_count;
   }
-  scan_exclusive(mb.listCnt, mb.listStart, nKeys, scratch, st);
+  scan_exclusive(mb.listCnt, mb.listStart, nKeys, &mb.cnt->nKeys, scratch, st);
   cudaMemsetAsync(mb.listCnt, 0, sizeof(int) * (nKeys + 1), st);
   if (nSt > 0) {
-    k_merge_list_fill<<<(nSt + 255) / 256, 256, 0, st>>>(nSt, sb, G, mb, mb.listCnt);
+    k_merge_list_fill<<<(nSt + 255) / 256, 256, 0, st>>>(sb, G, mb, mb.listCnt);
     ++g_launch_count;
   }
   if (nKeys > 0) {
@@ -490,7 +498,7 @@ void launch_merge_pairs(int nSt, const SectorTrackBufs sb, const GeomConst* G, M
                         cudaStream_t st) {
   cudaMemsetAsync(mb.pairCount, 0, sizeof(int), st);
   if (nSt > 0) {
-    k_merge_pairs<<<(nSt + 127) / 128, 128, 0, st>>>(nSt, sb, G, mb, err);
+    k_merge_pairs<<<(nSt + 127) / 128, 128, 0, st>>>(sb, G, mb, err);
     ++g_launch_count;
   }
 }
@@ -501,7 +509,7 @@ void launch_merge_select(int nPairs, int nKeys, MergeBufs mb, int* scratch, cuda
     k_pair_hist<<<(nPairs + 255) / 256, 256, 0, st>>>(mb);
     ++g_launch_count;
   }
-  scan_exclusive(mb.edgeCnt, mb.edgeStart, nKeys, scratch, st);
+  scan_exclusive(mb.edgeCnt, mb.edgeStart, nKeys, &mb.cnt->nKeys, scratch, st);
   cudaMemsetAsync(mb.edgeCnt, 0, sizeof(int) * (nKeys + 1), st);
   if (nPairs > 0) {
     k_pair_group<<<(nPairs + 255) / 256, 256, 0, st>>>(mb, mb.edgeCnt);
@@ -514,36 +522,30 @@ void launch_merge_select(int nPairs, int nKeys, MergeBufs mb, int* scratch, cuda
   }
 }
 
-void launch_chains(int nSt, int nTF, const int* stTfBegin, MergeBufs mb, int* headFlag, cudaStream_t st) {
-  (void)nTF;
-  (void)stTfBegin;
+void launch_chains(int nSt, MergeBufs mb, int* headFlag, cudaStream_t st) {
   if (nSt > 0) {
-    k_chain_reach<<<(nSt + 255) / 256, 256, 0, st>>>(nSt, mb);
-    ++g_launch_count;
-    k_chain_loops<<<(nSt + 255) / 256, 256, 0, st>>>(nSt, mb);
-    ++g_launch_count;
-    k_chain_loops_fix<<<(nSt + 255) / 256, 256, 0, st>>>(nSt, mb);
-    ++g_launch_count;
+    k_chain_reach<<<(nSt + 255) / 256, 256, 0, st>>>(mb);
+    k_chain_loops<<<(nSt + 255) / 256, 256, 0, st>>>(mb);
+    k_chain_loops_fix<<<(nSt + 255) / 256, 256, 0, st>>>(mb);
+    k_head_flags<<<(nSt + 255) / 256, 256, 0, st>>>(mb, headFlag);
+    g_launch_count += 4;
   }
-  if (nSt > 0) {
-    k_head_flags<<<(nSt + 255) / 256, 256, 0, st>>>(nSt, mb, headFlag);
+}
+
+void launch_chain_counts(int nHeads, const int* nHeadsDev, const int* heads, const SectorTrackBufs sb, MergeBufs mb,
+                         int* trkNcl, cudaStream_t st) {
+  if (nHeads > 0) {
+    k_chain_counts<<<(nHeads + 255) / 256, 256, 0, st>>>(nHeadsDev, heads, sb, mb, trkNcl);
     ++g_launch_count;
   }
 }
 
-void launch_chain_counts(int nHeads, const int* heads, const SectorTrackBufs sb, MergeBufs mb, int* trkNcl,
-                         cudaStream_t st) {
+void launch_final_refit(int nHeads, const int* nHeadsDev, const int* heads, const SectorTrackBufs sb, MergeBufs mb,
+                        const int2* syz, const int* sorig, const TFDesc* tfs, const GeomConst* G, int forceFp64,
+                        OutBufs ob, cudaStream_t st) {
   if (nHeads > 0) {
-    k_chain_counts<<<(nHeads + 255) / 256, 256, 0, st>>>(nHeads, heads, sb, mb, trkNcl);
-    ++g_launch_count;
-  }
-}
-
-void launch_final_refit(int nHeads, const int* heads, const SectorTrackBufs sb, MergeBufs mb, const int2* syz,
-                        const int* sorig, const TFDesc* tfs, const GeomConst* G, int forceFp64, OutBufs ob,
-                        cudaStream_t st) {
-  if (nHeads > 0) {
-    k_final_refit<<<(nHeads + 127) / 128, 128, 0, st>>>(nHeads, heads, sb, mb, syz, sorig, tfs, G, forceFp64, ob);
+    k_final_refit<<<(nHeads + 127) / 128, 128, 0, st>>>(nHeadsDev, heads, sb, mb, syz, sorig, tfs, G, forceFp64,
+                                                         ob);
     static int sms = 0;
     if (sms == 0) {
       int dev = 0;

@@ -124,11 +124,12 @@ __device__ inline void load_state(KState<float>& s, const float* src) {
 
 // (a) chain fit: seed from the first and third chain hits, then one update
 // per chain hit.  A transport failure drops the tracklet.
-__global__ void __launch_bounds__(128) k_tl_chain(int nTl, int* __restrict__ counter, const int* __restrict__ starts,
+__global__ void __launch_bounds__(128) k_tl_chain(const int* __restrict__ nTlDev, int* __restrict__ counter, const int* __restrict__ starts,
                                                   const int* __restrict__ up, const RowGrid* __restrict__ grid,
                                                   int nRows, const int2* __restrict__ syz,
                                                   const GeomConst* __restrict__ G, TrackletBufs tb) {
   const float zunit = G->zunit, bzc = G->bzc;
+  const int nTl = *nTlDev;
   for (;;) {
     const int k = atomicAdd(counter, 1);
     if (k >= nTl) return;
@@ -221,11 +222,12 @@ __device__ inline int follow(KState<float>& st, float (*s_last)[128], int r, int
 // (b) outward following above the chain; then the refit's starting state:
 // the last accepted state with the position of the top hit and a fresh
 // covariance.
-__global__ void __launch_bounds__(128) k_tl_out(int nTl, int* __restrict__ counter, const RowGrid* __restrict__ grid,
+__global__ void __launch_bounds__(128) k_tl_out(const int* __restrict__ nTlDev, int* __restrict__ counter, const RowGrid* __restrict__ grid,
                                                 const int* __restrict__ cellStart, const int2* __restrict__ syz,
                                                 const GeomConst* __restrict__ G, TrackletBufs tb) {
   __shared__ float s_last[21][128];
   const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
+  const int nTl = *nTlDev;
   for (;;) {
     const int k = atomicAdd(counter, 1);
     if (k >= nTl) return;
@@ -252,9 +254,10 @@ __global__ void __launch_bounds__(128) k_tl_out(int nTl, int* __restrict__ count
 
 // (c) inward refit from the top hit through every attached hit; a hit whose
 // transport fails is skipped.
-__global__ void __launch_bounds__(128) k_tl_refit(int nTl, int* __restrict__ counter, const int2* __restrict__ syz,
+__global__ void __launch_bounds__(128) k_tl_refit(const int* __restrict__ nTlDev, int* __restrict__ counter, const int2* __restrict__ syz,
                                                   const GeomConst* __restrict__ G, TrackletBufs tb) {
   const float zunit = G->zunit, bzc = G->bzc;
+  const int nTl = *nTlDev;
   for (;;) {
     const int k = atomicAdd(counter, 1);
     if (k >= nTl) return;
@@ -278,11 +281,12 @@ __global__ void __launch_bounds__(128) k_tl_refit(int nTl, int* __restrict__ cou
 
 // (d) inward following below the chain start; the state kept is the one at
 // the innermost accepted hit.
-__global__ void __launch_bounds__(128) k_tl_in(int nTl, int* __restrict__ counter, const RowGrid* __restrict__ grid,
+__global__ void __launch_bounds__(128) k_tl_in(const int* __restrict__ nTlDev, int* __restrict__ counter, const RowGrid* __restrict__ grid,
                                                const int* __restrict__ cellStart, const int2* __restrict__ syz,
                                                const GeomConst* __restrict__ G, TrackletBufs tb) {
   __shared__ float s_last[21][128];
   const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
+  const int nTl = *nTlDev;
   for (;;) {
     const int k = atomicAdd(counter, 1);
     if (k >= nTl) return;
@@ -315,10 +319,11 @@ __device__ inline unsigned long long own_key64(int nh, int lid) {
 
 // First tracklet of every (TF, sector) (start hits are sorted by hit index);
 // *wide = 1 when a sector holds 2^24 tracklets or more.
-__global__ void k_sector_ranges(int nSec, const RowGrid* __restrict__ grid, const int* __restrict__ starts, int nTl,
-                                int* __restrict__ secBegin, int* __restrict__ wide) {
+__global__ void k_sector_ranges(int nSec, const RowGrid* __restrict__ grid, const int* __restrict__ starts,
+                                const int* __restrict__ nTlDev, int* __restrict__ secBegin, int* __restrict__ wide) {
   const int ts = blockIdx.x * blockDim.x + threadIdx.x;
   if (ts > nSec) return;
+  const int nTl = *nTlDev;
   auto lower = [&](int key) {
     int lo = 0, hi = nTl;
     while (lo < hi) {
@@ -362,9 +367,9 @@ __device__ inline TlKey tl_key(const OwnCtx& o, const TrackletBufs& tb, int k, i
 
 // K8a: hit ownership (atomicMax of the key; a hit already holding a larger
 // key is skipped without an atomic).
-__global__ void k_ownership(int nTl, OwnCtx o, TrackletBufs tb) {
+__global__ void k_ownership(const int* __restrict__ nTlDev, OwnCtx o, TrackletBufs tb) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nTl) return;
+  if (k >= *nTlDev) return;
   const int nh = tb.nhits[k];
   if (nh < kMinHits) return;
   const TlKey key = tl_key(o, tb, k, nh);
@@ -386,10 +391,10 @@ __global__ void k_ownership(int nTl, OwnCtx o, TrackletBufs tb) {
 
 // K8b: segments per tracklet (count pass): owned hits in row order, split at
 // gaps of more than kMaxMiss rows, segments of >= kMinHits kept.
-__global__ void __launch_bounds__(128) k_segments_count(int nTl, OwnCtx o, TrackletBufs tb, int* __restrict__ nSeg,
-                                                        int* __restrict__ nSegHits) {
+__global__ void __launch_bounds__(128) k_segments_count(const int* __restrict__ nTlDev, OwnCtx o, TrackletBufs tb,
+                                                        int* __restrict__ nSeg, int* __restrict__ nSegHits) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nTl) return;
+  if (k >= *nTlDev) return;
   const int nh = tb.nhits[k];
   int cs = 0, ch = 0;
   if (nh >= kMinHits) {
@@ -419,12 +424,13 @@ __global__ void __launch_bounds__(128) k_segments_count(int nTl, OwnCtx o, Track
 // Hits go straight to their output slots: a segment that turns out too short
 // is overwritten by the next kept one, or lies past the tracklet's last kept
 // hit and is not written (the slots of a tracklet are exactly its kept hits).
-__global__ void __launch_bounds__(128) k_segments_write(int nTl, OwnCtx o, TrackletBufs tb,
+__global__ void __launch_bounds__(128) k_segments_write(const int* __restrict__ nTlDev, OwnCtx o, TrackletBufs tb,
                                                         const int* __restrict__ segPos,
                                                         const int* __restrict__ segHitPos,
-                                                        const int2* __restrict__ syz, SectorTrackBufs sb) {
+                                                        const int2* __restrict__ syz, SectorTrackBufs sb, int capSt,
+                                                        int capHits) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nTl) return;
+  if (k >= *nTlDev) return;
   const int nh = tb.nhits[k];
   if (nh < kMinHits || segPos[k + 1] == segPos[k]) return;
   const TlKey key = tl_key(o, tb, k, nh);
@@ -433,16 +439,19 @@ __global__ void __launch_bounds__(128) k_segments_write(int nTl, OwnCtx o, Track
   const uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
   const int ts = tb.rbase[k] / kNRow;
   const int tf = ts / kNSec, sector = ts % kNSec;
-  const int hoEnd = segHitPos[k + 1];
+  // the slots end at the tracklet's last kept hit, and at the capacity
+  const int hoEnd = min(segHitPos[k + 1], capHits);
   int id = segPos[k], ho = segHitPos[k];
   int m = 0, prev = -1000, first = -1;
   auto flush = [&](void) {
     if (m >= kMinHits) {
-      sb.tl[id] = k;
-      sb.tf[id] = tf;
-      sb.sector[id] = sector;
-      sb.off[id] = ho;
-      sb.zref[id] = syz[first].y;
+      if (id < capSt) {
+        sb.tl[id] = k;
+        sb.tf[id] = tf;
+        sb.sector[id] = sector;
+        sb.off[id] = min(ho, capHits);
+        sb.zref[id] = syz[first].y;
+      }
       ++id;
       ho += m;
     }
@@ -465,10 +474,11 @@ __global__ void __launch_bounds__(128) k_segments_write(int nTl, OwnCtx o, Track
   flush();
 }
 
-__global__ void __launch_bounds__(128) k_sector_fit(int nSt, TrackletBufs tb, const int2* __restrict__ syz,
-                                                    const GeomConst* __restrict__ G, SectorTrackBufs sb) {
+__global__ void __launch_bounds__(128) k_sector_fit(const int* __restrict__ nStDev, TrackletBufs tb,
+                                                    const int2* __restrict__ syz, const GeomConst* __restrict__ G,
+                                                    SectorTrackBufs sb) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= nSt) return;
+  if (id >= *nStDev) return;
   const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
   const int b = sb.off[id], m = sb.off[id + 1] - b;
   const int* H = sb.hits + b;
@@ -522,9 +532,9 @@ PassGrid pass_grid() {
 }
 }  // namespace
 
-void launch_tracklets(int nTl, int* workCounter, const int* starts, const int* up, const RowGrid* grid, int nRows,
-                      const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st,
-                      cudaEvent_t* passEnd) {
+void launch_tracklets(int nTl, const int* nTlDev, int* workCounter, const int* starts, const int* up,
+                      const RowGrid* grid, int nRows, const int* cellStart, const int2* syz, const GeomConst* G,
+                      TrackletBufs tb, cudaStream_t st, cudaEvent_t* passEnd) {
   auto mark = [&](int i) {
     if (passEnd) cudaEventRecord(passEnd[i], st);
   };
@@ -535,51 +545,51 @@ void launch_tracklets(int nTl, int* workCounter, const int* starts, const int* u
   const PassGrid g = pass_grid();
   auto blocks = [&](int perSm) { return std::min((nTl + 127) / 128, g.sms * std::max(perSm, 1)); };
   cudaMemsetAsync(workCounter, 0, 4 * sizeof(int), st);
-  k_tl_chain<<<blocks(g.chain), 128, 0, st>>>(nTl, workCounter, starts, up, grid, nRows, syz, G, tb);
+  k_tl_chain<<<blocks(g.chain), 128, 0, st>>>(nTlDev, workCounter, starts, up, grid, nRows, syz, G, tb);
   mark(0);
-  k_tl_out<<<blocks(g.out), 128, 0, st>>>(nTl, workCounter + 1, grid, cellStart, syz, G, tb);
+  k_tl_out<<<blocks(g.out), 128, 0, st>>>(nTlDev, workCounter + 1, grid, cellStart, syz, G, tb);
   mark(1);
-  k_tl_refit<<<blocks(g.refit), 128, 0, st>>>(nTl, workCounter + 2, syz, G, tb);
+  k_tl_refit<<<blocks(g.refit), 128, 0, st>>>(nTlDev, workCounter + 2, syz, G, tb);
   mark(2);
-  k_tl_in<<<blocks(g.in), 128, 0, st>>>(nTl, workCounter + 3, grid, cellStart, syz, G, tb);
+  k_tl_in<<<blocks(g.in), 128, 0, st>>>(nTlDev, workCounter + 3, grid, cellStart, syz, G, tb);
   mark(3);
   g_launch_count += 4;
 }
 
-void launch_ownership(int nTl, int nSec, const RowGrid* grid, const int* starts, TrackletBufs tb, void* w,
-                      int* secBegin, int* wide, cudaStream_t st) {
+void launch_ownership(int nTl, const int* nTlDev, int nSec, const RowGrid* grid, const int* starts, TrackletBufs tb,
+                      void* w, int* secBegin, int* wide, cudaStream_t st) {
   cudaMemsetAsync(wide, 0, sizeof(int), st);
-  k_sector_ranges<<<(nSec + 1 + 127) / 128, 128, 0, st>>>(nSec, grid, starts, nTl, secBegin, wide);
+  k_sector_ranges<<<(nSec + 1 + 127) / 128, 128, 0, st>>>(nSec, grid, starts, nTlDev, secBegin, wide);
   ++g_launch_count;
   if (nTl > 0) {
-    k_ownership<<<(nTl + 127) / 128, 128, 0, st>>>(nTl, OwnCtx{secBegin, wide, w}, tb);
+    k_ownership<<<(nTl + 127) / 128, 128, 0, st>>>(nTlDev, OwnCtx{secBegin, wide, w}, tb);
     ++g_launch_count;
   }
 }
 
-void launch_segments_count(int nTl, const int* secBegin, const int* wide, const void* w, TrackletBufs tb, int* nSeg,
-                           int* nSegHits, cudaStream_t st) {
+void launch_segments_count(int nTl, const int* nTlDev, const int* secBegin, const int* wide, const void* w,
+                           TrackletBufs tb, int* nSeg, int* nSegHits, cudaStream_t st) {
   if (nTl > 0) {
-    k_segments_count<<<(nTl + 127) / 128, 128, 0, st>>>(nTl, OwnCtx{secBegin, wide, const_cast<void*>(w)}, tb,
+    k_segments_count<<<(nTl + 127) / 128, 128, 0, st>>>(nTlDev, OwnCtx{secBegin, wide, const_cast<void*>(w)}, tb,
                                                          nSeg, nSegHits);
     ++g_launch_count;
   }
 }
 
-void launch_segments_write(int nTl, const int* secBegin, const int* wide, const void* w, TrackletBufs tb,
-                           const int* segPos, const int* segHitPos, const int2* syz, SectorTrackBufs sb,
-                           cudaStream_t st) {
+void launch_segments_write(int nTl, const int* nTlDev, const int* secBegin, const int* wide, const void* w,
+                           TrackletBufs tb, const int* segPos, const int* segHitPos, const int2* syz,
+                           SectorTrackBufs sb, int capSt, int capHits, cudaStream_t st) {
   if (nTl > 0) {
-    k_segments_write<<<(nTl + 127) / 128, 128, 0, st>>>(nTl, OwnCtx{secBegin, wide, const_cast<void*>(w)}, tb,
-                                                         segPos, segHitPos, syz, sb);
+    k_segments_write<<<(nTl + 127) / 128, 128, 0, st>>>(nTlDev, OwnCtx{secBegin, wide, const_cast<void*>(w)}, tb,
+                                                         segPos, segHitPos, syz, sb, capSt, capHits);
     ++g_launch_count;
   }
 }
 
-void launch_sector_fit(int nSt, const TrackletBufs tb, const int2* syz, const GeomConst* G, SectorTrackBufs sb,
-                       cudaStream_t st) {
+void launch_sector_fit(int nSt, const int* nStDev, const TrackletBufs tb, const int2* syz, const GeomConst* G,
+                       SectorTrackBufs sb, cudaStream_t st) {
   if (nSt > 0) {
-    k_sector_fit<<<(nSt + 127) / 128, 128, 0, st>>>(nSt, tb, syz, G, sb);
+    k_sector_fit<<<(nSt + 127) / 128, 128, 0, st>>>(nStDev, tb, syz, G, sb);
     ++g_launch_count;
   }
 }

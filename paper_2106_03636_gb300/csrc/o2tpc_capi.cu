@@ -421,13 +421,19 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   M.N = n;
   TFDesc* dTF = dalloc<TFDesc>(M, B);
   int2* dTiles = dalloc<int2>(M, nTiles);
+  Counts* C = dalloc<Counts>(M, 1);  // device-side sizes of this batch
   {
-    size_t b1 = sizeof(TFDesc) * B, b2 = sizeof(int2) * nTiles;
-    char* h = static_cast<char*>(c->stage(b1 + b2));
+    Counts hc{};
+    hc.n = n;
+    hc.nKeys = B * kNSec * 2;
+    size_t b1 = sizeof(TFDesc) * B, b2 = sizeof(int2) * nTiles, b3 = sizeof(Counts);
+    char* h = static_cast<char*>(c->stage(b1 + b2 + b3));
     memcpy(h, tfd.data(), b1);
     memcpy(h + b1, tiles.data(), b2);
+    memcpy(h + b1 + b2, &hc, b3);
     CK(cudaMemcpyAsync(dTF, h, b1, cudaMemcpyHostToDevice, st));
     if (nTiles) CK(cudaMemcpyAsync(dTiles, h + b1, b2, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(C, h + b1 + b2, b3, cudaMemcpyHostToDevice, st));
   }
   unsigned* dErr = dalloc<unsigned>(M, 4);
   CK(cudaMemsetAsync(dErr, 0, 16, st));
@@ -476,17 +482,19 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   launch_neighbours(nfBlocksMax, nfB, grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw, st);
   CKL();
   CK(cudaEventRecord(c->evs[3], st));
-  launch_clean(n, upRaw, dnRaw, up, dn, flag, st);
+  launch_clean(n, &C->n, upRaw, dnRaw, up, dn, flag, st);
   CKL();
-  scan_exclusive(flag, pos, n, scratch, st);
+  scan_exclusive(flag, pos, n, &C->n, scratch, st);
   CKL();
-  const int nTl = read_int(c, pos + n);  // sync 1
+  launch_count_at(pos, &C->n, &C->nTl, INT_MAX, &C->overflow, st);
+  CKL();
+  const int nTl = read_int(c, &C->nTl);  // sync 1
   M.nTl = nTl;
   int* starts = dalloc<int>(M, nTl);
-  launch_compact(n, flag, pos, starts, st);
+  launch_compact(n, &C->n, flag, pos, starts, nTl, &C->overflow, st);
   CKL();
   int* tlTfBegin = dalloc<int>(M, B + 1);
-  launch_tf_ranges(B, grid, starts, nTl, tlTfBegin, st);
+  launch_tf_ranges(B, grid, starts, &C->nTl, tlTfBegin, st);
   CKL();
 
   // ---- A8: tracklets
@@ -500,7 +508,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   tb.zref = dalloc<int>(M, nTl);
   tb.rbase = dalloc<int>(M, nTl);
   int* workCounter = dalloc<int>(M, 4);
-  launch_tracklets(nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st, c->evTl);
+  launch_tracklets(nTl, &C->nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st, c->evTl);
   CKL();
 
   // ---- A9: selection
@@ -509,21 +517,22 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CK(cudaMemsetAsync(w, 0, sizeof(unsigned long long) * std::max(n, 1), st));
   int* secBegin = dalloc<int>(M, B * kNSec + 1);
   int* wide = dalloc<int>(M, 1);
-  launch_ownership(nTl, B * kNSec, grid, starts, tb, w, secBegin, wide, st);
+  launch_ownership(nTl, &C->nTl, B * kNSec, grid, starts, tb, w, secBegin, wide, st);
   CKL();
   int* nSeg = dalloc<int>(M, nTl + 1);
   int* nSegHits = dalloc<int>(M, nTl + 1);
   int* segPos = dalloc<int>(M, nTl + 1);
   int* segHitPos = dalloc<int>(M, nTl + 1);
-  launch_segments_count(nTl, secBegin, wide, w, tb, nSeg, nSegHits, st);
+  launch_segments_count(nTl, &C->nTl, secBegin, wide, w, tb, nSeg, nSegHits, st);
   CKL();
-  scan_exclusive(nSeg, segPos, nTl, scratch, st);
+  scan_exclusive(nSeg, segPos, nTl, &C->nTl, scratch, st);
   CKL();
-  scan_exclusive(nSegHits, segHitPos, nTl, scratch, st);
+  scan_exclusive(nSegHits, segHitPos, nTl, &C->nTl, scratch, st);
+  CKL();
+  launch_count_at(segPos, &C->nTl, &C->nSt, INT_MAX, &C->overflow, st, segHitPos, &C->nStHits, INT_MAX);
   CKL();
   int hv[2];
-  CK(cudaMemcpyAsync(&hv[0], segPos + nTl, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(&hv[1], segHitPos + nTl, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hv, &C->nSt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));  // sync 2
   const int nSt = hv[0], nStHits = hv[1];
   M.nSt = nSt;
@@ -537,28 +546,26 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   sb.rows = dalloc<uint8_t>(M, nStHits);
   sb.in = dalloc<float>(M, (size_t)nSt * 21);
   sb.out = dalloc<float>(M, (size_t)nSt * 21);
-  launch_segments_write(nTl, secBegin, wide, w, tb, segPos, segHitPos, syz, sb, st);
+  launch_segments_write(nTl, &C->nTl, secBegin, wide, w, tb, segPos, segHitPos, syz, sb, nSt, nStHits, st);
   CKL();
-  CK(cudaMemcpyAsync(sb.off + nSt, segHitPos + nTl, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  // CSR end: sb.off[nSt] = nStHits
+  launch_count_at(segPos, &C->nTl, &C->nSt, nSt, &C->overflow, st, segHitPos, &C->nStHits, nStHits, sb.off);
+  CKL();
   CK(cudaEventRecord(c->evs[6], st));
-  launch_sector_fit(nSt, tb, syz, G, sb, st);
+  launch_sector_fit(nSt, &C->nSt, tb, syz, G, sb, st);
   CKL();
   int* stTfBegin = dalloc<int>(M, B + 1);
-  {
-    std::vector<int> keys(B + 1);
-    for (int i = 0; i <= B; ++i) keys[i] = i;
-    int* dk = dalloc<int>(M, B + 1);
-    CK(cudaMemcpyAsync(dk, keys.data(), sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st));
-    launch_lower_bounds(sb.tf, nSt, dk, B + 1, stTfBegin, st);
-    CKL();
-    CK(cudaStreamSynchronize(st));
-  }
+  int* tfKeys = dalloc<int>(M, B + 1);
+  launch_iota(tfKeys, B + 1, st);
+  launch_lower_bounds(sb.tf, &C->nSt, tfKeys, B + 1, stTfBegin, st);
+  CKL();
 
   // ---- A10: merger
   CK(cudaEventRecord(c->evs[7], st));
   const int nKeys = B * kNSec * 2;
   MergeBufs mb;
   mb.nSt = nSt;
+  mb.cnt = C;
   mb.keyIn = dalloc<int>(M, nSt);
   mb.keyOut = dalloc<int>(M, nSt);
   mb.listCnt = dalloc<int>(M, nKeys + 1);
@@ -592,13 +599,15 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CKL();
   int* headFlag = dalloc<int>(M, nSt + 1);
   int* headPos = dalloc<int>(M, nSt + 1);
-  launch_chains(nSt, B, stTfBegin, mb, headFlag, st);
+  launch_chains(nSt, mb, headFlag, st);
   CKL();
-  scan_exclusive(headFlag, headPos, nSt, scratch, st);
+  scan_exclusive(headFlag, headPos, nSt, &C->nSt, scratch, st);
   CKL();
-  const int nHeads = read_int(c, headPos + nSt);  // sync 4
+  launch_count_at(headPos, &C->nSt, &C->nHeads, INT_MAX, &C->overflow, st);
+  CKL();
+  const int nHeads = read_int(c, &C->nHeads);  // sync 4
   int* heads = dalloc<int>(M, nHeads);
-  launch_compact(nSt, headFlag, headPos, heads, st);
+  launch_compact(nSt, &C->nSt, headFlag, headPos, heads, nHeads, &C->overflow, st);
   CKL();
 
   // ---- A11: final refit and output
@@ -624,15 +633,16 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   ob.nFallback = dalloc<int>(OM, 1);
   ob.fallback = dalloc<int>(M, nHeads);
   CK(cudaMemsetAsync(ob.nFallback, 0, sizeof(int), st));
-  launch_chain_counts(nHeads, heads, sb, mb, trkNcl, st);
+  launch_chain_counts(nHeads, &C->nHeads, heads, sb, mb, trkNcl, st);
   CKL();
-  scan_exclusive(trkNcl, ob.off, nHeads, scratch, st);
+  scan_exclusive(trkNcl, ob.off, nHeads, &C->nHeads, scratch, st);
   CKL();
-  launch_final_refit(nHeads, heads, sb, mb, syz, sorig, dTF, G, (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, ob,
+  launch_final_refit(nHeads, &C->nHeads, heads, sb, mb, syz, sorig, dTF, G,
+                     (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, ob,
                      st);
   CKL();
   int* trkTfBegin = dalloc<int>(M, B + 1);
-  launch_lower_bounds(heads, nHeads, stTfBegin, B + 1, trkTfBegin, st);
+  launch_lower_bounds(heads, &C->nHeads, stTfBegin, B + 1, trkTfBegin, st);
   CKL();
   CK(cudaEventRecord(c->ev1, st));
   CK(cudaEventRecord(c->evs[9], st));

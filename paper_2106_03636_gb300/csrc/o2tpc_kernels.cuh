@@ -30,12 +30,34 @@ void launch_cell_sort(int nRows, const RowGrid* grid, const int4* bucket, int* c
 // k_ca.cu
 void launch_neighbours(int nfBlocks, int hitsPerBlock, const RowGrid* grid, const int* nfBlockStart, int nRows, const int* cellStart,
                        const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw, cudaStream_t st);
-void launch_clean(int n, const int* upRaw, const int* dnRaw, int* up, int* dn, int* startFlag, cudaStream_t st);
+// Data-dependent sizes are read by the kernels from device memory (nDev,
+// the fields of Counts); the host-side n of a launcher only sizes its grid:
+// the exact size on the regular path, a capacity on the captured path.
+struct Counts {
+  int n;         // clusters of the batch
+  int nTl;       // start hits = tracklets
+  int nSt;       // sector tracks
+  int nStHits;   // their hits
+  int nHeads;    // merged tracks
+  int overflow;  // a capacity was exceeded (captured path: rerun on the regular path)
+  int nKeys;     // merge lists / directed sector edges of the batch
+  int pad;
+};
+void launch_clean(int n, const int* nDev, const int* upRaw, const int* dnRaw, int* up, int* dn, int* startFlag,
+                  cudaStream_t st);
 int scan_scratch_ints(long long n);
-void scan_exclusive(const int* in, int* out, int n, int* scratch, cudaStream_t st);
-void launch_compact(int n, const int* flag, const int* pos, int* out, cudaStream_t st);
-void launch_tf_ranges(int nTF, const RowGrid* grid, const int* list, int nList, int* tfBegin, cudaStream_t st);
-void launch_lower_bounds(const int* list, int nList, const int* keys, int nKeys, int* out, cudaStream_t st);
+void scan_exclusive(const int* in, int* out, int n, const int* nDev, int* scratch, cudaStream_t st);
+void launch_compact(int n, const int* nDev, const int* flag, const int* pos, int* out, int cap, int* overflow,
+                    cudaStream_t st);
+// *dst = min(arr[*idx], cap); optionally *dst2 = min(arr2[*idx], cap2) and
+// endBase[*dst] = *dst2
+void launch_count_at(const int* arr, const int* idx, int* dst, int cap, int* overflow, cudaStream_t st,
+                     const int* arr2 = nullptr, int* dst2 = nullptr, int cap2 = 0, int* endBase = nullptr);
+void launch_iota(int* out, int n, cudaStream_t st);  // out[i] = i
+void launch_tf_ranges(int nTF, const RowGrid* grid, const int* list, const int* nListDev, int* tfBegin,
+                      cudaStream_t st);
+void launch_lower_bounds(const int* list, const int* nListDev, const int* keys, int nKeys, int* out,
+                         cudaStream_t st);
 
 // k_track.cu
 struct TrackletBufs {
@@ -49,9 +71,9 @@ struct TrackletBufs {
 };
 // passEnd: optional 4 events recorded after the chain-fit, outward, refit and
 // inward passes.
-void launch_tracklets(int nTl, int* workCounter, const int* starts, const int* up, const RowGrid* grid, int nRows,
-                      const int* cellStart, const int2* syz, const GeomConst* G, TrackletBufs tb, cudaStream_t st,
-                      cudaEvent_t* passEnd = nullptr);
+void launch_tracklets(int nTl, const int* nTlDev, int* workCounter, const int* starts, const int* up,
+                      const RowGrid* grid, int nRows, const int* cellStart, const int2* syz, const GeomConst* G,
+                      TrackletBufs tb, cudaStream_t st, cudaEvent_t* passEnd = nullptr);
 
 struct SectorTrackBufs {
   int* tl;        // [nSt] tracklet of the sector track
@@ -66,15 +88,16 @@ struct SectorTrackBufs {
 };
 // Ownership over w (n words: 32-bit keys, or 64-bit when *wide is set by the
 // sector ranges; w must hold 8 bytes per hit and start at zero).
-void launch_ownership(int nTl, int nSec, const RowGrid* grid, const int* starts, TrackletBufs tb, void* w,
-                      int* secBegin, int* wide, cudaStream_t st);
-void launch_segments_count(int nTl, const int* secBegin, const int* wide, const void* w, TrackletBufs tb, int* nSeg,
-                           int* nSegHits, cudaStream_t st);
-void launch_segments_write(int nTl, const int* secBegin, const int* wide, const void* w, TrackletBufs tb,
-                           const int* segPos, const int* segHitPos, const int2* syz, SectorTrackBufs sb,
-                           cudaStream_t st);
-void launch_sector_fit(int nSt, const TrackletBufs tb, const int2* syz, const GeomConst* G, SectorTrackBufs sb,
-                       cudaStream_t st);
+void launch_ownership(int nTl, const int* nTlDev, int nSec, const RowGrid* grid, const int* starts, TrackletBufs tb,
+                      void* w, int* secBegin, int* wide, cudaStream_t st);
+void launch_segments_count(int nTl, const int* nTlDev, const int* secBegin, const int* wide, const void* w,
+                           TrackletBufs tb, int* nSeg, int* nSegHits, cudaStream_t st);
+// capSt / capHits: room in the sector-track buffers (writes past them dropped)
+void launch_segments_write(int nTl, const int* nTlDev, const int* secBegin, const int* wide, const void* w,
+                           TrackletBufs tb, const int* segPos, const int* segHitPos, const int2* syz,
+                           SectorTrackBufs sb, int capSt, int capHits, cudaStream_t st);
+void launch_sector_fit(int nSt, const int* nStDev, const TrackletBufs tb, const int2* syz, const GeomConst* G,
+                       SectorTrackBufs sb, cudaStream_t st);
 
 // k_merge.cu
 struct MergeBufs {
@@ -96,15 +119,16 @@ struct MergeBufs {
   int* next;         // [nSt]
   int* prev;         // [nSt]
   int* reached;      // [nSt]
+  const Counts* cnt; // device sizes (nSt, nKeys)
 };
 void launch_merge_keys(int nSt, const SectorTrackBufs sb, const GeomConst* G, MergeBufs mb, int nKeys, int* scratch,
                        cudaStream_t st);
 void launch_merge_pairs(int nSt, const SectorTrackBufs sb, const GeomConst* G, MergeBufs mb, unsigned* err,
                         cudaStream_t st);
 void launch_merge_select(int nPairs, int nKeys, MergeBufs mb, int* scratch, cudaStream_t st);
-void launch_chains(int nSt, int nTF, const int* stTfBegin, MergeBufs mb, int* headFlag, cudaStream_t st);
-void launch_chain_counts(int nHeads, const int* heads, const SectorTrackBufs sb, MergeBufs mb, int* trkNcl,
-                         cudaStream_t st);
+void launch_chains(int nSt, MergeBufs mb, int* headFlag, cudaStream_t st);
+void launch_chain_counts(int nHeads, const int* nHeadsDev, const int* heads, const SectorTrackBufs sb, MergeBufs mb,
+                         int* trkNcl, cudaStream_t st);
 
 struct OutBufs {
   int* off;         // [nTrk + 1] batch-global offsets into cl
@@ -121,8 +145,8 @@ struct OutBufs {
   int* nFallback;   // [1]
   int* fallback;    // [nTrk] tracks queued for the FP64 refit
 };
-void launch_final_refit(int nHeads, const int* heads, const SectorTrackBufs sb, MergeBufs mb, const int2* syz,
-                        const int* sorig, const TFDesc* tfs, const GeomConst* G, int forceFp64, OutBufs ob,
-                        cudaStream_t st);
+void launch_final_refit(int nHeads, const int* nHeadsDev, const int* heads, const SectorTrackBufs sb, MergeBufs mb,
+                        const int2* syz, const int* sorig, const TFDesc* tfs, const GeomConst* G, int forceFp64,
+                        OutBufs ob, cudaStream_t st);
 
 }  // namespace o2tpc
