@@ -83,10 +83,14 @@ enum {
   O2TPC_FLAG_NO_BATCHING = 1u << 1, /* run every TF alone (one TF per batch)  */
   O2TPC_FLAG_FORCE_FP64 = 1u << 2,  /* take the FP64 covariance path in the final
                                        refit for every track (testing aid)     */
-  O2TPC_FLAG_AUTOTUNE = 1u << 3     /* on the first batch of >= 2^20 clusters,
+  O2TPC_FLAG_AUTOTUNE = 1u << 3,    /* on the first batch of >= 2^20 clusters,
                                        time the launch shapes of the tunable
                                        steps on that batch and keep the fastest
                                        (see o2tpc_get_tuning)                  */
+  O2TPC_FLAG_GRAPH_TIGHT = 1u << 4  /* captured path with token capacities (16
+                                       tracklets, sector tracks, pairs): batches
+                                       overflow and rerun on the regular path
+                                       (testing aid)                           */
 };
 
 typedef struct {
@@ -121,6 +125,16 @@ typedef struct {
                                     pad row: 64, 128 (default) or 256             */
   int32_t sort_threads_per_row;  /* cell sort: threads per pad row: 128, 256
                                     (default) or 512                              */
+  /* Captured path (0: off): batches of at most graph_max_tfs TFs (0: 64) and
+   * graph_max_clusters clusters run as ONE CUDA graph launch - the whole
+   * pipeline captured once and replayed, no host synchronisation inside -
+   * from a device arena allocated at o2tpc_create (about 200 bytes per
+   * cluster of graph_max_clusters, on top of mem_budget).  A batch whose
+   * data exceed the arena's capacities (e.g. far more tracklets than usual)
+   * is run again on the regular path; results are the same either way.
+   * Not used with O2TPC_FLAG_KEEP_STAGES. */
+  uint64_t graph_max_clusters;
+  int32_t graph_max_tfs;
 } o2tpc_config;
 
 /* Launch shapes in use and, once the autotuner has run, its timings (device
@@ -175,6 +189,9 @@ typedef struct {
    * inputs that were uploaded ahead on the context's copy stream; 14 and 15
    * the outward and the inward following passes inside step 4 */
   float ms_stage[16];
+  uint32_t captured;         /* 1: the batch ran as one CUDA graph launch (the
+                                captured path: ms_stage holds only 10-13)     */
+  uint32_t reserved;
 } o2tpc_stats;
 
 /* Result of one TF; library-owned memory, valid until o2tpc_result_release. */

@@ -30,6 +30,7 @@ CUDA_SOURCES = [
     "k_track.cu",
     "k_merge.cu",
     "o2tpc_static.cu",
+    "o2tpc_graph.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "o2tpc.h"
+#include "o2tpc_graph.cuh"
 #include "o2tpc_kernels.cuh"
 
 using namespace o2tpc;
@@ -121,6 +122,7 @@ struct Pending {
   cudaEvent_t dl0 = nullptr, dl1 = nullptr;
   float stageMs[16] = {};
   double hostPrepMs = 0;
+  bool captured = false;
   ~Pending() {
     if (dl0) cudaEventDestroy(dl0);
     if (dl1) cudaEventDestroy(dl1);
@@ -146,6 +148,15 @@ struct Ctx {
   cudaEvent_t evs[12] = {};
   cudaEvent_t evTl[4] = {};  // ends of the four tracklet passes
   o2tpc_tuning tune{};       // launch shapes in use (autotuner results)
+  // captured path: arena, graph, and the event after the last replay's
+  // result copies (the next replay overwrites the result arrays)
+  std::unique_ptr<GraphArena> graph;
+  void* graphMem = nullptr;
+  cudaGraphExec_t graphExec = nullptr;
+  long long graphKernels = 0;
+  int graphNf = 0, graphSort = 0;
+  cudaEvent_t graphDl = nullptr;
+  bool graphDlRecorded = false;
   // copy stream, its thread and the bytes uploaded ahead of their batch
   cudaStream_t upStream = nullptr;
   std::thread uploader;
@@ -355,29 +366,155 @@ void autotune(Ctx* c, int n, int nRows, const int* rowCnt, const int* rowMin, co
   launch_grid(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, c->tune.nf_hits_per_block, totals, st);
 }
 
-void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
+// What the download and the kept stages need from a pipeline run.
+struct Pipe {
+  int B = 0, n = 0, nHeads = 0;
+  long long launches = 0;
+  std::vector<TFDesc> tfd;
+  const RowGrid* grid = nullptr;
+  int *cellStart = nullptr, *sorig = nullptr, *upRaw = nullptr, *dnRaw = nullptr, *up = nullptr, *dn = nullptr;
+  int* starts = nullptr;
+  int2* syz = nullptr;
+  TrackletBufs tb{};
+  SectorTrackBufs sb{};
+  MergeBufs mb{};
+  OutBufs ob{};
+  const int *trkTfBegin = nullptr, *stTfBegin = nullptr, *tlTfBegin = nullptr;
+  const unsigned* dErr = nullptr;
+  std::shared_ptr<BatchMem> outMem;  // result arrays freed after the download (regular path)
+};
+
+// A batch runs on the captured path when it fits the arena.
+bool graph_fits(const Ctx* c, const std::vector<std::shared_ptr<Job>>& jobs) {
+  const GraphCaps& k = c->graph->caps;
+  if ((int)jobs.size() > k.BCap) return false;
+  long long n = 0;
+  for (auto& j : jobs) n += (long long)j->tf.n;
+  return n <= k.nCap;
+}
+
+size_t r256(size_t x) { return (x + 255) / 256 * 256; }
+
+// The captured path: the TF table, tiles and sizes are written into the
+// arena, then one graph launch runs the whole pipeline (captured on first
+// use, again after the launch shapes changed).  Returns false, with nothing
+// for the caller to undo, when a capacity overflowed or the capture failed:
+// the batch then runs on the regular path.
+bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, Pipe& pp) {
+  (void)M;
+  GraphArena& A = *c->graph;
+  const GraphCaps& k = A.caps;
   cudaStream_t st = c->stream;
-  const bool keep = (c->cfg.flags & O2TPC_FLAG_KEEP_STAGES) != 0;
-  auto mem = std::make_shared<BatchMem>();
-  mem->ctx = c;
-  BatchMem& M = *mem;
+  const int B = (int)jobs.size();
+  std::vector<TFDesc> tfd(k.BCap);
+  std::vector<int2> tiles;
+  long long N = 0;
+  size_t inOff = 0;
+  for (int i = 0; i < B; ++i) {
+    const o2tpc_tf& t = jobs[i]->tf;
+    TFDesc d{};
+    d.format = t.format;
+    d.n = (int)t.n;
+    d.inBase = (int)N;
+    if (t.location == O2TPC_LOC_DEVICE || t.n == 0) {
+      d.in0 = t.format == O2TPC_FMT_FIXED ? t.packed : (const void*)t.sector;
+      d.in1 = t.row;
+      d.y = t.y;
+      d.z = t.z;
+    } else if (jobs[i]->upState == 4) {  // uploaded ahead (the batch waited for the copy)
+      input_layout(t, jobs[i]->dIn, d);
+    } else {
+      void* p = A.input + inOff;
+      inOff += r256(input_bytes(t));
+      input_upload(t, p, st);
+      input_layout(t, p, d);
+    }
+    d.tileBase = (int)tiles.size();
+    d.nTiles = (int)((t.n + k.tileSize - 1) / k.tileSize);
+    for (int q = 0; q < d.nTiles; ++q) tiles.push_back(make_int2(i, q * k.tileSize));
+    tfd[i] = d;
+    N += (long long)t.n;
+  }
+  for (int i = B; i < k.BCap; ++i) {  // empty TFs up to the capacity
+    TFDesc d{};
+    d.format = O2TPC_FMT_FIXED;
+    d.inBase = (int)N;
+    d.in0 = A.input;
+    d.tileBase = (int)tiles.size();
+    tfd[i] = d;
+  }
+  while ((int)tiles.size() < k.nTilesCap) tiles.push_back(make_int2(0, 1 << 30));  // no clusters
+  {
+    Counts hc{};
+    hc.n = (int)N;
+    hc.nKeys = k.nKeys;
+    const size_t b1 = sizeof(TFDesc) * k.BCap, b2 = sizeof(int2) * k.nTilesCap, b3 = sizeof(Counts);
+    char* h = static_cast<char*>(c->stage(b1 + b2 + b3));
+    memcpy(h, tfd.data(), b1);
+    memcpy(h + b1, tiles.data(), b2);
+    memcpy(h + b1 + b2, &hc, b3);
+    CK(cudaMemcpyAsync(A.tfs, h, b1, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(A.tiles, h + b1, b2, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(A.cnt, h + b1 + b2, b3, cudaMemcpyHostToDevice, st));
+  }
+  if (c->graphDlRecorded) CK(cudaStreamWaitEvent(st, c->graphDl, 0));
+  if (c->graphExec && (c->graphNf != c->tune.nf_hits_per_block || c->graphSort != c->tune.sort_threads_per_row)) {
+    cudaGraphExecDestroy(c->graphExec);
+    c->graphExec = nullptr;
+  }
+  if (!c->graphExec) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    const long long before = g_launch_count;
+    graph_enqueue(A, c->dGeom, c->tune.nf_hits_per_block, c->tune.sort_threads_per_row,
+                  (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, st);
+    const cudaError_t ce = cudaStreamEndCapture(st, &g);
+    c->graphKernels = g_launch_count - before;
+    if (ce != cudaSuccess || !g || cudaGraphInstantiate(&c->graphExec, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      c->graphExec = nullptr;
+      std::fprintf(stderr, "o2tpc: graph capture failed; batches run on the regular path\n");
+      c->graph.reset();
+      return false;
+    }
+    cudaGraphDestroy(g);
+    c->graphNf = c->tune.nf_hits_per_block;
+    c->graphSort = c->tune.sort_threads_per_row;
+  }
+  g_launch_count = c->graphKernels;
+  CK(cudaEventRecord(c->evs[0], st));
+  CK(cudaGraphLaunch(c->graphExec, st));
+  CK(cudaEventRecord(c->ev1, st));
+  int hv[10];
+  CK(cudaMemcpyAsync(hv, A.cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hv + 8, A.mb.pairCount, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hv + 9, A.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  Counts hc;
+  memcpy(&hc, hv, sizeof(Counts));
+  if (hc.overflow || hv[8] > k.pairCap || (hv[9] & kErrOverflow)) return false;
+  tfd.resize(B);
+  pp.B = B;
+  pp.n = (int)N;
+  pp.tfd = tfd;
+  pp.grid = A.grid;
+  pp.ob = A.ob;
+  pp.nHeads = hc.nHeads;
+  pp.trkTfBegin = A.trkTfBegin;
+  pp.stTfBegin = A.stTfBegin;
+  pp.tlTfBegin = A.tlTfBegin;
+  pp.dErr = A.err;
+  pp.launches = c->graphKernels;
+  return true;
+}
+
+// The regular path: sizes read back at four points, buffers allocated
+// exactly (the batch's memory M), stage events recorded.
+void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, Pipe& pp) {
+  cudaStream_t st = c->stream;
   const int B = (int)jobs.size();
   const int nRows = B * kRowsPerTF;
-  M.nTF = B;
-  M.nRows = nRows;
-  CK(cudaEventRecord(c->ev0, st));
-  g_launch_count = 0;
-  // inputs uploaded ahead: the batch waits for their copies and owns their memory
-  for (auto& jp : jobs) {
-    if (jp->upState != 2) continue;
-    M.blocks.push_back({jp->dIn, (size_t)jp->dInBytes});
-    jp->upState = 4;  // the batch owns the copy now
-    CK(cudaStreamWaitEvent(st, jp->upEv, 0));
-    cudaEventDestroy(jp->upEv);
-    jp->upEv = nullptr;
-  }
-  CK(cudaEventRecord(c->evWait, st));
-
   // ---- inputs and TF table
   std::vector<TFDesc> tfd(B);
   std::vector<int2> tiles;
@@ -647,9 +784,67 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CK(cudaEventRecord(c->ev1, st));
   CK(cudaEventRecord(c->evs[9], st));
 
+  pp.B = B;
+  pp.n = n;
+  pp.tfd = tfd;
+  pp.grid = grid;
+  pp.cellStart = cellStart;
+  pp.sorig = sorig;
+  pp.syz = syz;
+  pp.upRaw = upRaw;
+  pp.dnRaw = dnRaw;
+  pp.up = up;
+  pp.dn = dn;
+  pp.starts = starts;
+  pp.tb = tb;
+  pp.sb = sb;
+  pp.mb = mb;
+  pp.ob = ob;
+  pp.nHeads = nHeads;
+  pp.trkTfBegin = trkTfBegin;
+  pp.stTfBegin = stTfBegin;
+  pp.tlTfBegin = tlTfBegin;
+  pp.dErr = dErr;
+  pp.outMem = outMem;
+  pp.launches = g_launch_count;
+}
+
+void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
+  cudaStream_t st = c->stream;
+  const bool keep = (c->cfg.flags & O2TPC_FLAG_KEEP_STAGES) != 0;
+  auto mem = std::make_shared<BatchMem>();
+  mem->ctx = c;
+  BatchMem& M = *mem;
+  const int B = (int)jobs.size();
+  const int nRows = B * kRowsPerTF;
+  M.nTF = B;
+  M.nRows = nRows;
+  CK(cudaEventRecord(c->ev0, st));
+  g_launch_count = 0;
+  // inputs uploaded ahead: the batch waits for their copies and owns their memory
+  for (auto& jp : jobs) {
+    if (jp->upState != 2) continue;
+    M.blocks.push_back({jp->dIn, (size_t)jp->dInBytes});
+    jp->upState = 4;  // the batch owns the copy now
+    CK(cudaStreamWaitEvent(st, jp->upEv, 0));
+    cudaEventDestroy(jp->upEv);
+    jp->upEv = nullptr;
+  }
+  CK(cudaEventRecord(c->evWait, st));
+  Pipe pp;
+  bool captured = false;
+  if (c->graph && !keep && graph_fits(c, jobs)) captured = run_captured(c, jobs, M, pp);
+  if (!captured) run_regular(c, jobs, M, pp);
+
   // ---- A12: download.  Sizes first (synchronously), then every TF's arrays
   // straight into its own pinned result block on the download stream, which
   // the finisher thread waits for while the worker starts the next batch.
+  const int n = pp.n, nHeads = pp.nHeads;
+  const OutBufs& ob = pp.ob;
+  const std::vector<TFDesc>& tfd = pp.tfd;
+  const RowGrid* grid = pp.grid;
+  const int *trkTfBegin = pp.trkTfBegin, *stTfBegin = pp.stTfBegin, *tlTfBegin = pp.tlTfBegin;
+  const unsigned* dErr = pp.dErr;
   const size_t nT = (size_t)nHeads;
   int* hSmall = static_cast<int*>(c->stage(sizeof(int) * (nT + 1 + 3 * (B + 1) + 8)));
   int* hOff = hSmall;
@@ -670,15 +865,18 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
 
   auto P = std::make_shared<Pending>();
   P->jobs = jobs;
-  P->out = outMem;
-  for (int k = 0; k < 10; ++k) cudaEventElapsedTime(&P->stageMs[k], c->evs[k], c->evs[k + 1]);
-  cudaEventElapsedTime(&P->stageMs[12], c->evWait, c->evs[0]);
+  P->out = pp.outMem;
+  P->captured = captured;
+  if (!captured) {  // the captured path records no stage events
+    for (int k = 0; k < 10; ++k) cudaEventElapsedTime(&P->stageMs[k], c->evs[k], c->evs[k + 1]);
+    cudaEventElapsedTime(&P->stageMs[12], c->evWait, c->evs[0]);
+    cudaEventElapsedTime(&P->stageMs[14], c->evTl[0], c->evTl[1]);
+    cudaEventElapsedTime(&P->stageMs[15], c->evTl[2], c->evTl[3]);
+  }
   cudaEventElapsedTime(&P->stageMs[13], c->ev0, c->evWait);
-  cudaEventElapsedTime(&P->stageMs[14], c->evTl[0], c->evTl[1]);
-  cudaEventElapsedTime(&P->stageMs[15], c->evTl[2], c->evTl[3]);
   float devMs = 0.f;
   cudaEventElapsedTime(&devMs, c->ev0, c->ev1);
-  const long long nLaunch = g_launch_count;
+  const long long nLaunch = pp.launches;
   const bool inputBad = (*hErr & kErrInput) != 0;
   cudaStream_t dl = c->dlStream;
   CK(cudaEventCreate(&P->dl0));
@@ -750,6 +948,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     J.tfIndex = i;
   }
   CK(cudaEventRecord(P->dl1, dl));
+  if (captured) CK(cudaEventRecord(c->graphDl, dl));  // the next replay reuses the result arrays
   P->hostPrepMs = now_ms() - tPrep;
 
   M.tfHitBase.resize(B);
@@ -763,18 +962,18 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     M.tfInBase[i] = tfd[i].inBase;
   }
   if (keep) {
-    M.grid = grid;
-    M.cellStart = cellStart;
-    M.sorig = sorig;
-    M.syz = syz;
-    M.upRaw = upRaw;
-    M.dnRaw = dnRaw;
-    M.up = up;
-    M.dn = dn;
-    M.starts = starts;
-    M.tb = tb;
-    M.sb = sb;
-    M.mb = mb;
+    M.grid = const_cast<RowGrid*>(pp.grid);
+    M.cellStart = pp.cellStart;
+    M.sorig = pp.sorig;
+    M.syz = pp.syz;
+    M.upRaw = pp.upRaw;
+    M.dnRaw = pp.dnRaw;
+    M.up = pp.up;
+    M.dn = pp.dn;
+    M.starts = pp.starts;
+    M.tb = pp.tb;
+    M.sb = pp.sb;
+    M.mb = pp.mb;
     M.refs = B;
     for (int i = 0; i < B; ++i) jobs[i]->mem = mem;
   }
@@ -873,6 +1072,10 @@ void worker_main(Ctx* c) {
         if (!batch.empty() && (fp + j->footprint > c->cfg.mem_budget || hits + j->tf.n > kMaxBatchHits ||
                                hits + j->tf.n > c->cfg.batch_full_clusters))
           break;
+        // with a captured path, batches stay within its arena where they can
+        if (!batch.empty() && c->graph &&
+            ((int)batch.size() >= c->graph->caps.BCap || hits + j->tf.n > (uint64_t)c->graph->caps.nCap))
+          break;
         fp += j->footprint;
         hits += j->tf.n;
         batch.push_back(j);
@@ -956,6 +1159,7 @@ void finisher_main(Ctx* c) {
         for (int k = 0; k < 16; ++k) R.stats.ms_stage[k] = P->stageMs[k];
         R.stats.ms_stage[10] = dlMs;
         R.stats.ms_stage[11] = (float)P->hostPrepMs;
+        R.stats.captured = P->captured ? 1u : 0u;
         R.stats.ms_batch = (float)(tEnd - jp->t_start);
       }
     } else {
@@ -1069,6 +1273,23 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
   } catch (const AllocError&) {
     delete x;
     return O2TPC_ENOMEM;
+  }
+  if (c.graph_max_clusters > 0) {
+    try {
+      CK(cudaEventCreateWithFlags(&x->graphDl, cudaEventDisableTiming));
+      x->graph.reset(new GraphArena());
+      x->graph->caps = graph_caps((long long)std::min<uint64_t>(c.graph_max_clusters, kMaxBatchHits / 2),
+                                  c.graph_max_tfs > 0 ? c.graph_max_tfs : 64,
+                                  (c.flags & O2TPC_FLAG_GRAPH_TIGHT) != 0);
+      const size_t bytes = graph_carve(*x->graph, nullptr);
+      x->graphMem = x->dev_alloc(bytes);
+      graph_carve(*x->graph, static_cast<char*>(x->graphMem));
+    } catch (...) {
+      cudaGetLastError();
+      x->graph.reset();
+      o2tpc_destroy(reinterpret_cast<o2tpc_ctx*>(x));
+      return O2TPC_ENOMEM;
+    }
   }
   x->worker = std::thread(worker_main, x);
   x->finisher = std::thread(finisher_main, x);
@@ -1203,7 +1424,10 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
   for (auto& kv : c->pinnedFree) cudaFreeHost(kv.second);
   c->pinnedFree.clear();
   c->dev_free(c->dGeom);
+  if (c->graphExec) cudaGraphExecDestroy(c->graphExec);
+  if (c->graphMem) c->dev_free(c->graphMem);
   cudaStreamSynchronize(c->stream);
+  if (c->graphDl) cudaEventDestroy(c->graphDl);
   if (c->hStage) cudaFreeHost(c->hStage);
   for (auto& e : c->evs)
     if (e) cudaEventDestroy(e);

@@ -33,6 +33,7 @@ O2TPC_LOC_DEVICE = 1
 
 O2TPC_FLAG_KEEP_STAGES = 1 << 0
 O2TPC_FLAG_AUTOTUNE = 1 << 3
+O2TPC_FLAG_GRAPH_TIGHT = 1 << 4
 O2TPC_FLAG_NO_BATCHING = 1 << 1
 O2TPC_FLAG_FORCE_FP64 = 1 << 2
 
@@ -56,6 +57,8 @@ class o2tpc_config(ctypes.Structure):
         ("batch_full_clusters", ctypes.c_uint64),
         ("nf_hits_per_block", ctypes.c_int32),
         ("sort_threads_per_row", ctypes.c_int32),
+        ("graph_max_clusters", ctypes.c_uint64),
+        ("graph_max_tfs", ctypes.c_int32),
     ]
 
 
@@ -97,6 +100,8 @@ class o2tpc_stats(ctypes.Structure):
         ("ms_device", ctypes.c_float),
         ("n_launches", ctypes.c_uint64),
         ("ms_stage", ctypes.c_float * 16),
+        ("captured", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
     ]
 
 STAGES = ("ingest", "sort", "neighbours", "clean_starts", "tracklets", "selection", "sector_fit", "merge",
@@ -288,7 +293,8 @@ class Tracker:
 
     def __init__(self, device: int = 0, bz: float = 0.5, vdrift: float = 2.58, flags: int = 0,
                  mem_budget: int = 0, max_inflight: int = 0, max_batch: int = 0, torch_memory: bool = False,
-                 batch_full_clusters: int = 0, nf_hits_per_block: int = 0, sort_threads_per_row: int = 0):
+                 batch_full_clusters: int = 0, nf_hits_per_block: int = 0, sort_threads_per_row: int = 0,
+                 graph_max_clusters: int = 0, graph_max_tfs: int = 0):
         self.cfg = o2tpc_config()
         self.cfg.device = device
         self.cfg.bz_tesla = bz
@@ -300,6 +306,8 @@ class Tracker:
         self.cfg.batch_full_clusters = batch_full_clusters
         self.cfg.nf_hits_per_block = nf_hits_per_block
         self.cfg.sort_threads_per_row = sort_threads_per_row
+        self.cfg.graph_max_clusters = graph_max_clusters
+        self.cfg.graph_max_tfs = graph_max_tfs
         self._keep = []
         import torch
 

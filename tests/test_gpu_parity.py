@@ -199,3 +199,23 @@ def test_launch_shapes_and_autotuner_leave_results_unchanged():
             assert np.array_equal(ref[k], r[k]), k
     with pytest.raises(o2tpc.O2TPCError):
         o2tpc.Tracker(nf_hits_per_block=100)
+
+
+def test_captured_path_equals_regular_path():
+    """Batches run as one CUDA graph launch (the captured path) give the same
+    results as the regular path, on two different batches in a row (the
+    second a replay of the graph); with token capacities every batch
+    overflows and reruns on the regular path, again with the same results."""
+    keys = ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref")
+    sets = [synth.chunk_mix(seed=41, n_chunks=5) + [synth.single_sector(seed=42)],
+            synth.chunk_mix(seed=43, n_chunks=7)]
+    with o2tpc.Tracker() as r:
+        ref = [[r.poll(t) for t in r.submit_many(s)] for s in sets]
+    for flags, captured in ((0, 1), (o2tpc.O2TPC_FLAG_GRAPH_TIGHT, 0)):
+        with o2tpc.Tracker(graph_max_clusters=32 << 20, graph_max_tfs=8, flags=flags) as g:
+            for s, rs in zip(sets, ref):
+                got = [g.poll(t) for t in g.submit_many(s)]
+                for x, y in zip(rs, got):
+                    assert y["status"] == 0 and y["stats"]["captured"] == captured
+                    for k in keys:
+                        assert np.array_equal(x[k], y[k]), k
