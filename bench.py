@@ -296,7 +296,10 @@ def run_chunks(args, rank, world, local):
     torch.cuda.synchronize()
     tune = 0 if args.no_autotune else o2tpc.O2TPC_FLAG_AUTOTUNE
     plain = o2tpc.Tracker(device=local, flags=o2tpc.O2TPC_FLAG_NO_BATCHING | tune)
-    batched = o2tpc.Tracker(device=local, max_batch=len(chunks), batch_full_clusters=2**64 - 1, flags=tune)
+    # batched: all chunks in one batch; captured path (one CUDA graph launch) unless --no-graph
+    gcap = 0 if args.no_graph else int(n * 1.25)
+    batched = o2tpc.Tracker(device=local, max_batch=len(chunks), batch_full_clusters=2**64 - 1, flags=tune,
+                            graph_max_clusters=gcap, graph_max_tfs=len(chunks))
 
     def pass_plain(loc=o2tpc.O2TPC_LOC_DEVICE, arrays=dev):
         out = []
@@ -316,7 +319,7 @@ def run_chunks(args, rank, world, local):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stage = np.zeros(16)
-        launches, sizes = 0, set()
+        launches, sizes, captured = 0, set(), set()
         e0.record(trk.stream)
         for _ in range(args.steps):
             rs = fn(*a)
@@ -332,14 +335,23 @@ def run_chunks(args, rank, world, local):
                 stage += np.asarray(r["stats"]["ms_stage"])
                 launches += int(r["stats"]["n_launches"])
                 sizes.add(int(r["stats"]["batch_size"]))
+                captured.add(int(r["stats"]["captured"]))
         e1.record(trk.stream)
         torch.cuda.synchronize()
         ms = device_max(e0.elapsed_time(e1), world, local)
+        timed.captured = sorted(captured)
         return ms / args.steps, stage / args.steps, launches // args.steps, sorted(sizes), rs
 
     with ClockSampler(local) as clk:
         ms_p, stage_p, l_p, _, _ = timed(pass_plain, plain)
         ms_b, stage_b, l_b, sizes_b, rs = timed(pass_batched, batched)
+        captured_b = timed.captured
+        if captured_b == [1]:
+            # the graph records no per-step events: step times of the same
+            # batch on the regular path, for stage_ms and the roofline line
+            reg = o2tpc.Tracker(device=local, max_batch=len(chunks), batch_full_clusters=2**64 - 1, flags=tune)
+            ms_r, stage_b, _, _, _ = timed(lambda: [reg.wait(t) for t in reg.submit_many(chunks, location=o2tpc.O2TPC_LOC_DEVICE, arrays=dev)], reg)
+            reg.close()
     e2e = None
     if not args.no_e2e:
         pin = [{"packed": torch.from_numpy(c.packed).pin_memory()} for c in chunks]
@@ -359,10 +371,12 @@ def run_chunks(args, rank, world, local):
                        "chunk_clusters_max": int(max(c.n for c in chunks)), "format": "fixed12",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
             "batched": {"value": world * n / (ms_b / 1e3), "ms_per_step": ms_b, "batch_sizes": sizes_b,
-                        "gpu_launches": l_b},
+                        "gpu_launches": l_b, "captured_graph": captured_b == [1],
+                        "graph_launches_per_step": 1 if captured_b == [1] else 0},
             "plain": {"value": world * n / (ms_p / 1e3), "ms_per_step": ms_p, "gpu_launches": l_p,
                       "stage_ms": {names[i]: round(float(stage_p[i]), 3) for i in range(16)}},
             "speedup_batched_vs_plain": ms_p / ms_b,
+            "stage_ms_source": "regular path, same batch" if captured_b == [1] else "batched arm",
             "stage_ms": {names[i]: round(float(stage_b[i]), 3) for i in range(16)},
             "roofline": roofline(stage_b, names, n, peak, peak_kind),
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "peak": peak,
@@ -507,6 +521,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--trace", action="store_true", help="per-TF stage times on stderr")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
+    ap.add_argument("--no-graph", action="store_true", help="chunks: batched arm on the regular path, not captured")
     ap.add_argument("--torch-memory", action="store_true",
                     help="device buffers from PyTorch's caching allocator (no uploads ahead)")
     ap.add_argument("--inflight", type=int, default=3, help="TFs kept in flight in the served measurement")

@@ -833,7 +833,12 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CK(cudaEventRecord(c->evWait, st));
   Pipe pp;
   bool captured = false;
-  if (c->graph && !keep && graph_fits(c, jobs)) captured = run_captured(c, jobs, M, pp);
+  // a batch the autotuner still waits for runs on the regular path (the
+  // graph is captured afterwards with the chosen shapes)
+  long long nb = 0;
+  for (auto& j : jobs) nb += (long long)j->tf.n;
+  const bool tunePending = (c->cfg.flags & O2TPC_FLAG_AUTOTUNE) && !c->tune.tuned && nb >= (1 << 20);
+  if (c->graph && !keep && !tunePending && graph_fits(c, jobs)) captured = run_captured(c, jobs, M, pp);
   if (!captured) run_regular(c, jobs, M, pp);
 
   // ---- A12: download.  Sizes first (synchronously), then every TF's arrays
