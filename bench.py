@@ -422,9 +422,12 @@ def run_serving(args, rank, world, local):
                 "mean_batch": float(sizes.mean()), "wall_s": wall}
 
     def served_run():
-        trk = o2tpc.Tracker(device=local, max_inflight=args.max_queue)
+        # batches of small TFs (up to the GPU-full size) run as one captured graph launch
+        trk = o2tpc.Tracker(device=local, max_inflight=args.max_queue,
+                            graph_max_clusters=0 if args.no_graph else 1 << 25, graph_max_tfs=16)
         warm(trk)
         done, pending = [], collections.deque()
+        n_captured = [0]
         cv = threading.Condition()
         state = {"closed": False}
 
@@ -439,6 +442,7 @@ def run_serving(args, rank, world, local):
                 if r["status"] != 0:
                     raise RuntimeError(o2tpc.o2tpc_strerror(r["status"]))
                 done.append((t_arr, time.perf_counter(), i, r["stats"]["batch_size"]))
+                n_captured[0] += int(r["stats"]["captured"])
 
         th = threading.Thread(target=poller, daemon=True)
         th.start()
@@ -463,7 +467,9 @@ def run_serving(args, rank, world, local):
             cv.notify()
         th.join()
         trk.close()
-        return summary(done, dropped, t0)
+        out = summary(done, dropped, t0)
+        out["captured_tfs"] = n_captured[0]
+        return out
 
     def plain_run():
         trk = o2tpc.Tracker(device=local, flags=o2tpc.O2TPC_FLAG_NO_BATCHING)
