@@ -135,18 +135,21 @@ typedef struct {
    * Not used with O2TPC_FLAG_KEEP_STAGES. */
   uint64_t graph_max_clusters;
   int32_t graph_max_tfs;
+  int32_t nf_staged;             /* NeighboursFinder candidates staged in shared
+                                    memory by TMA bulk copies (1) or read through
+                                    L1 (0, default); the autotuner times both    */
 } o2tpc_config;
 
 /* Launch shapes in use and, once the autotuner has run, its timings (device
- * ms of each candidate on the batch it tuned on; candidates in the order
- * listed above). */
+ * ms of each candidate on the batch it tuned on). */
 typedef struct {
   int32_t tuned;                 /* 1 once the autotuner has chosen               */
   int32_t nf_hits_per_block;
+  int32_t nf_staged;
   int32_t sort_threads_per_row;
   int32_t tuned_on_clusters;     /* size of the batch it tuned on                 */
-  float nf_ms[3];
-  float sort_ms[3];
+  float nf_ms[6];                /* 64, 128, 256 hits per block; L1 then staged   */
+  float sort_ms[3];              /* 128, 256, 512 threads per row                 */
 } o2tpc_tuning;
 
 typedef struct {

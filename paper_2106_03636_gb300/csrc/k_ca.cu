@@ -25,15 +25,17 @@ __device__ inline unsigned pack_res(int dy, int dz) { return ((unsigned)(dy + 10
 // slots: the newest goes to slot kNFCand-1, older ones move down, so slots
 // [kNFCand - n, kNFCand) hold them in ascending index order.  Returns the
 // number found (more than kNFCand: the caller takes the general path).
+// pts[c - base] holds the coordinates of sorted hit c (the block's staged
+// slab, or the global array with base 0).
 __device__ inline int nf_collect(const RowGrid& g, int iy0, int iy1, int iz0, int iz1,
-                                 const int* __restrict__ cellStart, const int2* __restrict__ syz, int2 hh,
+                                 const int* __restrict__ cellStart, const int2* pts, int base, int2 hh,
                                  int (&idx)[kNFCand], unsigned (&res)[kNFCand]) {
   int n = 0;
   for (int iz = iz0; iz <= iz1; ++iz) {
     const int a = __ldg(cellStart + g.cellBase + iz * g.ny + iy0);
     const int b = __ldg(cellStart + g.cellBase + iz * g.ny + iy1 + 1);
     for (int c = a; c < b; ++c) {
-      const int2 p = __ldg(syz + c);
+      const int2 p = pts[c - base];
       const int dy = hh.x - p.x, dz = hh.y - p.y;
       if (abs(dy) > kWinY || abs(dz) > kWinZ) continue;
 #pragma unroll
@@ -52,34 +54,133 @@ __device__ inline int nf_collect(const RowGrid& g, int iy0, int iy1, int iz0, in
 // K4: one thread per hit; blocks of kB hits tile the rows
 // (nfBlockStart, built for the same block size, maps a block to its row,
 // looked up once per block).
-template <int kB>
+// --- staging of the adjacent rows' candidate slabs (TMA bulk copy)
+constexpr int kSlab = 1024;            // staged hits per side (8 KB)
+constexpr int kSlabWaitLimit = 1 << 22;  // mbarrier polls before giving up on a copy
+
+__device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Waits (bounded) for phase 0 of the mbarrier; false if it did not complete.
+__device__ inline bool slab_wait(unsigned bar) {
+  for (int i = 0; i < kSlabWaitLimit; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// K4: one thread per hit; blocks of kB hits tile the rows (nfBlockStart,
+// built for the same block size, maps a block to its row, looked up once per
+// block).  With kStage, the candidates come from shared memory: a block's
+// hits are consecutive in (cell, input) order, so they lie in the cell rows
+// between those of its first and last hit, and their candidates in the cell
+// rows of each adjacent pad row that this drift range (widened by the window)
+// reaches - every cell across the row, one contiguous range of the sorted
+// coordinates.  Thread 0 issues one TMA bulk copy per side as soon as it knows
+// the range, completing on an mbarrier; the threads set up their windows
+// meanwhile and wait just before scanning.  A side whose range exceeds kSlab
+// hits (or a copy that does not complete within the wait limit, flagged in
+// err) reads global memory instead.  Without kStage every candidate is a
+// global (L1-cached) load.
+template <int kB, bool kStage>
 __global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ grid,
-                                                         const int* __restrict__ nfBlockStart, int nRows,
-                                                         const int* __restrict__ cellStart,
-                                                         const int2* __restrict__ syz, const GeomConst* __restrict__ G,
-                                                         int* __restrict__ upRaw, int* __restrict__ dnRaw) {
+                                                   const int* __restrict__ nfBlockStart, int nRows,
+                                                   const int* __restrict__ cellStart, const int2* __restrict__ syz,
+                                                   const GeomConst* __restrict__ G, int* __restrict__ upRaw,
+                                                   int* __restrict__ dnRaw, unsigned* __restrict__ err) {
   if ((int)blockIdx.x >= nfBlockStart[nRows]) return;  // launched with an upper bound of blocks
-  __shared__ int s_row;
-  if (threadIdx.x == 0) s_row = upper_bound_i32(nfBlockStart, nRows + 1, blockIdx.x) - 1;
+  __shared__ __align__(16) int2 s_slab[kStage ? 2 : 1][kStage ? kSlab : 1];
+  __shared__ __align__(8) unsigned long long s_bar;
+  __shared__ int s_row, s_base[2], s_use[2];
+  const unsigned bar = smem_addr(&s_bar);
+  if (threadIdx.x == 0) {
+    const int R0 = upper_bound_i32(nfBlockStart, nRows + 1, blockIdx.x) - 1;
+    s_row = R0;
+    s_use[0] = s_use[1] = 0;
+    const int r0 = (R0 % kRowsPerTF) % kNRow;
+    if (kStage && r0 >= 1 && r0 <= kNRow - 2) {
+      const RowGrid g0 = grid[R0];
+      const int hf = g0.start + (blockIdx.x - nfBlockStart[R0]) * kB;
+      const int hl = min(hf + kB, g0.start + g0.count) - 1;
+      // drift range of the block's cell rows
+      const int izf = cell_iz_floor(syz[hf].y, g0), izl = cell_iz_floor(syz[hl].y, g0);
+      const long long zlo = (long long)g0.zmin + (long long)izf * g0.cz - kWinZ;
+      const long long zhi = (long long)g0.zmin + (long long)(izl + 1) * g0.cz - 1 + kWinZ;
+      unsigned bytes = 0;
+      for (int side = 0; side < 2; ++side) {
+        const RowGrid g2 = grid[side == 0 ? R0 + 1 : R0 - 1];
+        s_base[side] = 0;
+        if (g2.count == 0) continue;
+        const int zl = (int)max(zlo, (long long)INT_MIN + 1), zh = (int)min(zhi, (long long)INT_MAX - 1);
+        int iza = cell_iz_floor(zl, g2), izb = cell_iz_floor(zh, g2);
+        if (iza < 0) iza = 0;
+        if (izb > g2.nz - 1) izb = g2.nz - 1;
+        if (iza > izb) continue;
+        const int a = cellStart[g2.cellBase + iza * g2.ny], b = cellStart[g2.cellBase + (izb + 1) * g2.ny];
+        const int a0 = a & ~1, b0 = (b + 1) & ~1;  // 16-byte aligned range (syz has one int2 of padding)
+        if (b0 - a0 > kSlab || b0 <= a0) continue;
+        s_use[side] = b0 - a0;
+        s_base[side] = a0;
+        bytes += (unsigned)(b0 - a0) * 8u;
+      }
+      if (bytes) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        for (int side = 0; side < 2; ++side)
+          if (s_use[side])
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_addr(&s_slab[side][0])),
+                "l"(syz + s_base[side]), "r"((unsigned)s_use[side] * 8u), "r"(bar)
+                : "memory");
+      }
+    }
+  }
   __syncthreads();
   const int R = s_row;
   const RowGrid g = grid[R];
   const int h = g.start + (blockIdx.x - nfBlockStart[R]) * kB + threadIdx.x;
-  if (h >= g.start + g.count) return;
+  const bool valid = h < g.start + g.count;
   const int r = (R % kRowsPerTF) % kNRow;
+  if (r < 1 || r > kNRow - 2) {  // rows 0 and 151 get no links (no copy was issued)
+    if (valid) {
+      upRaw[h] = -1;
+      dnRaw[h] = -1;
+    }
+    return;
+  }
+  const bool staged = kStage && (s_use[0] || s_use[1]);
+  bool slabOk = true;
   int bu = -1, bd = -1;
-  if (r >= 1 && r <= kNRow - 2) {
+  if (valid) {
     const RowGrid gu = grid[R + 1], gd = grid[R - 1];
     const int npu = G->npads[r + 1], npd = G->npads[r - 1];
     const int2 hh = syz[h];
     const int yh = hh.x, zh = hh.y;
     int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
-    if (cell_range(gu, npu, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, uy0, uy1, uz0, uz1) &&
-        cell_range(gd, npd, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, dy0, dy1, dz0, dz1)) {
+    const bool inWin = cell_range(gu, npu, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, uy0, uy1, uz0, uz1) &&
+                       cell_range(gd, npd, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, dy0, dy1, dz0, dz1);
+    if (staged) {
+      slabOk = slab_wait(bar);
+      if (!slabOk) atomicOr(err, kErrTimeout);
+    }
+    const int2* su = (staged && slabOk && s_use[0]) ? s_slab[0] : syz;
+    const int bu0 = (staged && slabOk && s_use[0]) ? s_base[0] : 0;
+    const int2* sd = (staged && slabOk && s_use[1]) ? s_slab[kStage ? 1 : 0] : syz;
+    const int bd0 = (staged && slabOk && s_use[1]) ? s_base[1] : 0;
+    if (inWin) {
       int ui[kNFCand] = {}, di[kNFCand] = {};
       unsigned ur[kNFCand] = {}, dr[kNFCand] = {};
-      const int nu = nf_collect(gu, uy0, uy1, uz0, uz1, cellStart, syz, hh, ui, ur);
-      const int nd = nu > 0 ? nf_collect(gd, dy0, dy1, dz0, dz1, cellStart, syz, hh, di, dr) : 0;
+      const int nu = nf_collect(gu, uy0, uy1, uz0, uz1, cellStart, su, bu0, hh, ui, ur);
+      const int nd = nu > 0 ? nf_collect(gd, dy0, dy1, dz0, dz1, cellStart, sd, bd0, hh, di, dr) : 0;
       // bestD starts one above the cut, so "D < bestD" also applies the cut
       int bestD = kMaxMetric + 1;
       if (nu <= kNFCand && nd <= kNFCand) {
@@ -126,8 +227,13 @@ __global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ g
       }
     }
   }
-  upRaw[h] = bu;
-  dnRaw[h] = bd;
+  if (valid) {
+    upRaw[h] = bu;
+    dnRaw[h] = bd;
+  }
+  // a copy that did not complete in time must land before the block's shared
+  // memory is released
+  if (staged && threadIdx.x == 0) slab_wait(bar);
 }
 
 // K5 + K6a: reciprocity filter on the raw (snapshot) links and the chain-head
@@ -328,16 +434,23 @@ void launch_lower_bounds(const int* list, const int* nListDev, const int* keys, 
   }
 }
 
-void launch_neighbours(int nfBlocks, int hitsPerBlock, const RowGrid* grid, const int* nfBlockStart, int nRows,
-                       const int* cellStart, const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw,
-                       cudaStream_t st) {
+void launch_neighbours(int nfBlocks, int hitsPerBlock, bool stage, const RowGrid* grid, const int* nfBlockStart,
+                       int nRows, const int* cellStart, const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw,
+                       unsigned* err, cudaStream_t st) {
   if (nfBlocks > 0) {
-    if (hitsPerBlock == 64)
-      k_neighbours<64><<<nfBlocks, 64, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw);
-    else if (hitsPerBlock == 256)
-      k_neighbours<256><<<nfBlocks, 256, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw);
-    else
-      k_neighbours<128><<<nfBlocks, 128, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw);
+#define O2TPC_NF(B, S) \
+  k_neighbours<B, S><<<nfBlocks, B, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw, err)
+    if (hitsPerBlock == 64) {
+      if (stage) O2TPC_NF(64, true);
+      else O2TPC_NF(64, false);
+    } else if (hitsPerBlock == 256) {
+      if (stage) O2TPC_NF(256, true);
+      else O2TPC_NF(256, false);
+    } else {
+      if (stage) O2TPC_NF(128, true);
+      else O2TPC_NF(128, false);
+    }
+#undef O2TPC_NF
     ++g_launch_count;
   }
 }

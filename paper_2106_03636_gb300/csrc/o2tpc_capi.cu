@@ -134,6 +134,7 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   bool ownStream = false;
   GeomConst* dGeom = nullptr;
+  Counts* dCounts = nullptr;  // sizes of the running regular-path batch
   GeomConst hGeom{};
   std::thread worker;
   std::mutex mu;
@@ -316,12 +317,12 @@ void fill_geom(GeomConst& g, double bz, double vd) {
 // shape before the real NeighboursFinder launch.
 void autotune(Ctx* c, int n, int nRows, const int* rowCnt, const int* rowMin, const int* rowMax, RowGrid* grid,
               int* nfBlockStart, int* totals, const int4* bucket, int* cellStart, int2* syz, int* sorig,
-              int* gscratch) {
+              int* gscratch, unsigned* err) {
   cudaStream_t st = c->stream;
   const GeomConst* G = c->dGeom;
   static const int kSort[3] = {128, 256, 512};
   static const int kNF[3] = {64, 128, 256};
-  cudaEvent_t es[3][3], en[3][2];
+  cudaEvent_t es[3][3], en[6][2];
   for (auto& r : es)
     for (auto& e : r) CK(cudaEventCreate(&e));
   for (auto& r : en)
@@ -335,24 +336,28 @@ void autotune(Ctx* c, int n, int nRows, const int* rowCnt, const int* rowMin, co
     launch_cell_sort(nRows, grid, bucket, cellStart, syz, sorig, gscratch, totals, st, kSort[i]);
     CK(cudaEventRecord(es[i][2], st));
   }
-  for (int i = 0; i < 3; ++i) {
-    launch_grid(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, kNF[i], totals, st);
-    const int blocks = n / kNF[i] + nRows + 1;
+  for (int i = 0; i < 6; ++i) {
+    const int hb = kNF[i % 3];
+    launch_grid(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, hb, totals, st);
+    const int blocks = n / hb + nRows + 1;
     CK(cudaEventRecord(en[i][0], st));
-    launch_neighbours(blocks, kNF[i], grid, nfBlockStart, nRows, cellStart, syz, G, up, up + n, st);
+    launch_neighbours(blocks, hb, i >= 3, grid, nfBlockStart, nRows, cellStart, syz, G, up, up + n, err, st);
     CK(cudaEventRecord(en[i][1], st));
   }
-  CK(cudaEventSynchronize(en[2][1]));
+  CK(cudaEventSynchronize(en[5][1]));
   c->dev_free(up);
   int bs = 0, bn = 0;
   for (int i = 0; i < 3; ++i) {
-    float a = 0.f, b = 0.f, m = 0.f;
+    float a = 0.f, b = 0.f;
     cudaEventElapsedTime(&a, es[i][0], es[i][1]);
     cudaEventElapsedTime(&b, es[i][1], es[i][2]);
     c->tune.sort_ms[i] = std::min(a, b);
+    if (c->tune.sort_ms[i] < c->tune.sort_ms[bs]) bs = i;
+  }
+  for (int i = 0; i < 6; ++i) {
+    float m = 0.f;
     cudaEventElapsedTime(&m, en[i][0], en[i][1]);
     c->tune.nf_ms[i] = m;
-    if (c->tune.sort_ms[i] < c->tune.sort_ms[bs]) bs = i;
     if (c->tune.nf_ms[i] < c->tune.nf_ms[bn]) bn = i;
   }
   for (auto& r : es)
@@ -360,7 +365,8 @@ void autotune(Ctx* c, int n, int nRows, const int* rowCnt, const int* rowMin, co
   for (auto& r : en)
     for (auto& e : r) cudaEventDestroy(e);
   c->tune.sort_threads_per_row = kSort[bs];
-  c->tune.nf_hits_per_block = kNF[bn];
+  c->tune.nf_hits_per_block = kNF[bn % 3];
+  c->tune.nf_staged = bn >= 3 ? 1 : 0;
   c->tune.tuned = 1;
   c->tune.tuned_on_clusters = n;
   launch_grid(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, c->tune.nf_hits_per_block, totals, st);
@@ -458,7 +464,8 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
     CK(cudaMemcpyAsync(A.cnt, h + b1 + b2, b3, cudaMemcpyHostToDevice, st));
   }
   if (c->graphDlRecorded) CK(cudaStreamWaitEvent(st, c->graphDl, 0));
-  if (c->graphExec && (c->graphNf != c->tune.nf_hits_per_block || c->graphSort != c->tune.sort_threads_per_row)) {
+  if (c->graphExec && (c->graphNf != c->tune.nf_hits_per_block * 2 + c->tune.nf_staged ||
+                       c->graphSort != c->tune.sort_threads_per_row)) {
     cudaGraphExecDestroy(c->graphExec);
     c->graphExec = nullptr;
   }
@@ -466,7 +473,7 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     const long long before = g_launch_count;
-    graph_enqueue(A, c->dGeom, c->tune.nf_hits_per_block, c->tune.sort_threads_per_row,
+    graph_enqueue(A, c->dGeom, c->tune.nf_hits_per_block, c->tune.nf_staged != 0, c->tune.sort_threads_per_row,
                   (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, st);
     const cudaError_t ce = cudaStreamEndCapture(st, &g);
     c->graphKernels = g_launch_count - before;
@@ -479,7 +486,7 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
       return false;
     }
     cudaGraphDestroy(g);
-    c->graphNf = c->tune.nf_hits_per_block;
+    c->graphNf = c->tune.nf_hits_per_block * 2 + c->tune.nf_staged;
     c->graphSort = c->tune.sort_threads_per_row;
   }
   g_launch_count = c->graphKernels;
@@ -558,7 +565,7 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   M.N = n;
   TFDesc* dTF = dalloc<TFDesc>(M, B);
   int2* dTiles = dalloc<int2>(M, nTiles);
-  Counts* C = dalloc<Counts>(M, 1);  // device-side sizes of this batch
+  Counts* C = c->dCounts;  // device-side sizes of this batch (the context's own slot)
   {
     Counts hc{};
     hc.n = n;
@@ -596,13 +603,14 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   int* cellStart = dalloc<int>(M, cellsMax + 1);
   int* gscratch = dalloc<int>(M, cellsMax);
   int4* bucket = dalloc<int4>(M, n);
-  int2* syz = dalloc<int2>(M, n);
+  int2* syz = dalloc<int2>(M, (size_t)n + 2);  // padding read by the NeighboursFinder's aligned slab copies
   int* sorig = dalloc<int>(M, n);
   launch_row_scatter(dTF, dTiles, nTiles, tileSize, G, tileStats, grid, bucket, st);
   CKL();
   launch_cell_sort(nRows, grid, bucket, cellStart, syz, sorig, gscratch, totals, st, c->tune.sort_threads_per_row);
   if ((c->cfg.flags & O2TPC_FLAG_AUTOTUNE) && !c->tune.tuned && n >= (1 << 20))
-    autotune(c, n, nRows, rowCnt, rowMin, rowMax, grid, nfBlockStart, totals, bucket, cellStart, syz, sorig, gscratch);
+    autotune(c, n, nRows, rowCnt, rowMin, rowMax, grid, nfBlockStart, totals, bucket, cellStart, syz, sorig, gscratch,
+             dErr);
   CKL();
 
   // ---- A5-A7: neighbours, cleaner, start hits
@@ -616,7 +624,8 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   int* scratch = dalloc<int>(M, scan_scratch_ints((long long)n + 8) + (nRows + 8) * 2 / 4096 + 64);
   const int nfB = c->tune.nf_hits_per_block;
   const int nfBlocksMax = n / nfB + nRows + 1;
-  launch_neighbours(nfBlocksMax, nfB, grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw, st);
+  launch_neighbours(nfBlocksMax, nfB, c->tune.nf_staged != 0, grid, nfBlockStart, nRows, cellStart, syz, G, upRaw,
+                    dnRaw, dErr, st);
   CKL();
   CK(cudaEventRecord(c->evs[3], st));
   launch_clean(n, &C->n, upRaw, dnRaw, up, dn, flag, st);
@@ -645,7 +654,7 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   tb.zref = dalloc<int>(M, nTl);
   tb.rbase = dalloc<int>(M, nTl);
   int* workCounter = dalloc<int>(M, 4);
-  launch_tracklets(nTl, &C->nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st, c->evTl);
+  launch_tracklets(nTl, nullptr, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st, c->evTl);
   CKL();
 
   // ---- A9: selection
@@ -1235,6 +1244,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
   x->cfg = c;
   x->tune.nf_hits_per_block = c.nf_hits_per_block;
   x->tune.sort_threads_per_row = c.sort_threads_per_row;
+  x->tune.nf_staged = c.nf_staged ? 1 : 0;
   x->traceCopies = std::getenv("O2TPC_TRACE_COPIES") != nullptr;
   x->traceMode = x->traceCopies ? std::atoi(std::getenv("O2TPC_TRACE_COPIES")) : 0;
   try {
@@ -1269,6 +1279,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
     for (auto& e : x->evTl) CK(cudaEventCreate(&e));
     fill_geom(x->hGeom, c.bz_tesla, c.vdrift_cm_us);
     x->dGeom = static_cast<GeomConst*>(x->dev_alloc(sizeof(GeomConst)));
+    x->dCounts = static_cast<Counts*>(x->dev_alloc(sizeof(Counts)));
     CK(cudaMemcpyAsync(x->dGeom, &x->hGeom, sizeof(GeomConst), cudaMemcpyHostToDevice, x->stream));
     CK(cudaStreamSynchronize(x->stream));
   } catch (const CudaError&) {
@@ -1429,6 +1440,7 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
   for (auto& kv : c->pinnedFree) cudaFreeHost(kv.second);
   c->pinnedFree.clear();
   c->dev_free(c->dGeom);
+  c->dev_free(c->dCounts);
   if (c->graphExec) cudaGraphExecDestroy(c->graphExec);
   if (c->graphMem) c->dev_free(c->graphMem);
   cudaStreamSynchronize(c->stream);

@@ -66,7 +66,7 @@ size_t graph_carve(GraphArena& A, char* base) {
   take(A.cellStart, k.cellsCap + 1);
   take(A.gscratch, k.cellsCap);
   take(A.bucket, n);
-  take(A.syz, n);
+  take(A.syz, n + 2);
   take(A.sorig, n);
   take(A.upRaw, n);
   take(A.dnRaw, n);
@@ -144,8 +144,8 @@ size_t graph_carve(GraphArena& A, char* base) {
 
 // The batch pipeline with capacities for sizes and no host synchronisation;
 // the TF table, tiles and Counts (n, nKeys) are filled before each replay.
-void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, int sortThreads, int forceFp64,
-                   cudaStream_t st) {
+void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, bool nfStage, int sortThreads,
+                   int forceFp64, cudaStream_t st) {
   const GraphCaps& k = A.caps;
   Counts* C = A.cnt;
   const int n = k.nCap;
@@ -158,8 +158,8 @@ void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, int sor
   launch_row_scatter(A.tfs, A.tiles, k.nTilesCap, k.tileSize, G, A.tileStats, A.grid, A.bucket, st);
   launch_cell_sort(k.nRows, A.grid, A.bucket, A.cellStart, A.syz, A.sorig, A.gscratch, A.totals, st, sortThreads);
   // A5-A7
-  launch_neighbours(n / nfBlock + k.nRows + 1, nfBlock, A.grid, A.nfBlockStart, k.nRows, A.cellStart, A.syz, G,
-                    A.upRaw, A.dnRaw, st);
+  launch_neighbours(n / nfBlock + k.nRows + 1, nfBlock, nfStage, A.grid, A.nfBlockStart, k.nRows, A.cellStart, A.syz, G,
+                    A.upRaw, A.dnRaw, A.err, st);
   launch_clean(n, &C->n, A.upRaw, A.dnRaw, A.up, A.dn, A.flag, st);
   scan_exclusive(A.flag, A.pos, n, &C->n, A.scratch, st);
   launch_count_at(A.pos, &C->n, &C->nTl, k.tlCap, &C->overflow, st);

@@ -51,7 +51,7 @@ GraphCaps graph_caps(long long maxClusters, int maxTFs, bool tight = false);
 // Assigns the arena's pointers from base (null: only counts); returns bytes.
 size_t graph_carve(GraphArena& A, char* base);
 // Enqueues the whole pipeline on st (for stream capture).
-void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, int sortThreads, int forceFp64,
-                   cudaStream_t st);
+void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, bool nfStage, int sortThreads,
+                   int forceFp64, cudaStream_t st);
 
 }  // namespace o2tpc

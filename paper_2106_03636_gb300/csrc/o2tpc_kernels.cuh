@@ -28,8 +28,11 @@ void launch_cell_sort(int nRows, const RowGrid* grid, const int4* bucket, int* c
                       int threadsPerRow = 256);
 
 // k_ca.cu
-void launch_neighbours(int nfBlocks, int hitsPerBlock, const RowGrid* grid, const int* nfBlockStart, int nRows, const int* cellStart,
-                       const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw, cudaStream_t st);
+// syz must hold one int2 of padding past the last hit (the 16-byte aligned
+// slab copies may read it); err collects kErrTimeout.
+void launch_neighbours(int nfBlocks, int hitsPerBlock, bool stage, const RowGrid* grid, const int* nfBlockStart,
+                       int nRows, const int* cellStart, const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw,
+                       unsigned* err, cudaStream_t st);
 // Data-dependent sizes are read by the kernels from device memory (nDev,
 // the fields of Counts); the host-side n of a launcher only sizes its grid:
 // the exact size on the regular path, a capacity on the captured path.
@@ -71,6 +74,7 @@ struct TrackletBufs {
 };
 // passEnd: optional 4 events recorded after the chain-fit, outward, refit and
 // inward passes.
+// nTlDev: device tracklet count, or null to take nTl as exact
 void launch_tracklets(int nTl, const int* nTlDev, int* workCounter, const int* starts, const int* up,
                       const RowGrid* grid, int nRows, const int* cellStart, const int2* syz, const GeomConst* G,
                       TrackletBufs tb, cudaStream_t st, cudaEvent_t* passEnd = nullptr);

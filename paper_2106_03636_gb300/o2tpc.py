@@ -59,6 +59,7 @@ class o2tpc_config(ctypes.Structure):
         ("sort_threads_per_row", ctypes.c_int32),
         ("graph_max_clusters", ctypes.c_uint64),
         ("graph_max_tfs", ctypes.c_int32),
+        ("nf_staged", ctypes.c_int32),
     ]
 
 
@@ -66,9 +67,10 @@ class o2tpc_tuning(ctypes.Structure):
     _fields_ = [
         ("tuned", ctypes.c_int32),
         ("nf_hits_per_block", ctypes.c_int32),
+        ("nf_staged", ctypes.c_int32),
         ("sort_threads_per_row", ctypes.c_int32),
         ("tuned_on_clusters", ctypes.c_int32),
-        ("nf_ms", ctypes.c_float * 3),
+        ("nf_ms", ctypes.c_float * 6),
         ("sort_ms", ctypes.c_float * 3),
     ]
 
@@ -294,7 +296,7 @@ class Tracker:
     def __init__(self, device: int = 0, bz: float = 0.5, vdrift: float = 2.58, flags: int = 0,
                  mem_budget: int = 0, max_inflight: int = 0, max_batch: int = 0, torch_memory: bool = False,
                  batch_full_clusters: int = 0, nf_hits_per_block: int = 0, sort_threads_per_row: int = 0,
-                 graph_max_clusters: int = 0, graph_max_tfs: int = 0):
+                 graph_max_clusters: int = 0, graph_max_tfs: int = 0, nf_staged: bool = False):
         self.cfg = o2tpc_config()
         self.cfg.device = device
         self.cfg.bz_tesla = bz
@@ -308,6 +310,7 @@ class Tracker:
         self.cfg.sort_threads_per_row = sort_threads_per_row
         self.cfg.graph_max_clusters = graph_max_clusters
         self.cfg.graph_max_tfs = graph_max_tfs
+        self.cfg.nf_staged = int(nf_staged)
         self._keep = []
         import torch
 
@@ -396,7 +399,7 @@ class Tracker:
         rc, t = o2tpc_get_tuning(self.ctx)
         if rc != O2TPC_OK:
             raise O2TPCError(rc, "o2tpc_get_tuning")
-        return {"tuned": bool(t.tuned), "nf_hits_per_block": t.nf_hits_per_block,
+        return {"tuned": bool(t.tuned), "nf_hits_per_block": t.nf_hits_per_block, "nf_staged": bool(t.nf_staged),
                 "sort_threads_per_row": t.sort_threads_per_row, "tuned_on_clusters": t.tuned_on_clusters,
                 "nf_ms": list(t.nf_ms), "sort_ms": list(t.sort_ms)}
 

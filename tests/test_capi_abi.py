@@ -40,4 +40,4 @@ def test_binding_structures_match_header_sizes():
     # device, budget, inflight, batch, bz, vdrift, flags(+pad), 2 callbacks, user, stream, batch_full,
     # two launch shapes
     assert ctypes.sizeof(o2tpc.o2tpc_config) == 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 * 4 + 8 + 4 + 4 + 8 + 8
-    assert ctypes.sizeof(o2tpc.o2tpc_tuning) == 4 * 4 + 6 * 4
+    assert ctypes.sizeof(o2tpc.o2tpc_tuning) == 5 * 4 + 9 * 4

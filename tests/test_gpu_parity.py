@@ -186,15 +186,17 @@ def test_launch_shapes_and_autotuner_leave_results_unchanged():
     with o2tpc.Tracker() as a:
         ref = a.track(tf)
         assert a.tuning()["tuned"] is False
-    with o2tpc.Tracker(nf_hits_per_block=64, sort_threads_per_row=512) as b:
+    with o2tpc.Tracker(nf_hits_per_block=64, sort_threads_per_row=512, nf_staged=True) as b:
         other = b.track(tf)
+    with o2tpc.Tracker(nf_staged=True) as b2:
+        staged = b2.track(tf)
     with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_AUTOTUNE) as c:
         tuned = c.track(tf)
         t = c.tuning()
     assert t["tuned"] and t["tuned_on_clusters"] == tf.n
     assert t["nf_hits_per_block"] in (64, 128, 256) and t["sort_threads_per_row"] in (128, 256, 512)
     assert all(v > 0 for v in t["nf_ms"] + t["sort_ms"])
-    for r in (other, tuned):
+    for r in (other, staged, tuned):
         for k in keys:
             assert np.array_equal(ref[k], r[k]), k
     with pytest.raises(o2tpc.O2TPCError):
