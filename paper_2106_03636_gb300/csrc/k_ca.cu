@@ -286,9 +286,9 @@ __device__ inline int block_excl(int v, int* total) {
   return incl - v;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int* __restrict__ in, const int* __restrict__ nDev,
-                                                            int* __restrict__ sums) {
-  const int n = *nDev;
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int* __restrict__ in, int nHost,
+                                                            const int* __restrict__ nDev, int* __restrict__ sums) {
+  const int n = nDev ? *nDev : nHost;
   long long base = (long long)blockIdx.x * kScanTile;
   int s = 0;
 #pragma unroll
@@ -314,9 +314,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_mid(int* __restrict__ sum
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restrict__ in, const int* __restrict__ nDev,
-                                                             const int* __restrict__ sums, int* __restrict__ out) {
-  const int n = *nDev;
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restrict__ in, int nHost,
+                                                             const int* __restrict__ nDev, const int* __restrict__ sums,
+                                                             int* __restrict__ out) {
+  const int n = nDev ? *nDev : nHost;
   long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
   int v[kScanItems];
   int s = 0;
@@ -338,37 +339,28 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* __restri
 }
 
 // out[0..m] = exclusive scan of in[0..m-1], out[m] = total, m = *nDev <= n
-// (the grid covers n; tiles past m add zeros); out may alias in.
+// (the grid covers n; tiles past m add zeros), or m = n when nDev is null;
+// out may alias in.
 // scratch: >= scan_scratch_ints(n) ints.
 int scan_scratch_ints(long long n) { return (int)((n + kScanTile - 1) / kScanTile) + 1; }
 
-__global__ void k_store_zero_at(int* __restrict__ out, const int* __restrict__ nDev) { out[*nDev] = 0; }
+__global__ void k_store_zero_at(int* __restrict__ out, int nHost, const int* __restrict__ nDev) {
+  out[nDev ? *nDev : nHost] = 0;
+}
 
 void scan_exclusive(const int* in, int* out, int n, const int* nDev, int* scratch, cudaStream_t st) {
   int nb = (n + kScanTile - 1) / kScanTile;
   if (nb == 0) {
-    k_store_zero_at<<<1, 1, 0, st>>>(out, nDev);
+    k_store_zero_at<<<1, 1, 0, st>>>(out, n, nDev);
     ++g_launch_count;
     return;
   }
-  k_scan_sums<<<nb, kScanThreads, 0, st>>>(in, nDev, scratch);
+  k_scan_sums<<<nb, kScanThreads, 0, st>>>(in, n, nDev, scratch);
   ++g_launch_count;
   k_scan_mid<<<1, kScanThreads, 0, st>>>(scratch, nb);
   ++g_launch_count;
-  k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, nDev, scratch, out);
+  k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, n, nDev, scratch, out);
   ++g_launch_count;
-}
-
-// ordered compaction: out[pos[i]] = i for flag[i] != 0 (pos = exclusive
-// scan), i < *nDev; entries past the capacity are dropped and flagged
-__global__ void k_compact(const int* __restrict__ nDev, const int* __restrict__ flag, const int* __restrict__ pos,
-                          int* __restrict__ out, int cap, int* __restrict__ overflow) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < *nDev && flag[i]) {
-    const int p = pos[i];
-    if (p < cap) out[p] = i;
-    else *overflow = 1;
-  }
 }
 
 // *dst = min(arr[*idx], cap) (a count read off the end of a scan), flagging
@@ -463,10 +455,101 @@ void launch_clean(int n, const int* nDev, const int* upRaw, const int* dnRaw, in
   }
 }
 
-void launch_compact(int n, const int* nDev, const int* flag, const int* pos, int* out, int cap, int* overflow,
-                    cudaStream_t st) {
-  if (n > 0) {
-    k_compact<<<(n + 255) / 256, 256, 0, st>>>(nDev, flag, pos, out, cap, overflow);
+
+// ---- ordered compaction with warp ballots
+// Flags are taken in tiles of kBallotTile (1024 threads x 4 chunks).  Pass 1
+// counts each tile's set flags with one ballot and popcount per warp and
+// chunk; the tile counts are scanned; pass 2 writes every flagged index at
+// tile offset + earlier chunks + earlier warps (a 32-entry shuffle scan) +
+// its rank among the set lanes of its warp (popcount of the lower lanes).
+// Only one int per tile is scanned instead of one per flag.
+constexpr int kBallotTile = 4096;
+
+__global__ void __launch_bounds__(1024) k_ballot_counts(const int* __restrict__ flag, const int* __restrict__ nDev,
+                                                        int* __restrict__ tileCnt) {
+  __shared__ int ws[32];
+  const int n = *nDev, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = blockIdx.x * kBallotTile + k * 1024 + threadIdx.x;
+    c += __popc(__ballot_sync(0xffffffffu, i < n && flag[i] != 0));
+  }
+  if (lane == 0) ws[w] = c;
+  __syncthreads();
+  if (w == 0) {
+    int v = ws[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) tileCnt[blockIdx.x] = v;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_ballot_compact(const int* __restrict__ flag, const int* __restrict__ nDev,
+                                                         const int* __restrict__ tileOff, int* __restrict__ out,
+                                                         int cap, int* __restrict__ overflow) {
+  __shared__ int ws[32], s_tot;
+  const int n = *nDev, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int carry = tileOff[blockIdx.x];
+  for (int k = 0; k < 4; ++k) {
+    const int i = blockIdx.x * kBallotTile + k * 1024 + threadIdx.x;
+    const bool f = i < n && flag[i] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) ws[w] = __popc(m);
+    __syncthreads();
+    if (w == 0) {  // exclusive scan of the 32 warp counts
+      const int v = ws[lane];
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      ws[lane] = x - v;
+      if (lane == 31) s_tot = x;
+    }
+    __syncthreads();
+    if (f) {
+      const int p = carry + ws[w] + __popc(m & ((1u << lane) - 1u));
+      if (p < cap) out[p] = i;
+      else *overflow = 1;
+    }
+    carry += s_tot;
+    __syncthreads();
+  }
+}
+
+// *dst = min(total, cap) with total = tileOff[number of tiles of *nDev]
+__global__ void k_ballot_total(const int* __restrict__ tileOff, const int* __restrict__ nDev, int* __restrict__ dst,
+                               int cap, int* __restrict__ overflow) {
+  int v = tileOff[(*nDev + kBallotTile - 1) / kBallotTile];
+  if (v > cap) {
+    v = cap;
+    *overflow = 1;
+  }
+  *dst = v;
+}
+
+int ballot_tiles(long long n) { return (int)((n + kBallotTile - 1) / kBallotTile); }
+
+void launch_ballot_count(int n, const int* nDev, const int* flag, int* tileCnt, int* tileOff, int* count, int cap,
+                         int* overflow, int* scratch, cudaStream_t st) {
+  const int nt = ballot_tiles(n);
+  if (nt > 0) {
+    k_ballot_counts<<<nt, 1024, 0, st>>>(flag, nDev, tileCnt);
+    ++g_launch_count;
+  }
+  // tiles past *nDev count zero; the scan runs over all nt
+  scan_exclusive(tileCnt, tileOff, nt, nullptr, scratch, st);
+  k_ballot_total<<<1, 1, 0, st>>>(tileOff, nDev, count, cap, overflow);
+  ++g_launch_count;
+}
+
+void launch_ballot_compact(int n, const int* nDev, const int* flag, const int* tileOff, int* out, int cap,
+                           int* overflow, cudaStream_t st) {
+  const int nt = ballot_tiles(n);
+  if (nt > 0) {
+    k_ballot_compact<<<nt, 1024, 0, st>>>(flag, nDev, tileOff, out, cap, overflow);
     ++g_launch_count;
   }
 }

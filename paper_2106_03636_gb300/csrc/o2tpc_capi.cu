@@ -620,7 +620,6 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   int* up = dalloc<int>(M, n);
   int* dn = dalloc<int>(M, n);
   int* flag = dalloc<int>(M, n + 1);
-  int* pos = dalloc<int>(M, n + 1);
   int* scratch = dalloc<int>(M, scan_scratch_ints((long long)n + 8) + (nRows + 8) * 2 / 4096 + 64);
   const int nfB = c->tune.nf_hits_per_block;
   const int nfBlocksMax = n / nfB + nRows + 1;
@@ -630,14 +629,14 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   CK(cudaEventRecord(c->evs[3], st));
   launch_clean(n, &C->n, upRaw, dnRaw, up, dn, flag, st);
   CKL();
-  scan_exclusive(flag, pos, n, &C->n, scratch, st);
-  CKL();
-  launch_count_at(pos, &C->n, &C->nTl, INT_MAX, &C->overflow, st);
+  int* tileCnt = dalloc<int>(M, ballot_tiles(n) + 1);
+  int* tileOff = dalloc<int>(M, ballot_tiles(n) + 1);
+  launch_ballot_count(n, &C->n, flag, tileCnt, tileOff, &C->nTl, INT_MAX, &C->overflow, scratch, st);
   CKL();
   const int nTl = read_int(c, &C->nTl);  // sync 1
   M.nTl = nTl;
   int* starts = dalloc<int>(M, nTl);
-  launch_compact(n, &C->n, flag, pos, starts, nTl, &C->overflow, st);
+  launch_ballot_compact(n, &C->n, flag, tileOff, starts, nTl, &C->overflow, st);
   CKL();
   int* tlTfBegin = dalloc<int>(M, B + 1);
   launch_tf_ranges(B, grid, starts, &C->nTl, tlTfBegin, st);
@@ -744,16 +743,13 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   launch_merge_select(nPairs, nKeys, mb, scratch, st);
   CKL();
   int* headFlag = dalloc<int>(M, nSt + 1);
-  int* headPos = dalloc<int>(M, nSt + 1);
   launch_chains(nSt, mb, headFlag, st);
   CKL();
-  scan_exclusive(headFlag, headPos, nSt, &C->nSt, scratch, st);
-  CKL();
-  launch_count_at(headPos, &C->nSt, &C->nHeads, INT_MAX, &C->overflow, st);
+  launch_ballot_count(nSt, &C->nSt, headFlag, tileCnt, tileOff, &C->nHeads, INT_MAX, &C->overflow, scratch, st);
   CKL();
   const int nHeads = read_int(c, &C->nHeads);  // sync 4
   int* heads = dalloc<int>(M, nHeads);
-  launch_compact(nSt, &C->nSt, headFlag, headPos, heads, nHeads, &C->overflow, st);
+  launch_ballot_compact(nSt, &C->nSt, headFlag, tileOff, heads, nHeads, &C->overflow, st);
   CKL();
 
   // ---- A11: final refit and output

@@ -73,7 +73,8 @@ size_t graph_carve(GraphArena& A, char* base) {
   take(A.up, n);
   take(A.dn, n);
   take(A.flag, n + 1);
-  take(A.pos, n + 1);
+  take(A.tileCnt, ballot_tiles((long long)n) + 1);
+  take(A.tileOff, ballot_tiles((long long)n) + 1);
   take(A.scratch, scan_scratch_ints((long long)n + 8) + (k.nRows + 8) * 2 / 4096 + 64);
   take(A.starts, k.tlCap);
   take(A.tlTfBegin, k.BCap + 1);
@@ -119,7 +120,6 @@ size_t graph_carve(GraphArena& A, char* base) {
   take(A.mb.pairsSorted, k.pairCap);
   take(A.mb.sortScratch, 2 * (size_t)std::max(k.pairCap, k.stCap) + 16);
   take(A.headFlag, k.stCap + 1);
-  take(A.headPos, k.stCap + 1);
   take(A.heads, k.headCap);
   take(A.trkNcl, k.headCap + 1);
   take(A.ob.off, k.headCap + 1);
@@ -161,9 +161,8 @@ void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, bool nf
   launch_neighbours(n / nfBlock + k.nRows + 1, nfBlock, nfStage, A.grid, A.nfBlockStart, k.nRows, A.cellStart, A.syz, G,
                     A.upRaw, A.dnRaw, A.err, st);
   launch_clean(n, &C->n, A.upRaw, A.dnRaw, A.up, A.dn, A.flag, st);
-  scan_exclusive(A.flag, A.pos, n, &C->n, A.scratch, st);
-  launch_count_at(A.pos, &C->n, &C->nTl, k.tlCap, &C->overflow, st);
-  launch_compact(n, &C->n, A.flag, A.pos, A.starts, k.tlCap, &C->overflow, st);
+  launch_ballot_count(n, &C->n, A.flag, A.tileCnt, A.tileOff, &C->nTl, k.tlCap, &C->overflow, A.scratch, st);
+  launch_ballot_compact(n, &C->n, A.flag, A.tileOff, A.starts, k.tlCap, &C->overflow, st);
   launch_tf_ranges(k.BCap, A.grid, A.starts, &C->nTl, A.tlTfBegin, st);
   // A8
   launch_tracklets(k.tlCap, &C->nTl, A.workCounter, A.starts, A.up, A.grid, k.nRows, A.cellStart, A.syz, G, A.tb,
@@ -186,9 +185,9 @@ void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, bool nf
   launch_merge_pairs(k.stCap, A.sb, G, A.mb, A.err, st);
   launch_merge_select(k.pairCap, k.nKeys, A.mb, A.scratch, st);
   launch_chains(k.stCap, A.mb, A.headFlag, st);
-  scan_exclusive(A.headFlag, A.headPos, k.stCap, &C->nSt, A.scratch, st);
-  launch_count_at(A.headPos, &C->nSt, &C->nHeads, k.headCap, &C->overflow, st);
-  launch_compact(k.stCap, &C->nSt, A.headFlag, A.headPos, A.heads, k.headCap, &C->overflow, st);
+  launch_ballot_count(k.stCap, &C->nSt, A.headFlag, A.tileCnt, A.tileOff, &C->nHeads, k.headCap, &C->overflow,
+                      A.scratch, st);
+  launch_ballot_compact(k.stCap, &C->nSt, A.headFlag, A.tileOff, A.heads, k.headCap, &C->overflow, st);
   // A11
   cudaMemsetAsync(A.ob.nFallback, 0, sizeof(int), st);
   launch_chain_counts(k.headCap, &C->nHeads, A.heads, A.sb, A.mb, A.trkNcl, st);

@@ -32,7 +32,7 @@ struct GraphArena {
   int4* bucket;
   int2* syz;
   int* sorig;
-  int *upRaw, *dnRaw, *up, *dn, *flag, *pos, *scratch;
+  int *upRaw, *dnRaw, *up, *dn, *flag, *tileCnt, *tileOff, *scratch;
   int* starts;
   int* tlTfBegin;
   TrackletBufs tb;
@@ -42,7 +42,7 @@ struct GraphArena {
   SectorTrackBufs sb;
   int *stTfBegin, *tfKeys;
   MergeBufs mb;
-  int *headFlag, *headPos, *heads, *trkNcl;
+  int *headFlag, *heads, *trkNcl;
   OutBufs ob;
   int* trkTfBegin;
 };

@@ -50,8 +50,15 @@ void launch_clean(int n, const int* nDev, const int* upRaw, const int* dnRaw, in
                   cudaStream_t st);
 int scan_scratch_ints(long long n);
 void scan_exclusive(const int* in, int* out, int n, const int* nDev, int* scratch, cudaStream_t st);
-void launch_compact(int n, const int* nDev, const int* flag, const int* pos, int* out, int cap, int* overflow,
-                    cudaStream_t st);
+// Ordered compaction with warp ballots: the indices i < *nDev with flag[i]
+// set, ascending, into out (at most cap; more raise *overflow).
+// launch_ballot_count: tile counts, their scan into tileOff and *count;
+// launch_ballot_compact: the writes.  tileCnt/tileOff: ballot_tiles(n) + 1.
+int ballot_tiles(long long n);
+void launch_ballot_count(int n, const int* nDev, const int* flag, int* tileCnt, int* tileOff, int* count, int cap,
+                         int* overflow, int* scratch, cudaStream_t st);
+void launch_ballot_compact(int n, const int* nDev, const int* flag, const int* tileOff, int* out, int cap,
+                           int* overflow, cudaStream_t st);
 // *dst = min(arr[*idx], cap); optionally *dst2 = min(arr2[*idx], cap2) and
 // endBase[*dst] = *dst2
 void launch_count_at(const int* arr, const int* idx, int* dst, int cap, int* overflow, cudaStream_t st,
