@@ -138,6 +138,10 @@ typedef struct {
   int32_t nf_staged;             /* NeighboursFinder candidates staged in shared
                                     memory by TMA bulk copies (1) or read through
                                     L1 (0, default); the autotuner times both    */
+  const char* tune_cache_path;   /* NULL, or a text file keeping the autotuner's
+                                    choice per GPU model: read at o2tpc_create
+                                    (a matching entry counts as tuned), written
+                                    after tuning                                  */
 } o2tpc_config;
 
 /* Launch shapes in use and, once the autotuner has run, its timings (device
@@ -160,7 +164,9 @@ typedef struct {
   const uint8_t* sector;
   const uint8_t* row;
   const float* y;          /* cm                                                       */
-  const float* z;          /* cm, apparent z (see above)                               */
+  const float* z;          /* cm, apparent z (see above); may be NULL when time is set  */
+  const float* time;       /* drift time in us (used when z is NULL): zeta units =
+                              rintf(time * 320), as the fixed format's time64          */
   /* FIXED: n records of 12 bytes, little endian:
    *   u32 time64 (drift time in 1/64 of a 200 ns bin, < 2^30), u16 pad64
    *   (pad position in 1/64 pad, 0 at the sector's pad-plane edge), u16 charge,

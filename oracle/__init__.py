@@ -39,6 +39,7 @@ class _Input(ctypes.Structure):
         ("row", ctypes.c_void_p),
         ("y", ctypes.c_void_p),
         ("z", ctypes.c_void_p),
+        ("time", ctypes.c_void_p),
         ("packed", ctypes.c_void_p),
         ("bz", ctypes.c_double),
         ("vdrift", ctypes.c_double),
@@ -104,7 +105,8 @@ def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=N
     inp.format = tf.fmt
     keep = []
     if tf.fmt == 0:
-        for nm in ("sector", "row", "y", "z"):
+        names = ("sector", "row", "y", "z") if getattr(tf, "z", None) is not None else ("sector", "row", "y", "time")
+        for nm in names:
             a = np.ascontiguousarray(getattr(tf, nm))
             keep.append(a)
             setattr(inp, nm, _vp(a))

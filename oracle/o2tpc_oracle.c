@@ -280,11 +280,17 @@ static int o_ingest(oracle_result* R, const oracle_input* in) {
     } else {
       s = in->sector[i]; r = in->row[i];
       if (s >= O_NSEC || r >= O_NROW) return -1;
-      float yf = in->y[i], zf = in->z[i];
+      float yf = in->y[i];
+      float zf = in->z ? in->z[i] : in->time[i];
       if (!isfinite(yf) || !isfinite(zf)) return -1;
       float yq = rintf(yf * 160.0f);
-      float d = (s < 18) ? (250.0f - zf) : (250.0f + zf);
-      float zq = rintf(d * kz);
+      float zq;
+      if (in->z) {
+        float d = (s < 18) ? (250.0f - zf) : (250.0f + zf);
+        zq = rintf(d * kz);
+      } else {
+        zq = rintf(zf * 320.0f); /* drift time in us -> 1/64 of a 200 ns bin */
+      }
       if (fabsf(yq) > 1048576.0f || fabsf(zq) > 1073741824.0f) return -1;
       yu = (int64_t)yq; zu = (int64_t)zq;
     }

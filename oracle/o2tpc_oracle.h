@@ -19,7 +19,8 @@ typedef struct {
   const uint8_t* sector;   /* float format */
   const uint8_t* row;      /* float format */
   const float* y;          /* cm, local */
-  const float* z;          /* cm, apparent z for a collision at t = 0 */
+  const float* z;          /* cm, apparent z for a collision at t = 0 (NULL: use time) */
+  const float* time;       /* us, drift time (float format without z) */
   const uint8_t* packed;   /* fixed format, n * 12 bytes */
   double bz;               /* T */
   double vdrift;           /* cm/us */

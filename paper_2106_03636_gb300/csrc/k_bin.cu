@@ -31,12 +31,17 @@ __device__ inline bool decode(const TFDesc& t, int i, const GeomConst* __restric
   } else {
     s = __ldg(static_cast<const uint8_t*>(t.in0) + i);
     r = __ldg(static_cast<const uint8_t*>(t.in1) + i);
-    float yf = __ldg(t.y + i), zf = __ldg(t.z + i);
+    float yf = __ldg(t.y + i), zf = t.z ? __ldg(t.z + i) : __ldg(t.time + i);
     if (s >= kNSec || r >= kNRow) { ok = false; s = 0; r = 0; }
     if (!isfinite(yf) || !isfinite(zf)) { ok = false; yf = 0.f; zf = 0.f; }
     float yq = rintf(__fmul_rn(yf, 160.0f));
-    float d = (s < 18) ? __fsub_rn(250.0f, zf) : __fadd_rn(250.0f, zf);
-    float zq = rintf(__fmul_rn(d, G->kz));
+    float zq;
+    if (t.z) {
+      const float d = (s < 18) ? __fsub_rn(250.0f, zf) : __fadd_rn(250.0f, zf);
+      zq = rintf(__fmul_rn(d, G->kz));
+    } else {
+      zq = rintf(__fmul_rn(zf, 320.0f));  // drift time (us) -> 1/64 of a 200 ns bin
+    }
     if (fabsf(yq) > 1048576.0f || fabsf(zq) > 1073741824.0f) { ok = false; yq = 0.f; zq = 0.f; }
     yu = (int)yq;
     zu = (int)zq;

@@ -264,7 +264,9 @@ void input_layout(const o2tpc_tf& t, void* p, TFDesc& d) {
   d.in0 = b;
   d.in1 = b + t.n;
   d.y = py;
-  d.z = py + t.n;
+  // the fourth array is z, or the drift time when the TF carries no z
+  d.z = t.z ? py + t.n : nullptr;
+  d.time = t.z ? nullptr : py + t.n;
 }
 
 void input_upload(const o2tpc_tf& t, void* p, cudaStream_t s) {
@@ -277,7 +279,8 @@ void input_upload(const o2tpc_tf& t, void* p, cudaStream_t s) {
   CK(cudaMemcpyAsync(const_cast<void*>(d.in0), t.sector, t.n, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(const_cast<void*>(d.in1), t.row, t.n, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(const_cast<float*>(d.y), t.y, 4 * t.n, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(const_cast<float*>(d.z), t.z, 4 * t.n, cudaMemcpyHostToDevice, s));
+  if (t.z) CK(cudaMemcpyAsync(const_cast<float*>(d.z), t.z, 4 * t.n, cudaMemcpyHostToDevice, s));
+  else CK(cudaMemcpyAsync(const_cast<float*>(d.time), t.time, 4 * t.n, cudaMemcpyHostToDevice, s));
 }
 
 int read_int(Ctx* c, const int* dptr) {
@@ -309,6 +312,8 @@ void fill_geom(GeomConst& g, double bz, double vd) {
 }
 
 // ------------------------------------------------------------ the batch
+void tune_cache_store(Ctx* c);
+
 // Autotuner: the cell sort and the NeighboursFinder are pure functions of
 // their inputs, so every candidate launch shape is timed on the batch at hand
 // (cell sort: best of two runs; CUDA events on the compute stream) and the fastest
@@ -369,6 +374,7 @@ void autotune(Ctx* c, int n, int nRows, const int* rowCnt, const int* rowMin, co
   c->tune.nf_staged = bn >= 3 ? 1 : 0;
   c->tune.tuned = 1;
   c->tune.tuned_on_clusters = n;
+  tune_cache_store(c);
   launch_grid(nRows, rowCnt, rowMin, rowMax, G, grid, nfBlockStart, c->tune.nf_hits_per_block, totals, st);
 }
 
@@ -427,6 +433,7 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
       d.in1 = t.row;
       d.y = t.y;
       d.z = t.z;
+      d.time = t.time;
     } else if (jobs[i]->upState == 4) {  // uploaded ahead (the batch waited for the copy)
       input_layout(t, jobs[i]->dIn, d);
     } else {
@@ -537,6 +544,7 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
       d.in1 = t.row;
       d.y = t.y;
       d.z = t.z;
+      d.time = t.time;
     } else if (jobs[i]->upState == 4) {
       input_layout(t, jobs[i]->dIn, d);  // uploaded ahead on the copy stream
     } else {
@@ -812,6 +820,61 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   pp.dErr = dErr;
   pp.outMem = outMem;
   pp.launches = g_launch_count;
+}
+
+// Autotuner cache: one line per GPU model, "<name>\t<nf hits>\t<staged>\t<sort threads>".
+std::string gpu_name(int dev) {
+  cudaDeviceProp p{};
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string n = p.name;
+  for (auto& ch : n)
+    if (ch == '\t' || ch == '\n') ch = ' ';
+  return n;
+}
+
+void tune_cache_load(Ctx* c) {
+  if (!c->cfg.tune_cache_path) return;
+  FILE* f = std::fopen(c->cfg.tune_cache_path, "r");
+  if (!f) return;
+  const std::string me = gpu_name(c->cfg.device);
+  char line[512];
+  while (std::fgets(line, sizeof(line), f)) {
+    char* tab = std::strchr(line, '\t');
+    if (!tab) continue;
+    *tab = 0;
+    int nf = 0, staged = 0, sort = 0;
+    if (me != line || std::sscanf(tab + 1, "%d %d %d", &nf, &staged, &sort) != 3) continue;
+    if ((nf == 64 || nf == 128 || nf == 256) && (sort == 128 || sort == 256 || sort == 512)) {
+      c->tune.nf_hits_per_block = nf;
+      c->tune.nf_staged = staged ? 1 : 0;
+      c->tune.sort_threads_per_row = sort;
+      c->tune.tuned = 1;
+    }
+  }
+  std::fclose(f);
+}
+
+void tune_cache_store(Ctx* c) {
+  if (!c->cfg.tune_cache_path) return;
+  const std::string me = gpu_name(c->cfg.device);
+  std::vector<std::string> keep;
+  if (FILE* f = std::fopen(c->cfg.tune_cache_path, "r")) {  // other GPU models' lines stay
+    char line[512];
+    while (std::fgets(line, sizeof(line), f)) {
+      const char* tab = std::strchr(line, '\t');
+      if (tab && std::string(line, (size_t)(tab - line)) != me) keep.emplace_back(line);
+    }
+    std::fclose(f);
+  }
+  FILE* f = std::fopen(c->cfg.tune_cache_path, "w");
+  if (!f) return;
+  for (auto& l : keep) std::fputs(l.c_str(), f);
+  std::fprintf(f, "%s\t%d %d %d\n", me.c_str(), c->tune.nf_hits_per_block, c->tune.nf_staged,
+               c->tune.sort_threads_per_row);
+  std::fclose(f);
 }
 
 void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
@@ -1241,6 +1304,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
   x->tune.nf_hits_per_block = c.nf_hits_per_block;
   x->tune.sort_threads_per_row = c.sort_threads_per_row;
   x->tune.nf_staged = c.nf_staged ? 1 : 0;
+  if (c.flags & O2TPC_FLAG_AUTOTUNE) tune_cache_load(x);
   x->traceCopies = std::getenv("O2TPC_TRACE_COPIES") != nullptr;
   x->traceMode = x->traceCopies ? std::atoi(std::getenv("O2TPC_TRACE_COPIES")) : 0;
   try {
@@ -1315,7 +1379,8 @@ static int check_tf(const Ctx* c, const o2tpc_tf* tf) {
   if (tf->location != O2TPC_LOC_HOST && tf->location != O2TPC_LOC_DEVICE) return O2TPC_EINVAL;
   if (tf->n > 0) {
     if (tf->format == O2TPC_FMT_FIXED && !tf->packed) return O2TPC_EINVAL;
-    if (tf->format == O2TPC_FMT_FLOAT && (!tf->sector || !tf->row || !tf->y || !tf->z)) return O2TPC_EINVAL;
+    if (tf->format == O2TPC_FMT_FLOAT && (!tf->sector || !tf->row || !tf->y || (!tf->z && !tf->time)))
+      return O2TPC_EINVAL;
   }
   if (tf->n >= kMaxBatchHits) return O2TPC_ETOOBIG;
   if (footprint_of(tf->n) > c->cfg.mem_budget) return O2TPC_ETOOBIG;

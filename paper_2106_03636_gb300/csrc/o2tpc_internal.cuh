@@ -69,13 +69,14 @@ struct TFDesc {
   const void* in0;   // FLOAT: sector (uint8) / FIXED: packed records
   const void* in1;   // FLOAT: row (uint8)
   const float* y;    // FLOAT
-  const float* z;    // FLOAT
+  const float* z;    // FLOAT: apparent z, or null
+  const float* time; // FLOAT without z: drift time (us)
   int format;
   int n;             // clusters
   int inBase;        // first batch-global input index of this TF
   int tileBase;      // first tile of this TF
   int nTiles;
-  int pad[3];
+  int pad;
 };
 
 // Device error word bits

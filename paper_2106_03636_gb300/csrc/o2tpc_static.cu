@@ -123,7 +123,7 @@ extern "C" int o2tpc_sort_tf_static(const o2tpc_tf* tf, double vdrift_cm_us, int
   if (tf->format != O2TPC_FMT_FLOAT && tf->format != O2TPC_FMT_FIXED) return O2TPC_EINVAL;
   if (!row_grid || !cell_start || (tf->n > 0 && (!sorted_orig || !sorted_yz))) return O2TPC_EINVAL;
   if (tf->n > 0 && tf->format == O2TPC_FMT_FIXED && !tf->packed) return O2TPC_EINVAL;
-  if (tf->n > 0 && tf->format == O2TPC_FMT_FLOAT && (!tf->sector || !tf->row || !tf->y || !tf->z))
+  if (tf->n > 0 && tf->format == O2TPC_FMT_FLOAT && (!tf->sector || !tf->row || !tf->y || (!tf->z && !tf->time)))
     return O2TPC_EINVAL;
   const long long cellsMax = (long long)tf->n / kHitsPerCell + 46ll * kRowsPerTF + 1;
   if (cell_capacity < (uint64_t)cellsMax + 1) return O2TPC_EINVAL;
@@ -147,6 +147,7 @@ extern "C" int o2tpc_sort_tf_static(const o2tpc_tf* tf, double vdrift_cm_us, int
   d.in1 = tf->row;
   d.y = tf->y;
   d.z = tf->z;
+  d.time = tf->time;
   d.tileBase = 0;
   d.nTiles = (n + kStaticTile - 1) / kStaticTile;
   int2 tiles[kStaticTiles];

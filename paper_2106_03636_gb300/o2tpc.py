@@ -60,6 +60,7 @@ class o2tpc_config(ctypes.Structure):
         ("graph_max_clusters", ctypes.c_uint64),
         ("graph_max_tfs", ctypes.c_int32),
         ("nf_staged", ctypes.c_int32),
+        ("tune_cache_path", ctypes.c_char_p),
     ]
 
 
@@ -84,6 +85,7 @@ class o2tpc_tf(ctypes.Structure):
         ("row", ctypes.c_void_p),
         ("y", ctypes.c_void_p),
         ("z", ctypes.c_void_p),
+        ("time", ctypes.c_void_p),
         ("packed", ctypes.c_void_p),
         ("user_tag", ctypes.c_uint64),
     ]
@@ -272,7 +274,8 @@ def result_to_dict(r: o2tpc_result) -> dict:
 def make_tf(tf, location: int = O2TPC_LOC_HOST, arrays: dict | None = None, user_tag: int = 0) -> o2tpc_tf:
     """Builds an ``o2tpc_tf`` from a ``synth.TimeFrame`` (host numpy arrays)
     or from ``arrays`` (numpy or torch tensors, host or device)."""
-    src = arrays if arrays is not None else {k: getattr(tf, k) for k in ("sector", "row", "y", "z", "packed")}
+    src = arrays if arrays is not None else {k: getattr(tf, k, None) for k in ("sector", "row", "y", "z", "time",
+                                                                            "packed")}
     t = o2tpc_tf()
     t.n = int(tf.n)
     t.format = int(tf.fmt)
@@ -280,7 +283,11 @@ def make_tf(tf, location: int = O2TPC_LOC_HOST, arrays: dict | None = None, user
     if t.format == O2TPC_FMT_FIXED:
         t.packed = _ptr(src["packed"])
     else:
-        t.sector, t.row, t.y, t.z = (_ptr(src[k]) for k in ("sector", "row", "y", "z"))
+        t.sector, t.row, t.y = (_ptr(src[k]) for k in ("sector", "row", "y"))
+        if src.get("z") is not None:
+            t.z = _ptr(src["z"])
+        else:
+            t.time = _ptr(src["time"])
     t.user_tag = user_tag
     return t
 
@@ -296,7 +303,8 @@ class Tracker:
     def __init__(self, device: int = 0, bz: float = 0.5, vdrift: float = 2.58, flags: int = 0,
                  mem_budget: int = 0, max_inflight: int = 0, max_batch: int = 0, torch_memory: bool = False,
                  batch_full_clusters: int = 0, nf_hits_per_block: int = 0, sort_threads_per_row: int = 0,
-                 graph_max_clusters: int = 0, graph_max_tfs: int = 0, nf_staged: bool = False):
+                 graph_max_clusters: int = 0, graph_max_tfs: int = 0, nf_staged: bool = False,
+                 tune_cache_path: str | None = None):
         self.cfg = o2tpc_config()
         self.cfg.device = device
         self.cfg.bz_tesla = bz
@@ -311,6 +319,8 @@ class Tracker:
         self.cfg.graph_max_clusters = graph_max_clusters
         self.cfg.graph_max_tfs = graph_max_tfs
         self.cfg.nf_staged = int(nf_staged)
+        self._cache_path = tune_cache_path.encode() if tune_cache_path else None
+        self.cfg.tune_cache_path = self._cache_path
         self._keep = []
         import torch
 

@@ -99,7 +99,8 @@ class TimeFrame:
     """One Time Frame of clusters in submission order.
 
     ``fmt`` FMT_FLOAT: ``sector``, ``row`` (uint8), ``y``, ``z`` (float32;
-    z is the apparent z for a collision at t = 0, side * (250 - v_d t)).
+    z is the apparent z for a collision at t = 0, side * (250 - v_d t)), or
+    ``time`` (float32 drift time in us) instead of ``z``.
     ``fmt`` FMT_FIXED: ``packed`` (uint8 [n, 12]) records.
     ``truth_track`` is the generating track id (-1 noise); ``truth`` holds
     per-track pt, eta, phi0, zv, t0, q, coll.
@@ -110,6 +111,7 @@ class TimeFrame:
     row: np.ndarray
     y: np.ndarray | None = None
     z: np.ndarray | None = None
+    time: np.ndarray | None = None
     packed: np.ndarray | None = None
     truth_track: np.ndarray | None = None
     truth: dict = field(default_factory=dict)
@@ -257,3 +259,19 @@ def serving_pool(seed: int = 20210611, n_tf: int = 24, orbits: int = TF_ORBITS, 
         out.append(generate(seed=seed * 1000 + i, t0=t0, ntracks=ntr, zvtx_sigma=5.0, t_window=t_len, fmt=fmt,
                             with_truth=False, name=name, **kw))
     return out
+
+
+def float_time_from_fixed(tf: TimeFrame) -> TimeFrame:
+    """The same clusters as a fixed-point TF, in float format with drift time
+    instead of z: y = y_u / 160 cm and time = time64 / 320 us, which quantize
+    back to the same integer units."""
+    rec = tf.packed
+    t64 = rec[:, 0:4].copy().view(np.uint32).ravel()
+    pad = rec[:, 4:6].copy().view(np.uint16).ravel().astype(np.int64)
+    row = rec[:, 8].copy()
+    sector = rec[:, 9].copy()
+    npads = np.floor(2.0 * (85.0 + row.astype(np.float64) * 160.0 / 151.0) * math.tan(math.radians(10.0)) / 0.4)
+    yu = pad - 32 * npads.astype(np.int64)
+    return TimeFrame(n=tf.n, fmt=FMT_FLOAT, sector=sector, row=row, y=(yu / 160.0).astype(np.float32),
+                     time=(t64.astype(np.float64) / 320.0).astype(np.float32), bz=tf.bz, vdrift=tf.vdrift,
+                     name=tf.name + "_time")

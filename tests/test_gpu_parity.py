@@ -221,3 +221,32 @@ def test_captured_path_equals_regular_path():
                     assert y["status"] == 0 and y["stats"]["captured"] == captured
                     for k in keys:
                         assert np.array_equal(x[k], y[k]), k
+
+
+def test_float_time_input_parity(trk):
+    """Float input with drift time instead of z: bit-exact integer stages and
+    the track criteria against the oracle on the same input."""
+    tf = synth.float_time_from_fixed(synth.full_tpc_1ms(seed=62, n_coll=2, fmt=synth.FMT_FIXED))
+    ticket, res, o = run_both(trk, tf)
+    compare_stages(trk, ticket, o)
+    print(compare_tracks(res, o, ZUNIT))
+    trk.release(ticket, res)
+
+
+def test_autotuner_cache_file(tmp_path):
+    """The autotuner's choice is written per GPU model and read back by the
+    next context, which then counts as tuned without timing anything."""
+    path = str(tmp_path / "tune.txt")
+    tf = synth.full_tpc_1ms(seed=22, n_coll=3)
+    with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_AUTOTUNE, tune_cache_path=path) as a:
+        a.track(tf)
+        first = a.tuning()
+    assert first["tuned"]
+    name, vals = open(path).read().strip().split("\t")
+    assert vals.split() == [str(first["nf_hits_per_block"]), str(int(first["nf_staged"])),
+                            str(first["sort_threads_per_row"])]
+    with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_AUTOTUNE, tune_cache_path=path) as b:
+        t = b.tuning()
+        assert t["tuned"] and t["tuned_on_clusters"] == 0
+        for k in ("nf_hits_per_block", "nf_staged", "sort_threads_per_row"):
+            assert t[k] == first[k]

@@ -176,3 +176,18 @@ def test_float_and_fixed_formats_agree():
 
     sa, sb = sets(a), sets(b)
     assert len(sa & sb) >= 0.98 * max(len(sa), len(sb))
+
+
+def test_float_time_input_equals_fixed_input():
+    """Float input carrying drift time instead of z quantizes to the same
+    integer units as the fixed-point records (time64 = rint(t * 320)), so the
+    whole chain gives identical results."""
+    tf = synth.full_tpc_1ms(seed=61, n_coll=1, ntracks=600, fmt=synth.FMT_FIXED)
+    tt = synth.float_time_from_fixed(tf)
+    assert tt.z is None and tt.time is not None
+    fields = ["yu", "zu", "sorted_orig", "up", "dn", "starts", "trk_off", "trk_cl", "trk_par"]
+    a = oracle.run(tf, fields=fields)
+    b = oracle.run(tt, fields=fields)
+    for k in fields:
+        assert np.array_equal(a[k], b[k]), k
+    assert len(a["trk_off"]) > 100
