@@ -346,7 +346,7 @@ __device__ int refit_chain(int head, int tail, const SectorTrackBufs& sb, const 
   frame = sb.sector[tail];
   const int hl = sb.off[tail + 1] - 1;
   const float* so = sb.out + (size_t)tail * 21;
-  const int2 pl = syz[sb.hits[hl]];
+  const int2 pl = sb.yz[hl];
   int yref = pl.x;
   const T xl = sizeof(T) == 8 ? (T)G->rowx_d[sb.rows[hl]] : (T)G->rowx[sb.rows[hl]];
   kf_reset<T>(t, xl, T(0), (T)(pl.y - zref) * zunit, (T)so[3], (T)so[4], (T)so[5]);
@@ -358,7 +358,7 @@ __device__ int refit_chain(int head, int tail, const SectorTrackBufs& sb, const 
     const int sec = sb.sector[sg];
     for (int i = sb.off[sg + 1] - 1; i >= sb.off[sg]; --i) {
       if (first) { first = false; continue; }
-      const int2 p = syz[sb.hits[i]];
+      const int2 p = sb.yz[i];
       if (sec != frame) {
         const int dd = ((sec % 18) - (frame % 18) + 18) % 18;
         const T sgn = (dd == 1) ? T(1) : T(-1);
@@ -440,8 +440,8 @@ __global__ void __launch_bounds__(128) k_final_refit(const int* __restrict__ nHe
   const int inBase = tfs[sb.tf[head]].inBase;
   int o = ob.off[t];
   for (int c = head, j = 0; j < nseg; c = mb.next[c], ++j)
-    for (int i = sb.off[c]; i < sb.off[c + 1]; ++i) ob.cl[o++] = sorig[sb.hits[i]] - inBase;
-  const int zref = syz[sb.hits[sb.off[head]]].y;
+    for (int i = sb.off[c]; i < sb.off[c + 1]; ++i) ob.cl[o++] = sb.orig[i] - inBase;
+  const int zref = sb.yz[sb.off[head]].y;
   KState<float> sf;
   float c2f;
   int used, frame, yref;
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(128) k_final_refit64(const int* __restrict__ h
     const int head = heads[t];
     int nseg;
     const int tail = chain_tail(head, mb.next, &nseg);
-    const int zref = syz[sb.hits[sb.off[head]]].y;
+    const int zref = sb.yz[sb.off[head]].y;
     KState<double> sd;
     double c2d;
     int used, frame, yref;

@@ -431,7 +431,8 @@ __global__ void __launch_bounds__(128) k_segments_count(const int* __restrict__ 
 __global__ void __launch_bounds__(128) k_segments_write(const int* __restrict__ nTlDev, OwnCtx o, TrackletBufs tb,
                                                         const int* __restrict__ segPos,
                                                         const int* __restrict__ segHitPos,
-                                                        const int2* __restrict__ syz, SectorTrackBufs sb, int capSt,
+                                                        const int2* __restrict__ syz,
+                                                        const int* __restrict__ sorig, SectorTrackBufs sb, int capSt,
                                                         int capHits) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= *nTlDev) return;
@@ -478,6 +479,17 @@ __global__ void __launch_bounds__(128) k_segments_write(const int* __restrict__ 
   flush();
 }
 
+// K8d: coordinates and input index of every sector-track hit, gathered once
+// (one thread per hit) for the sector fits and the final refit.
+__global__ void k_st_gather(const int* __restrict__ nHitsDev, SectorTrackBufs sb, const int2* __restrict__ syz,
+                            const int* __restrict__ sorig) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= *nHitsDev) return;
+  const int h = sb.hits[i];
+  sb.yz[i] = syz[h];
+  sb.orig[i] = sorig[h];
+}
+
 __global__ void __launch_bounds__(128) k_sector_fit(const int* __restrict__ nStDev, TrackletBufs tb,
                                                     const int2* __restrict__ syz, const GeomConst* __restrict__ G,
                                                     SectorTrackBufs sb) {
@@ -485,7 +497,7 @@ __global__ void __launch_bounds__(128) k_sector_fit(const int* __restrict__ nStD
   if (id >= *nStDev) return;
   const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
   const int b = sb.off[id], m = sb.off[id + 1] - b;
-  const int* H = sb.hits + b;
+  const int2* P = sb.yz + b;
   const uint8_t* Rw = sb.rows + b;
   const int zref = sb.zref[id];
   KState<float> sd;
@@ -496,21 +508,21 @@ __global__ void __launch_bounds__(128) k_sector_fit(const int* __restrict__ nStD
     if (kf_prop<float>(tmp, xa, bzc) == 0) sd = tmp;
   }
   KState<float> t;
-  int2 p = syz[H[0]];
+  int2 p = P[0];
   const int yref = p.x;
   kf_reset<float>(t, xa, hit_y(p.x, yref), hit_z(p.y, zref, zunit), sd.p[2], sd.p[3], sd.p[4]);
   for (int i = 1; i < m; ++i) {
     if (kf_prop<float>(t, G->rowx[Rw[i]], bzc) != 0) continue;
-    p = syz[H[i]];
+    p = P[i];
     kf_update<float>(t, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
   }
   store_state(sb.out + (size_t)id * 21, t, yref);
   KState<float> u;
-  p = syz[H[m - 1]];
+  p = P[m - 1];
   kf_reset<float>(u, G->rowx[Rw[m - 1]], hit_y(p.x, yref), hit_z(p.y, zref, zunit), t.p[2], t.p[3], t.p[4]);
   for (int i = m - 2; i >= 0; --i) {
     if (kf_prop<float>(u, G->rowx[Rw[i]], bzc) != 0) continue;
-    p = syz[H[i]];
+    p = P[i];
     kf_update<float>(u, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
   }
   store_state(sb.in + (size_t)id * 21, u, yref);
@@ -588,10 +600,18 @@ void launch_segments_count(int nTl, const int* nTlDev, const int* secBegin, cons
 
 void launch_segments_write(int nTl, const int* nTlDev, const int* secBegin, const int* wide, const void* w,
                            TrackletBufs tb, const int* segPos, const int* segHitPos, const int2* syz,
-                           SectorTrackBufs sb, int capSt, int capHits, cudaStream_t st) {
+                           const int* sorig, SectorTrackBufs sb, int capSt, int capHits, cudaStream_t st) {
   if (nTl > 0) {
     k_segments_write<<<(nTl + 127) / 128, 128, 0, st>>>(nTlDev, OwnCtx{secBegin, wide, const_cast<void*>(w)}, tb,
-                                                         segPos, segHitPos, syz, sb, capSt, capHits);
+                                                         segPos, segHitPos, syz, sorig, sb, capSt, capHits);
+    ++g_launch_count;
+  }
+}
+
+void launch_st_gather(int nHits, const int* nHitsDev, SectorTrackBufs sb, const int2* syz, const int* sorig,
+                      cudaStream_t st) {
+  if (nHits > 0) {
+    k_st_gather<<<(nHits + 255) / 256, 256, 0, st>>>(nHitsDev, sb, syz, sorig);
     ++g_launch_count;
   }
 }

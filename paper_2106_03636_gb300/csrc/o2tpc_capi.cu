@@ -697,12 +697,16 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   sb.off = dalloc<int>(M, nSt + 1);
   sb.hits = dalloc<int>(M, nStHits);
   sb.rows = dalloc<uint8_t>(M, nStHits);
+  sb.yz = dalloc<int2>(M, nStHits);
+  sb.orig = dalloc<int>(M, nStHits);
   sb.in = dalloc<float>(M, (size_t)nSt * 21);
   sb.out = dalloc<float>(M, (size_t)nSt * 21);
-  launch_segments_write(nTl, &C->nTl, secBegin, wide, w, tb, segPos, segHitPos, syz, sb, nSt, nStHits, st);
+  launch_segments_write(nTl, &C->nTl, secBegin, wide, w, tb, segPos, segHitPos, syz, sorig, sb, nSt, nStHits, st);
   CKL();
   // CSR end: sb.off[nSt] = nStHits
   launch_count_at(segPos, &C->nTl, &C->nSt, nSt, &C->overflow, st, segHitPos, &C->nStHits, nStHits, sb.off);
+  CKL();
+  launch_st_gather(nStHits, &C->nStHits, sb, syz, sorig, st);
   CKL();
   CK(cudaEventRecord(c->evs[6], st));
   launch_sector_fit(nSt, &C->nSt, tb, syz, G, sb, st);

@@ -100,6 +100,8 @@ size_t graph_carve(GraphArena& A, char* base) {
   take(A.sb.off, k.stCap + 1);
   take(A.sb.hits, k.stHitsCap);
   take(A.sb.rows, k.stHitsCap);
+  take(A.sb.yz, k.stHitsCap);
+  take(A.sb.orig, k.stHitsCap);
   take(A.sb.in, (size_t)k.stCap * 21);
   take(A.sb.out, (size_t)k.stCap * 21);
   take(A.stTfBegin, k.BCap + 1);
@@ -173,10 +175,11 @@ void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, bool nf
   launch_segments_count(k.tlCap, &C->nTl, A.secBegin, A.wide, A.w, A.tb, A.nSeg, A.nSegHits, st);
   scan_exclusive(A.nSeg, A.segPos, k.tlCap, &C->nTl, A.scratch, st);
   scan_exclusive(A.nSegHits, A.segHitPos, k.tlCap, &C->nTl, A.scratch, st);
-  launch_segments_write(k.tlCap, &C->nTl, A.secBegin, A.wide, A.w, A.tb, A.segPos, A.segHitPos, A.syz, A.sb,
-                        k.stCap, k.stHitsCap, st);
+  launch_segments_write(k.tlCap, &C->nTl, A.secBegin, A.wide, A.w, A.tb, A.segPos, A.segHitPos, A.syz, A.sorig,
+                        A.sb, k.stCap, k.stHitsCap, st);
   launch_count_at(A.segPos, &C->nTl, &C->nSt, k.stCap, &C->overflow, st, A.segHitPos, &C->nStHits, k.stHitsCap,
                   A.sb.off);
+  launch_st_gather(k.stHitsCap, &C->nStHits, A.sb, A.syz, A.sorig, st);
   launch_sector_fit(k.stCap, &C->nSt, A.tb, A.syz, G, A.sb, st);
   launch_iota(A.tfKeys, k.BCap + 1, st);
   launch_lower_bounds(A.sb.tf, &C->nSt, A.tfKeys, k.BCap + 1, A.stTfBegin, st);

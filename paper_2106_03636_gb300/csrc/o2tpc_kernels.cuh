@@ -94,6 +94,8 @@ struct SectorTrackBufs {
   int* off;       // [nSt + 1] into hits
   int* hits;      // sorted hit indices, ascending rows
   uint8_t* rows;  // row of each hit
+  int2* yz;       // coordinates of each hit (gathered once for the fits)
+  int* orig;      // batch-global input index of each hit
   float* in;      // [nSt * 21] state at the innermost hit (inward fit)
   float* out;     // [nSt * 21] state at the outermost hit (outward fit)
 };
@@ -106,7 +108,10 @@ void launch_segments_count(int nTl, const int* nTlDev, const int* secBegin, cons
 // capSt / capHits: room in the sector-track buffers (writes past them dropped)
 void launch_segments_write(int nTl, const int* nTlDev, const int* secBegin, const int* wide, const void* w,
                            TrackletBufs tb, const int* segPos, const int* segHitPos, const int2* syz,
-                           SectorTrackBufs sb, int capSt, int capHits, cudaStream_t st);
+                           const int* sorig, SectorTrackBufs sb, int capSt, int capHits, cudaStream_t st);
+// sb.yz / sb.orig of every sector-track hit (after the CSR end is written)
+void launch_st_gather(int nHits, const int* nHitsDev, SectorTrackBufs sb, const int2* syz, const int* sorig,
+                      cudaStream_t st);
 void launch_sector_fit(int nSt, const int* nStDev, const TrackletBufs tb, const int2* syz, const GeomConst* G,
                        SectorTrackBufs sb, cudaStream_t st);
 
