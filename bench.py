@@ -268,17 +268,30 @@ def roofline(stage, names, n, peak, peak_kind, workload=None):
             "bytes_per_cluster": STAGE_BYTES[k], "ms_per_launch": ms}
 
 
-def device_max(ms, world, local):
-    """Max over ranks of a duration (replicas; the only collective)."""
+def device_max(ms, world, local, device=None):
+    """Max over ranks of a duration (replicas; the only collective).  The
+    tensor lives on the rank's GPU (NCCL), or on `device` (gloo on CPU)."""
     if world == 1:
         return ms
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([ms], device=f"cuda:{local}")
+    t = torch.tensor([ms], device=device or f"cuda:{local}")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.barrier()
     return float(t.item())
+
+
+def replica_seed(seed: int, rank: int) -> int:
+    """Each replica tracks its own Time Frames (weak scaling): seeds differ
+    by rank."""
+    return seed + 1000 * rank
+
+
+def aggregate_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return world * units_per_rank / (ms / 1e3)
 
 
 def run_chunks(args, rank, world, local):
@@ -290,7 +303,7 @@ def run_chunks(args, rank, world, local):
 
     from paper_2106_03636_gb300 import o2tpc, synth
 
-    chunks = synth.chunk_mix(seed=20210610 + 1000 * rank)
+    chunks = synth.chunk_mix(seed=replica_seed(20210610, rank))
     n = sum(c.n for c in chunks)
     dev = [{"packed": torch.from_numpy(c.packed).to(f"cuda:{local}")} for c in chunks]
     torch.cuda.synchronize()
@@ -401,7 +414,7 @@ def run_serving(args, rank, world, local):
 
     from paper_2106_03636_gb300 import o2tpc, synth
 
-    pool = synth.serving_pool(seed=20210611 + 1000 * rank)
+    pool = synth.serving_pool(seed=replica_seed(20210611, rank))
     pin = [{"packed": torch.from_numpy(t.packed).pin_memory()} for t in pool]
     rng = np.random.default_rng(20210611 + rank)
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate_hz, int(args.rate_hz * args.serve_seconds * 2) + 10))
@@ -556,7 +569,7 @@ def main():
     if args.workload == "serving":
         return run_serving(args, rank, world, local)
 
-    tf, cfg = make_workload(args.workload, args.seed + 1000 * rank)
+    tf, cfg = make_workload(args.workload, replica_seed(args.seed, rank))
     n = tf.n
     host_in = torch.from_numpy(tf.packed if tf.fmt == 1 else np.zeros(1, np.uint8))
     dev = {}
@@ -604,12 +617,7 @@ def main():
             launches += int(r["stats"]["n_launches"])
         e1.record(st)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-            dist.barrier()
+        ms = device_max(e0.elapsed_time(e1), world, local)
         return ms, stage / args.steps, launches, lat, r
 
     def served(location, arrays, total, inflight):
@@ -643,12 +651,7 @@ def main():
             done += 1
         e1.record(st)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-            dist.barrier()
+        ms = device_max(e0.elapsed_time(e1), world, local)
         return ms, lat, sizes, int(round(launches))
 
     n_served = max(6, 2 * args.steps)
@@ -659,8 +662,8 @@ def main():
         ms_s, lat_s, sizes_s, launches_s = served(o2tpc.O2TPC_LOC_DEVICE, dev, n_served, args.inflight)
     clocks = clk.summary()
     ms_step = ms / args.steps
-    plain_value = world * n / (ms_step / 1e3)
-    served_value = world * n * n_served / (ms_s / 1e3)
+    plain_value = aggregate_rate(n, world, ms_step)
+    served_value = aggregate_rate(n * n_served, world, ms_s)
     value = served_value
 
     # e2e: pinned host input, H2D and result download inside the timed region
