@@ -661,7 +661,7 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   tb.zref = dalloc<int>(M, nTl);
   tb.rbase = dalloc<int>(M, nTl);
   int* workCounter = dalloc<int>(M, 4);
-  launch_tracklets(nTl, nullptr, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st, c->evTl);
+  launch_tracklets(nTl, &C->nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st, c->evTl);
   CKL();
 
   // ---- A9: selection

@@ -81,7 +81,7 @@ struct TrackletBufs {
 };
 // passEnd: optional 4 events recorded after the chain-fit, outward, refit and
 // inward passes.
-// nTlDev: device tracklet count, or null to take nTl as exact
+// nTl sizes the grids; the kernels read the count at nTlDev
 void launch_tracklets(int nTl, const int* nTlDev, int* workCounter, const int* starts, const int* up,
                       const RowGrid* grid, int nRows, const int* cellStart, const int2* syz, const GeomConst* G,
                       TrackletBufs tb, cudaStream_t st, cudaEvent_t* passEnd = nullptr);
