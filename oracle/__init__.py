@@ -45,6 +45,8 @@ class _Input(ctypes.Structure):
         ("vdrift", ctypes.c_double),
         ("sector_mask", ctypes.c_uint64),
         ("reverse_tracklet_order", ctypes.c_int32),
+        ("coll_time", ctypes.c_void_p),
+        ("n_coll", ctypes.c_int64),
     ]
 
 
@@ -69,6 +71,8 @@ def _load():
         lib.oracle_update.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
         lib.oracle_rotate.restype = ctypes.c_int32
         lib.oracle_rotate.argtypes = [dp, dp, dp, ctypes.c_double]
+        lib.oracle_dca_arc.restype = ctypes.c_double
+        lib.oracle_dca_arc.argtypes = [ctypes.c_double] * 4
         lib.oracle_fit_points.restype = ctypes.c_int32
         lib.oracle_fit_points.argtypes = [ctypes.c_int32, dp, dp, dp, ctypes.c_double, dp, dp]
         _lib = lib
@@ -84,6 +88,7 @@ FIELDS = [
     "tl_hits", "tl_state", "st_sector", "st_tracklet", "st_zref", "st_off", "st_hits", "st_in", "st_out",
     "st_next", "st_prev", "pair_ab", "pair_chi2", "trk_off", "trk_cl", "trk_x", "trk_alpha", "trk_par",
     "trk_cov", "trk_chi2", "trk_ndf", "trk_sector", "trk_flags", "trk_zref", "trk_head", "trk_nseg",
+    "trk_t0", "trk_t0err", "trk_t0lo", "trk_t0hi", "trk_mate", "trk_coll", "mpair_ab", "mpair_chi2",
 ]
 
 
@@ -95,10 +100,11 @@ def _vp(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=None) -> dict:
+def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=None, coll_time=None) -> dict:
     """Runs the oracle on a ``synth.TimeFrame``-like object (attributes n,
-    fmt, sector, row, y, z, packed, bz, vdrift).  Returns a dict of numpy
-    arrays (copies) named as in ``FIELDS``."""
+    fmt, sector, row, y, z, packed, bz, vdrift, and optionally coll_time,
+    the TF's interaction times in us).  ``coll_time`` overrides the TF's.
+    Returns a dict of numpy arrays (copies) named as in ``FIELDS``."""
     lib = _load()
     inp = _Input()
     inp.n = tf.n
@@ -118,6 +124,12 @@ def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=N
     inp.vdrift = tf.vdrift
     inp.sector_mask = sector_mask
     inp.reverse_tracklet_order = int(reverse_tracklet_order)
+    ct = coll_time if coll_time is not None else getattr(tf, "coll_time", None)
+    if ct is not None and len(ct):
+        ct = np.ascontiguousarray(np.asarray(ct, dtype=np.float64))
+        keep.append(ct)
+        inp.coll_time = _vp(ct)
+        inp.n_coll = len(ct)
     st = ctypes.c_int32()
     h = lib.oracle_run(ctypes.byref(inp), ctypes.byref(st))
     if st.value != 0 or not h:
@@ -145,8 +157,9 @@ def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=N
         out["trk_par"] = out["trk_par"].reshape(-1, 5)
     if "trk_cov" in out:
         out["trk_cov"] = out["trk_cov"].reshape(-1, 15)
-    if "pair_ab" in out:
-        out["pair_ab"] = out["pair_ab"].reshape(-1, 2)
+    for nm in ("pair_ab", "mpair_ab"):
+        if nm in out:
+            out[nm] = out[nm].reshape(-1, 2)
     return out
 
 
@@ -190,3 +203,9 @@ def fit_points(x, y, z, bz: float, seed_p5, c15_init=None):
     c = np.zeros(15, np.float64) if c15_init is None else np.array(c15_init, np.float64)
     rc = lib.oracle_fit_points(len(x), _dptr(x), _dptr(y), _dptr(z), bz, _dptr(p), _dptr(c))
     return rc, p, c
+
+
+def dca_arc(x0: float, y0: float, snp: float, k: float) -> float:
+    """Signed transverse arc length from (x0, y0), sin(phi) = snp, curvature
+    k = dphi/ds, to the closest approach to the origin."""
+    return float(_load().oracle_dca_arc(x0, y0, snp, k))

@@ -112,7 +112,11 @@ struct oracle_result {
   int64_t* trk_off; int32_t* trk_cl; int64_t trk_ncl;
   double *trk_x, *trk_alpha, *trk_par, *trk_cov, *trk_chi2;
   int32_t *trk_ndf, *trk_sector, *trk_flags, *trk_zref, *trk_head, *trk_nseg;
-  o_field fields[64]; int nf;
+  /* continuous readout: t0 (us), its error and bounds, membrane partner, collision */
+  double *trk_t0, *trk_t0err, *trk_t0lo, *trk_t0hi;
+  int32_t *trk_mate, *trk_coll;
+  int64_t nmpair; int32_t* mpair_ab; double* mpair_chi2;
+  o_field fields[80]; int nf;
 };
 
 /* ---------------------------------------------------- Kalman building blocks */
@@ -822,6 +826,215 @@ static void o_final(oracle_result* R) {
   free(hs); free(hsec);
 }
 
+/* ------------------------------------------- continuous-readout completion
+ * Sec. 2: with continuous readout the drift coordinate of a cluster is
+ * v_d (t0 + t_drift), so a track's own clusters fix its collision time t0
+ * only up to the unknown z of its vertex, and tracks are assigned to
+ * collisions after tracking.  The paper gives no method; the readings here
+ * (all constants below are ours):
+ *  - t0 bounds from the clusters: every cluster lies at 0 <= |z| <= 250 cm,
+ *    so zeta_max - 250 <= v_d t0 <= zeta_min;
+ *  - vertex t0: the track extrapolated to its closest approach to the beam
+ *    axis in the transverse plane, assuming z_vertex = 0 there, clamped into
+ *    the bounds; its error adds the beam-spot length O_SIGMA_ZV;
+ *  - membrane crossing: a track segment that runs towards the central
+ *    membrane (z = 0) and ends, and a segment of the other side (in the
+ *    same sector angle or a neighbouring one) that starts a few rows further
+ *    out, are the two halves of
+ *    one track when their y, sin(phi), tan(lambda), q/pT agree (chi2 on 4
+ *    parameters) at the outer segment's first cluster.  z is continuous at
+ *    the crossing, so at any common x the membrane sits at the mean of the
+ *    two segments' drift coordinates, which gives t0 without any assumption
+ *    on the vertex; one partner per segment, greedy in (chi2, inner, outer);
+ *  - collision assignment: among the interaction times of the TF (input,
+ *    sorted ascending) compatible with the t0 bounds (plus O_T0_SLACK), the
+ *    one nearest to the track's t0 (ties: the earlier).                   */
+#define O_SIGMA_ZV 5.0       /* beam-spot length, cm                          */
+#define O_MEM_ROWGAP 10      /* outer segment starts 1..10 rows further out   */
+#define O_MEM_DZU 384        /* |zeta_out(inner) - zeta_in(outer)|, units      */
+#define O_CHI2_MEM 25.0      /* chi2 on 4 parameters                           */
+#define O_MEM_ZTOL 1.0       /* membrane zeta may sit this far below a cluster */
+#define O_T0_SLACK 0.3       /* us, on the t0 bounds when assigning            */
+
+/* Signed transverse arc length from (x0, y0, direction phi0) to the point of
+ * the circle of curvature k (dphi/ds) closest to the origin: with
+ * t = -(x0 cos + y0 sin) and d = x0 sin - y0 cos, the turning angle to that
+ * point is atan2(k t, 1 - k d), which tends to the straight line's t. */
+static double o_dca_arc(double x0, double y0, double snp, double k) {
+  double csp = sqrt((1.0 - snp) * (1.0 + snp));
+  double t = -(x0 * csp + y0 * snp), d = x0 * snp - y0 * csp;
+  if (k == 0.0) return t;
+  return atan2(k * t, 1.0 - k * d) / k;
+}
+
+double oracle_dca_arc(double x0, double y0, double snp, double k) { return o_dca_arc(x0, y0, snp, k); }
+
+typedef struct { int32_t zmin, zmax, zin, zout, rin, rout, sin, sout; } o_ends;
+
+static void o_continuous(oracle_result* R, const oracle_input* in) {
+  int64_t nt = R->ntrk, n1 = nt + 1;
+  double zu = R->zunit, vd = in->vdrift;
+  R->trk_t0 = (double*)calloc((size_t)n1, 8); R->trk_t0err = (double*)calloc((size_t)n1, 8);
+  R->trk_t0lo = (double*)calloc((size_t)n1, 8); R->trk_t0hi = (double*)calloc((size_t)n1, 8);
+  R->trk_mate = (int32_t*)malloc((size_t)n1 * 4); R->trk_coll = (int32_t*)malloc((size_t)n1 * 4);
+  o_ends* E = (o_ends*)calloc((size_t)n1, sizeof(o_ends));
+  for (int64_t i = 0; i < nt; ++i) {
+    o_ends* e = E + i;
+    int32_t c0 = R->trk_cl[R->trk_off[i]], c1 = R->trk_cl[R->trk_off[i + 1] - 1];
+    e->zin = R->zu[c0]; e->zout = R->zu[c1];
+    e->rin = R->rid[c0] % O_NROW; e->sin = R->rid[c0] / O_NROW;
+    e->rout = R->rid[c1] % O_NROW; e->sout = R->rid[c1] / O_NROW;
+    e->zmin = e->zmax = e->zin;
+    for (int64_t q = R->trk_off[i]; q < R->trk_off[i + 1]; ++q) {
+      int32_t z = R->zu[R->trk_cl[q]];
+      if (z < e->zmin) e->zmin = z;
+      if (z > e->zmax) e->zmax = z;
+    }
+    R->trk_t0lo[i] = ((double)e->zmax * zu - 250.0) / vd;
+    R->trk_t0hi[i] = (double)e->zmin * zu / vd;
+    R->trk_mate[i] = -1;
+  }
+  /* membrane pairs: inner segment a (towards the membrane), outer b */
+  int64_t np = 0, pcap = 256;
+  o_pair* P = (o_pair*)malloc(sizeof(o_pair) * pcap);
+  double* zmid = NULL; /* membrane zeta (cm, absolute) and its variance per pair */
+  double* zvar = NULL;
+  zmid = (double*)malloc(sizeof(double) * pcap); zvar = (double*)malloc(sizeof(double) * pcap);
+  /* tracks by the sector of their first cluster, ascending ids */
+  int64_t bstart[37] = {0};
+  for (int64_t i = 0; i < nt; ++i) bstart[E[i].sin + 1]++;
+  for (int q = 0; q < 36; ++q) bstart[q + 1] += bstart[q];
+  int64_t* bfill = (int64_t*)calloc(36, sizeof(int64_t));
+  int32_t* bsec = (int32_t*)malloc(sizeof(int32_t) * n1);
+  for (int64_t i = 0; i < nt; ++i) bsec[bstart[E[i].sin] + bfill[E[i].sin]++] = (int32_t)i;
+  free(bfill);
+  for (int64_t a = 0; a < nt; ++a) {
+    const o_ends* ea = E + a;
+    const double* pa = R->trk_par + 5 * a;
+    int sa = o_side(ea->sout);
+    if ((R->trk_flags[a] & 4) || R->trk_sector[a] != ea->sin) continue;
+    if (ea->rout > O_NROW - 2 || !(sa * pa[3] < 0.0)) continue;
+    for (int d = -1; d <= 1; ++d) {
+      /* the outer piece may start one sector angle off the inner piece's end */
+      int jb = (ea->sout % 18 + d + 18) % 18;
+      int sb_need = (sa > 0 ? 18 : 0) + jb;
+      int jrot = ((jb - ea->sin % 18) % 18 + 27) % 18 - 9; /* in [-9, 8] */
+      if (jrot < -2 || jrot > 2) continue;
+      for (int64_t qb = bstart[sb_need]; qb < bstart[sb_need + 1]; ++qb) {
+        int64_t b = bsec[qb];
+        const o_ends* eb = E + b;
+        const double* pb = R->trk_par + 5 * b;
+        if ((R->trk_flags[b] & 4) || R->trk_sector[b] != eb->sin) continue;
+        if (eb->rin < 1 || !(o_side(eb->sin) * pb[3] > 0.0)) continue;
+        int gap = eb->rin - ea->rout;
+        if (gap < 1 || gap > O_MEM_ROWGAP) continue;
+        if (abs(eb->zin - ea->zout) > O_MEM_DZU) continue;
+        /* a's state in the tracker's convention (dzeta/ds), turned into b's
+         * frame and moved to b's x */
+        ost t;
+        double sga = (sa > 0) ? -1.0 : 1.0;
+        t.x = R->trk_x[a];
+        memcpy(t.p, pa, 5 * sizeof(double)); memcpy(t.C, R->trk_cov + 15 * a, 15 * sizeof(double));
+        t.p[3] *= sga;
+        for (int q = 0; q < 5; ++q) if (q != 3) t.C[o_ix(3, q)] *= sga;
+        if (jrot != 0 && o_rot(&t, jrot * 20.0 * O_PI / 180.0, R->bzc) != 0) continue;
+        if (o_prop(&t, R->trk_x[b], R->bzc) != 0) continue;
+        t.p[3] *= sga;
+        for (int q = 0; q < 5; ++q) if (q != 3) t.C[o_ix(3, q)] *= sga;
+        static const int idx[4] = {0, 2, 3, 4};
+        double dv[5] = {0}, cs[15] = {0};
+        const double* cb = R->trk_cov + 15 * b;
+        for (int i = 0; i < 4; ++i) {
+          dv[i] = t.p[idx[i]] - pb[idx[i]];
+          for (int j = 0; j <= i; ++j) cs[o_ix(i, j)] = t.C[o_ix(idx[i], idx[j])] + cb[o_ix(idx[i], idx[j])];
+        }
+        cs[o_ix(4, 4)] = 1.0; /* 4x4 block padded with a unit pivot: dv[4] = 0 adds nothing */
+        double chi2;
+        if (o_chi2_5(dv, cs, &chi2) != 0 || !(chi2 <= O_CHI2_MEM)) continue;
+        double za = (double)R->trk_zref[a] * zu + t.p[1];
+        double zb = (double)R->trk_zref[b] * zu + pb[1];
+        double zm = 0.5 * (za + zb);
+        int32_t zmx = ea->zmax > eb->zmax ? ea->zmax : eb->zmax;
+        if (zm < (double)zmx * zu - O_MEM_ZTOL) continue;
+        if (np == pcap) {
+          pcap *= 2;
+          P = (o_pair*)realloc(P, sizeof(o_pair) * pcap);
+          zmid = (double*)realloc(zmid, sizeof(double) * pcap); zvar = (double*)realloc(zvar, sizeof(double) * pcap);
+        }
+        P[np].chi2 = chi2; P[np].a = (int32_t)a; P[np].b = (int32_t)b;
+        zmid[np] = zm; zvar[np] = 0.25 * (t.C[o_ix(1, 1)] + cb[o_ix(1, 1)]);
+        ++np;
+      }
+    }
+  }
+  free(bsec);
+  /* greedy over pairs sorted by (chi2, a, b); the membrane zeta of a taken
+   * pair is found again by its (a, b) after sorting */
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (np + 1));
+  o_pair* S = (o_pair*)malloc(sizeof(o_pair) * (np + 1));
+  memcpy(S, P, sizeof(o_pair) * np);
+  qsort(S, (size_t)np, sizeof(o_pair), o_paircmp);
+  for (int64_t q = 0; q < np; ++q) {
+    int64_t k = 0;
+    while (!(P[k].a == S[q].a && P[k].b == S[q].b)) ++k;
+    order[q] = k;
+  }
+  int32_t* tm = (int32_t*)calloc((size_t)n1, 4); /* 1: t0 from the membrane */
+  for (int64_t q = 0; q < np; ++q) {
+    int32_t a = S[q].a, b = S[q].b;
+    if (R->trk_mate[a] >= 0 || R->trk_mate[b] >= 0) continue;
+    R->trk_mate[a] = b; R->trk_mate[b] = a;
+    double t0 = (zmid[order[q]] - 250.0) / vd, er = sqrt(zvar[order[q]]) / vd;
+    double lo = R->trk_t0lo[a] > R->trk_t0lo[b] ? R->trk_t0lo[a] : R->trk_t0lo[b];
+    double hi = R->trk_t0hi[a] < R->trk_t0hi[b] ? R->trk_t0hi[a] : R->trk_t0hi[b];
+    R->trk_t0[a] = R->trk_t0[b] = t0; R->trk_t0err[a] = R->trk_t0err[b] = er;
+    R->trk_t0lo[a] = R->trk_t0lo[b] = lo; R->trk_t0hi[a] = R->trk_t0hi[b] = hi;
+    tm[a] = tm[b] = 1;
+    R->trk_flags[a] |= 8; R->trk_flags[b] |= 8;
+  }
+  R->nmpair = np;
+  R->mpair_ab = (int32_t*)malloc(sizeof(int32_t) * 2 * (np + 1)); R->mpair_chi2 = (double*)malloc(sizeof(double) * (np + 1));
+  for (int64_t q = 0; q < np; ++q) { R->mpair_ab[2 * q] = S[q].a; R->mpair_ab[2 * q + 1] = S[q].b; R->mpair_chi2[q] = S[q].chi2; }
+  free(P); free(S); free(order); free(zmid); free(zvar);
+  /* vertex t0 of the tracks without a partner */
+  for (int64_t i = 0; i < nt; ++i) {
+    if (tm[i]) continue;
+    const double* p = R->trk_par + 5 * i; const double* C = R->trk_cov + 15 * i;
+    int side = o_side(R->trk_sector[i]);
+    double lo = R->trk_t0lo[i], hi = R->trk_t0hi[i];
+    if (!(fabs(p[2]) < 1.0)) { /* no direction: the middle of the bounds */
+      R->trk_t0[i] = 0.5 * (lo + hi); R->trk_t0err[i] = 0.5 * (hi - lo);
+      continue;
+    }
+    double k = p[4] * R->bzc;
+    double s = o_dca_arc(R->trk_x[i], p[0], p[2], k);
+    double dzds = -(double)side * p[3]; /* dzeta/ds */
+    double zv = (double)R->trk_zref[i] * zu + p[1] + dzds * s;
+    double t0 = (zv - 250.0) / vd;
+    if (t0 < lo) t0 = lo;
+    if (t0 > hi) t0 = hi;
+    /* variance of zeta + s dzeta/ds (s held fixed) plus the beam spot */
+    double c13 = -(double)side * C[o_ix(1, 3)], c33 = C[o_ix(3, 3)];
+    double var = C[o_ix(1, 1)] + 2.0 * s * c13 + s * s * c33;
+    if (!(var >= 0.0)) var = 0.0;
+    var += O_SIGMA_ZV * O_SIGMA_ZV;
+    R->trk_t0[i] = t0; R->trk_t0err[i] = sqrt(var) / vd;
+  }
+  free(tm);
+  /* collision assignment */
+  for (int64_t i = 0; i < nt; ++i) {
+    int32_t best = -1; double bd = 0;
+    for (int64_t c = 0; c < in->n_coll; ++c) {
+      double tc = in->coll_time[c];
+      if (tc < R->trk_t0lo[i] - O_T0_SLACK || tc > R->trk_t0hi[i] + O_T0_SLACK) continue;
+      double d = fabs(tc - R->trk_t0[i]);
+      if (best < 0 || d < bd) { best = (int32_t)c; bd = d; }
+    }
+    R->trk_coll[i] = best;
+  }
+  free(E);
+}
+
 /* ---------------------------------------------------------------- driver */
 static void o_add(oracle_result* R, const char* name, const void* p, int64_t n, int32_t type) {
   R->fields[R->nf].name = name; R->fields[R->nf].ptr = p; R->fields[R->nf].n = n; R->fields[R->nf].type = type; R->nf++;
@@ -845,6 +1058,7 @@ oracle_result* oracle_run(const oracle_input* in, int32_t* status) {
   o_select(R, in->reverse_tracklet_order);
   o_merge(R, in->sector_mask);
   o_final(R);
+  o_continuous(R, in);
   o_add(R, "yu", R->yu, R->n, 0); o_add(R, "zu", R->zu, R->n, 0); o_add(R, "rid", R->rid, R->n, 0);
   o_add(R, "sorted_orig", R->s_orig, R->nsel, 0); o_add(R, "sorted_rid", R->s_rid, R->nsel, 0);
   o_add(R, "sorted_y", R->s_y, R->nsel, 0); o_add(R, "sorted_z", R->s_z, R->nsel, 0); o_add(R, "sorted_cell", R->s_cell, R->nsel, 0);
@@ -871,6 +1085,10 @@ oracle_result* oracle_run(const oracle_input* in, int32_t* status) {
   o_add(R, "trk_sector", R->trk_sector, R->ntrk, 0); o_add(R, "trk_flags", R->trk_flags, R->ntrk, 0);
   o_add(R, "trk_zref", R->trk_zref, R->ntrk, 0); o_add(R, "trk_head", R->trk_head, R->ntrk, 0);
   o_add(R, "trk_nseg", R->trk_nseg, R->ntrk, 0);
+  o_add(R, "trk_t0", R->trk_t0, R->ntrk, 2); o_add(R, "trk_t0err", R->trk_t0err, R->ntrk, 2);
+  o_add(R, "trk_t0lo", R->trk_t0lo, R->ntrk, 2); o_add(R, "trk_t0hi", R->trk_t0hi, R->ntrk, 2);
+  o_add(R, "trk_mate", R->trk_mate, R->ntrk, 0); o_add(R, "trk_coll", R->trk_coll, R->ntrk, 0);
+  o_add(R, "mpair_ab", R->mpair_ab, R->nmpair * 2, 0); o_add(R, "mpair_chi2", R->mpair_chi2, R->nmpair, 2);
   *status = 0;
   return R;
 }
@@ -888,7 +1106,8 @@ void oracle_free(oracle_result* R) {
                 R->tl_hits, R->tl_state, R->st_sector, R->st_tracklet, R->st_zref, R->st_off, R->st_hits,
                 R->st_in, R->st_out, R->st_next, R->st_prev, R->pair_ab, R->pair_chi2, R->trk_off, R->trk_cl,
                 R->trk_x, R->trk_alpha, R->trk_par, R->trk_cov, R->trk_chi2, R->trk_ndf, R->trk_sector,
-                R->trk_flags, R->trk_zref, R->trk_head, R->trk_nseg};
+                R->trk_flags, R->trk_zref, R->trk_head, R->trk_nseg, R->trk_t0, R->trk_t0err, R->trk_t0lo,
+                R->trk_t0hi, R->trk_mate, R->trk_coll, R->mpair_ab, R->mpair_chi2};
   for (size_t i = 0; i < sizeof(ps) / sizeof(ps[0]); ++i) free(ps[i]);
   free(R);
 }

@@ -26,6 +26,8 @@ typedef struct {
   double vdrift;           /* cm/us */
   uint64_t sector_mask;    /* bit s set: sector s is tracked (0 = all) */
   int32_t reverse_tracklet_order; /* 1: build tracklets in reverse order (selection order-independence test) */
+  const double* coll_time; /* interaction times of the TF, us, ascending (may be NULL) */
+  int64_t n_coll;
 } oracle_input;
 
 typedef struct oracle_result oracle_result;
@@ -46,6 +48,9 @@ int32_t oracle_rotate(double* x, double* p5, double* c15, double dalpha);
  * seeds y and zeta, (sin phi, t, q/pT) come from p5; the initial covariance is
  * c15 if c15[0] > 0, else the tracker's initial diagonal.  Returns the state
  * and covariance at the last point in p5, c15. */
+/* Signed transverse arc length from (x0, y0) with sin(phi) = snp and
+ * curvature k = dphi/ds to the closest approach to the origin. */
+double oracle_dca_arc(double x0, double y0, double snp, double k);
 int32_t oracle_fit_points(int32_t n, const double* x, const double* y, const double* z, double bz,
                           double* p5_inout, double* c15_out);
 

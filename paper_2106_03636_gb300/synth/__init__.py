@@ -115,6 +115,7 @@ class TimeFrame:
     packed: np.ndarray | None = None
     truth_track: np.ndarray | None = None
     truth: dict = field(default_factory=dict)
+    coll_time: np.ndarray | None = None
     bz: float = BZ
     vdrift: float = VDRIFT
     name: str = ""
@@ -149,6 +150,9 @@ def generate(*, seed: int, t0, ntracks, fmt: int = FMT_FLOAT, sector_only: int =
         n = n.value
         tf = TimeFrame(n=n, fmt=fmt, sector=np.empty(n, np.uint8), row=np.empty(n, np.uint8),
                        bz=bz, vdrift=vdrift, name=name)
+        # the interaction record of the TF: the collision times, ascending
+        # (the truth's collision index points into it)
+        tf.coll_time = t0.copy() if np.all(np.diff(t0) >= 0) else None
         if fmt == FMT_FLOAT:
             tf.y = np.empty(n, np.float32)
             tf.z = np.empty(n, np.float32)
@@ -274,4 +278,4 @@ def float_time_from_fixed(tf: TimeFrame) -> TimeFrame:
     yu = pad - 32 * npads.astype(np.int64)
     return TimeFrame(n=tf.n, fmt=FMT_FLOAT, sector=sector, row=row, y=(yu / 160.0).astype(np.float32),
                      time=(t64.astype(np.float64) / 320.0).astype(np.float32), bz=tf.bz, vdrift=tf.vdrift,
-                     name=tf.name + "_time")
+                     name=tf.name + "_time", coll_time=tf.coll_time)
