@@ -39,8 +39,8 @@ METRIC = "TPC clusters/s and TF/s at 50 kHz Pb-Pb on 1 GB300 (served vs plain); 
 
 # Algorithmic HBM bytes per cluster of each step: data the step must read or
 # write once per cluster at minimum (16-byte sort records, 8-byte sorted
-# coordinates, 4-byte indices, 8-byte ownership words).  Their sum is the
-# 64 B/cluster of the whole path.
+# coordinates, 4-byte indices, 8-byte ownership words).  The whole path's
+# minimum is PATH_BYTES per cluster.
 STAGE_BYTES = {
     "ingest": 12.0,        # read the 12-byte packed record
     "sort": 12.0 + 12.0,   # read the record again, write sorted y, zeta + input index
@@ -59,6 +59,9 @@ STAGE_BYTES = {
     # write their indices, >= 8 + 4 bytes per cluster
     "tl_out": 12.0,
     "tl_in": 12.0,
+    # continuous readout: per track ~150 B (ends, state, covariance, results)
+    # over ~150 clusters per track
+    "continuous": 1.0,
 }
 # DRAM bytes (read + write) per launch that ncu measured for a kernel on a
 # workload (the launch list in profiles/launches_full_tf.md), valid while the
@@ -86,7 +89,7 @@ def measured_traffic(kernel: str, workload: str):
 ROOF_KERNELS = {"tl_out": "k_tl_out", "tl_in": "k_tl_in", "neighbours": "k_neighbours",
                 "refit": "k_final_refit", "sort": "k_row_scatter+k_cell_sort", "selection": "k_ownership+k_segments",
                 "sector_fit": "k_sector_fit", "merge": "k_merge_*"}
-PATH_BYTES = 64.0
+PATH_BYTES = 65.0
 
 
 def peaks():
@@ -331,7 +334,7 @@ def run_chunks(args, rank, world, local):
             dist.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        stage = np.zeros(16)
+        stage = np.zeros(len(o2tpc.STAGES))
         launches, sizes, captured = 0, set(), set()
         e0.record(trk.stream)
         for _ in range(args.steps):
@@ -387,10 +390,10 @@ def run_chunks(args, rank, world, local):
                         "gpu_launches": l_b, "captured_graph": captured_b == [1],
                         "graph_launches_per_step": 1 if captured_b == [1] else 0},
             "plain": {"value": world * n / (ms_p / 1e3), "ms_per_step": ms_p, "gpu_launches": l_p,
-                      "stage_ms": {names[i]: round(float(stage_p[i]), 3) for i in range(16)}},
+                      "stage_ms": {names[i]: round(float(stage_p[i]), 3) for i in range(len(o2tpc.STAGES) - 1)}},
             "speedup_batched_vs_plain": ms_p / ms_b,
             "stage_ms_source": "regular path, same batch" if captured_b == [1] else "batched arm",
-            "stage_ms": {names[i]: round(float(stage_b[i]), 3) for i in range(16)},
+            "stage_ms": {names[i]: round(float(stage_b[i]), 3) for i in range(len(o2tpc.STAGES) - 1)},
             "roofline": roofline(stage_b, names, n, peak, peak_kind),
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "peak": peak,
                               "frac": n / (ms_b / 1e3) * PATH_BYTES / 1e9 / peak},
@@ -588,7 +591,7 @@ def main():
         if args.trace:
             st = r["stats"]["ms_stage"]
             print(f"{tag}: batch {r['stats']['batch_size']} device {r['stats']['ms_device']:.2f} ms, "
-                  + ", ".join(f"{o2tpc.STAGES[i]} {st[i]:.2f}" for i in range(16)), file=sys.stderr, flush=True)
+                  + ", ".join(f"{o2tpc.STAGES[i]} {st[i]:.2f}" for i in range(len(o2tpc.STAGES) - 1)), file=sys.stderr, flush=True)
 
     def step(location, arrays):
         r = trk.wait(trk.submit(tf, location=location, arrays=arrays))
@@ -605,7 +608,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        stage = np.zeros(16)
+        stage = np.zeros(len(o2tpc.STAGES))
         launches = 0
         lat = []
         e0.record(st)
@@ -684,7 +687,7 @@ def main():
                "p99_ms": float(np.percentile(lat_hs, 99)), "batch_sizes": sizes_hs,
                "plain": {"value": world * n / (ms_h / args.steps / 1e3), "ms_per_step": ms_h / args.steps,
                          "p50_ms": float(np.percentile(lat_h, 50)), "p99_ms": float(np.percentile(lat_h, 99)),
-                         "stage_ms": {o2tpc.STAGES[i]: round(float(stage_h[i]), 3) for i in range(16)}}}
+                         "stage_ms": {o2tpc.STAGES[i]: round(float(stage_h[i]), 3) for i in range(len(o2tpc.STAGES) - 1)}}}
 
     peak, peak_kind = peaks()
     names = o2tpc.STAGES
@@ -713,7 +716,7 @@ def main():
             "plain": {"value": plain_value, "tf_per_s": world / (ms_step / 1e3), "ms_per_step": ms_step,
                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                       "steps": args.steps},
-            "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(16)},
+            "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(len(o2tpc.STAGES) - 1)},
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "frac": path_frac, "peak": peak},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_s, "clocks": clocks,
             "autotune": trk.tuning()}

@@ -173,6 +173,13 @@ typedef struct {
    *   u8 row, u8 sector, u16 spare */
   const void* packed;
   uint64_t user_tag;       /* echoed in the result                                     */
+  /* Interaction record (Sec. 2: tracks are assigned to collisions after
+   * tracking): n_coll collision times of this TF in us from its start,
+   * ascending and finite, in HOST memory whatever `location` says (copied at
+   * the batch start; borrowed like the clusters).  May be NULL with n_coll 0:
+   * every track's collision is then -1.  Unsorted or non-finite -> EINVAL. */
+  const double* coll_time;
+  uint64_t n_coll;
 } o2tpc_tf;
 
 typedef struct {
@@ -196,8 +203,10 @@ typedef struct {
    * the batch start to the start of step 0 (host-resident inputs copied in
    * the batch's own stream, descriptor tables); 13 time the batch waited for
    * inputs that were uploaded ahead on the context's copy stream; 14 and 15
-   * the outward and the inward following passes inside step 4 */
-  float ms_stage[16];
+   * the outward and the inward following passes inside step 4; 16 the
+   * continuous-readout step (t0, membrane links, collision assignment) that
+   * follows step 8; 17 reserved (0) */
+  float ms_stage[18];
   uint32_t captured;         /* 1: the batch ran as one CUDA graph launch (the
                                 captured path: ms_stage holds only 10-13)     */
   uint32_t reserved;
@@ -218,8 +227,24 @@ typedef struct {
   const uint8_t* sector;       /* [n_tracks] sector of the reported frame             */
   const uint8_t* flags;        /* [n_tracks] bit0 FP64 fallback, bit1 merged from
                                   several sectors, bit2 refit stopped at a sector
-                                  boundary                                           */
+                                  boundary, bit3 linked across the central
+                                  membrane (t0 from the crossing)                    */
   const uint32_t* zeta_ref;    /* [n_tracks] drift coordinate origin of par[1]        */
+  /* Continuous readout (Sec. 2).  Every cluster has 0 <= |z| <= 250 cm, so
+   * the drift coordinates of the track's two end clusters (the extremes of
+   * a helix) bound the collision time: t0_lo <= t0 <= t0_hi.
+   * A track linked across the central membrane (mate >= 0, flags bit3) gets
+   * t0 from where its two halves meet; any other track from its closest
+   * approach to the beam axis with z_vertex = 0 assumed (error including a
+   * 5 cm beam spot), clamped into the bounds.  collision: index into the
+   * TF's coll_time of the compatible time (within the bounds +- 0.3 us)
+   * nearest to t0, -1 if none.                                              */
+  const float* t0;             /* [n_tracks] us from the TF start                    */
+  const float* t0_err;         /* [n_tracks] us                                      */
+  const float* t0_lo;          /* [n_tracks] us                                      */
+  const float* t0_hi;          /* [n_tracks] us                                      */
+  const int32_t* mate;         /* [n_tracks] the other half across the membrane, -1 */
+  const int32_t* collision;    /* [n_tracks] interaction index, -1                   */
   o2tpc_stats stats;
   uint64_t user_tag;
   int32_t status;              /* O2TPC_OK or the error of this TF                    */

@@ -833,7 +833,8 @@ static void o_final(oracle_result* R) {
  * collisions after tracking.  The paper gives no method; the readings here
  * (all constants below are ours):
  *  - t0 bounds from the clusters: every cluster lies at 0 <= |z| <= 250 cm,
- *    so zeta_max - 250 <= v_d t0 <= zeta_min;
+ *    so zeta_max - 250 <= v_d t0 <= zeta_min; zeta is linear along the
+ *    helix, so its extremes are those of the track's two end clusters;
  *  - vertex t0: the track extrapolated to its closest approach to the beam
  *    axis in the transverse plane, assuming z_vertex = 0 there, clamped into
  *    the bounds; its error adds the beam-spot length O_SIGMA_ZV;
@@ -884,12 +885,9 @@ static void o_continuous(oracle_result* R, const oracle_input* in) {
     e->zin = R->zu[c0]; e->zout = R->zu[c1];
     e->rin = R->rid[c0] % O_NROW; e->sin = R->rid[c0] / O_NROW;
     e->rout = R->rid[c1] % O_NROW; e->sout = R->rid[c1] / O_NROW;
-    e->zmin = e->zmax = e->zin;
-    for (int64_t q = R->trk_off[i]; q < R->trk_off[i + 1]; ++q) {
-      int32_t z = R->zu[R->trk_cl[q]];
-      if (z < e->zmin) e->zmin = z;
-      if (z > e->zmax) e->zmax = z;
-    }
+    /* zeta is linear along the helix: its extremes sit at the end clusters */
+    e->zmin = e->zin < e->zout ? e->zin : e->zout;
+    e->zmax = e->zin < e->zout ? e->zout : e->zin;
     R->trk_t0lo[i] = ((double)e->zmax * zu - 250.0) / vd;
     R->trk_t0hi[i] = (double)e->zmin * zu / vd;
     R->trk_mate[i] = -1;

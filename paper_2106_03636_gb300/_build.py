@@ -29,6 +29,7 @@ CUDA_SOURCES = [
     "k_ca.cu",
     "k_track.cu",
     "k_merge.cu",
+    "k_cont.cu",
     "o2tpc_static.cu",
     "o2tpc_graph.cu",
 ]
@@ -41,6 +42,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FILE_FLAGS = {
     "k_track.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
     "k_merge.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+    "k_cont.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
 }
 
 

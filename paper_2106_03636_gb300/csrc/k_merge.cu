@@ -437,11 +437,22 @@ __global__ void __launch_bounds__(128) k_final_refit(const int* __restrict__ nHe
   const int head = heads[t];
   int nseg;
   const int tail = chain_tail(head, mb.next, &nseg);
-  const int inBase = tfs[sb.tf[head]].inBase;
+  const int tf = sb.tf[head];
+  const int inBase = tfs[tf].inBase;
   int o = ob.off[t];
   for (int c = head, j = 0; j < nseg; c = mb.next[c], ++j)
     for (int i = sb.off[c]; i < sb.off[c + 1]; ++i) ob.cl[o++] = sb.orig[i] - inBase;
   const int zref = sb.yz[sb.off[head]].y;
+  {
+    // the drift coordinate is linear along the helix: its extremes over the
+    // track are those of the two end clusters
+    const int hl = sb.off[tail + 1] - 1;
+    const int zl = sb.yz[hl].y;
+    ob.ends[t] = make_int4(min(zref, zl), max(zref, zl), zref, zl);
+    ob.endsR[t] = make_int2(sb.rows[sb.off[head]] | (sb.rows[hl] << 8) | (sb.sector[head] << 16) |
+                                (sb.sector[tail] << 24),
+                            tf);
+  }
   KState<float> sf;
   float c2f;
   int used, frame, yref;
@@ -488,6 +499,13 @@ void launch_merge_keys(int nSt, const SectorTrackBufs sb, const GeomConst* G, Me
     k_merge_list_fill<<<(nSt + 255) / 256, 256, 0, st>>>(sb, G, mb, mb.listCnt);
     ++g_launch_count;
   }
+  if (nKeys > 0) {
+    k_merge_list_sort<<<nKeys, 512, 0, st>>>(mb, reinterpret_cast<int2*>(mb.sortScratch));
+    ++g_launch_count;
+  }
+}
+
+void launch_list_sort(int nKeys, MergeBufs mb, cudaStream_t st) {
   if (nKeys > 0) {
     k_merge_list_sort<<<nKeys, 512, 0, st>>>(mb, reinterpret_cast<int2*>(mb.sortScratch));
     ++g_launch_count;

@@ -120,7 +120,7 @@ struct Pending {
   std::vector<std::shared_ptr<Job>> jobs;
   std::shared_ptr<BatchMem> out;  // device result arrays, freed once copied
   cudaEvent_t dl0 = nullptr, dl1 = nullptr;
-  float stageMs[16] = {};
+  float stageMs[18] = {};
   double hostPrepMs = 0;
   bool captured = false;
   ~Pending() {
@@ -308,6 +308,7 @@ void fill_geom(GeomConst& g, double bz, double vd) {
   g.bzc = (float)g.bzc_d;
   g.zunit_d = 0.003125 * vd;
   g.zunit = (float)g.zunit_d;
+  g.vd_d = vd;
   g.kz = (float)(1.0 / (0.003125 * vd));
 }
 
@@ -400,9 +401,12 @@ struct Pipe {
 bool graph_fits(const Ctx* c, const std::vector<std::shared_ptr<Job>>& jobs) {
   const GraphCaps& k = c->graph->caps;
   if ((int)jobs.size() > k.BCap) return false;
-  long long n = 0;
-  for (auto& j : jobs) n += (long long)j->tf.n;
-  return n <= k.nCap;
+  long long n = 0, nc = 0;
+  for (auto& j : jobs) {
+    n += (long long)j->tf.n;
+    nc += (long long)j->tf.n_coll;
+  }
+  return n <= k.nCap && nc <= k.collCap;
 }
 
 size_t r256(size_t x) { return (x + 255) / 256 * 256; }
@@ -422,6 +426,7 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
   std::vector<int2> tiles;
   long long N = 0;
   size_t inOff = 0;
+  int nColl = 0;
   for (int i = 0; i < B; ++i) {
     const o2tpc_tf& t = jobs[i]->tf;
     TFDesc d{};
@@ -445,6 +450,9 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
     d.tileBase = (int)tiles.size();
     d.nTiles = (int)((t.n + k.tileSize - 1) / k.tileSize);
     for (int q = 0; q < d.nTiles; ++q) tiles.push_back(make_int2(i, q * k.tileSize));
+    d.nColl = (int)t.n_coll;
+    d.collBase = nColl;
+    nColl += (int)t.n_coll;
     tfd[i] = d;
     N += (long long)t.n;
   }
@@ -462,13 +470,18 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
     hc.n = (int)N;
     hc.nKeys = k.nKeys;
     const size_t b1 = sizeof(TFDesc) * k.BCap, b2 = sizeof(int2) * k.nTilesCap, b3 = sizeof(Counts);
-    char* h = static_cast<char*>(c->stage(b1 + b2 + b3));
+    const size_t b4 = sizeof(double) * nColl;
+    char* h = static_cast<char*>(c->stage(b1 + b2 + b3 + b4));
     memcpy(h, tfd.data(), b1);
     memcpy(h + b1, tiles.data(), b2);
     memcpy(h + b1 + b2, &hc, b3);
+    for (int i = 0; i < B; ++i)
+      if (tfd[i].nColl) memcpy(h + b1 + b2 + b3 + sizeof(double) * tfd[i].collBase, jobs[i]->tf.coll_time,
+                               sizeof(double) * tfd[i].nColl);
     CK(cudaMemcpyAsync(A.tfs, h, b1, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(A.tiles, h + b1, b2, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(A.cnt, h + b1 + b2, b3, cudaMemcpyHostToDevice, st));
+    if (nColl) CK(cudaMemcpyAsync(A.coll, h + b1 + b2 + b3, b4, cudaMemcpyHostToDevice, st));
   }
   if (c->graphDlRecorded) CK(cudaStreamWaitEvent(st, c->graphDl, 0));
   if (c->graphExec && (c->graphNf != c->tune.nf_hits_per_block * 2 + c->tune.nf_staged ||
@@ -507,7 +520,7 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
   CK(cudaStreamSynchronize(st));
   Counts hc;
   memcpy(&hc, hv, sizeof(Counts));
-  if (hc.overflow || hv[8] > k.pairCap || (hv[9] & kErrOverflow)) return false;
+  if (hc.overflow || hv[8] > k.pairCap || (hv[9] & (kErrOverflow | kErrMembrane))) return false;
   tfd.resize(B);
   pp.B = B;
   pp.n = (int)N;
@@ -533,6 +546,7 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   std::vector<TFDesc> tfd(B);
   std::vector<int2> tiles;
   long long N = 0;
+  int nColl = 0;
   for (int i = 0; i < B; ++i) {
     const o2tpc_tf& t = jobs[i]->tf;
     TFDesc d{};
@@ -556,6 +570,9 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
     d.tileBase = (int)tiles.size();
     d.nTiles = (int)((t.n + tileSize - 1) / tileSize);
     for (int k = 0; k < d.nTiles; ++k) tiles.push_back(make_int2(i, k * tileSize));
+    d.nColl = (int)t.n_coll;
+    d.collBase = nColl;
+    nColl += (int)t.n_coll;
     tfd[i] = d;
     N += (long long)t.n;
   }
@@ -573,19 +590,24 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   M.N = n;
   TFDesc* dTF = dalloc<TFDesc>(M, B);
   int2* dTiles = dalloc<int2>(M, nTiles);
+  double* dColl = dalloc<double>(M, nColl);
   Counts* C = c->dCounts;  // device-side sizes of this batch (the context's own slot)
   {
     Counts hc{};
     hc.n = n;
     hc.nKeys = B * kNSec * 2;
-    size_t b1 = sizeof(TFDesc) * B, b2 = sizeof(int2) * nTiles, b3 = sizeof(Counts);
-    char* h = static_cast<char*>(c->stage(b1 + b2 + b3));
+    size_t b1 = sizeof(TFDesc) * B, b2 = sizeof(int2) * nTiles, b3 = sizeof(Counts), b4 = sizeof(double) * nColl;
+    char* h = static_cast<char*>(c->stage(b1 + b2 + b3 + b4));
     memcpy(h, tfd.data(), b1);
     memcpy(h + b1, tiles.data(), b2);
     memcpy(h + b1 + b2, &hc, b3);
+    for (int i = 0; i < B; ++i)
+      if (tfd[i].nColl) memcpy(h + b1 + b2 + b3 + sizeof(double) * tfd[i].collBase, jobs[i]->tf.coll_time,
+                               sizeof(double) * tfd[i].nColl);
     CK(cudaMemcpyAsync(dTF, h, b1, cudaMemcpyHostToDevice, st));
     if (nTiles) CK(cudaMemcpyAsync(dTiles, h + b1, b2, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(C, h + b1 + b2, b3, cudaMemcpyHostToDevice, st));
+    if (nColl) CK(cudaMemcpyAsync(dColl, h + b1 + b2 + b3, b4, cudaMemcpyHostToDevice, st));
   }
   unsigned* dErr = dalloc<unsigned>(M, 4);
   CK(cudaMemsetAsync(dErr, 0, 16, st));
@@ -786,6 +808,14 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   ob.zref = dalloc<int>(OM, nHeads);
   ob.nFallback = dalloc<int>(OM, 1);
   ob.fallback = dalloc<int>(M, nHeads);
+  ob.ends = dalloc<int4>(M, nHeads);
+  ob.endsR = dalloc<int2>(M, nHeads);
+  ob.t0 = dalloc<float>(OM, nHeads);
+  ob.t0err = dalloc<float>(OM, nHeads);
+  ob.t0lo = dalloc<float>(OM, nHeads);
+  ob.t0hi = dalloc<float>(OM, nHeads);
+  ob.mate = dalloc<int>(OM, nHeads);
+  ob.coll = dalloc<int>(OM, nHeads);
   CK(cudaMemsetAsync(ob.nFallback, 0, sizeof(int), st));
   launch_chain_counts(nHeads, &C->nHeads, heads, sb, mb, trkNcl, st);
   CKL();
@@ -797,6 +827,17 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   CKL();
   int* trkTfBegin = dalloc<int>(M, B + 1);
   launch_lower_bounds(heads, &C->nHeads, stTfBegin, B + 1, trkTfBegin, st);
+  CKL();
+  // ---- continuous readout: t0, membrane links, collision assignment
+  CK(cudaEventRecord(c->evs[11], st));
+  {
+    // the merger's buffers, with links and a pair count of the stage's own
+    MergeBufs mm = mb;
+    mm.next = dalloc<int>(M, nHeads);
+    mm.prev = dalloc<int>(M, nHeads);
+    mm.pairCount = dalloc<int>(M, 1);
+    launch_continuous(nHeads, &C->nHeads, nKeys, ob, mm, G, dTF, dColl, trkTfBegin, dErr, scratch, st);
+  }
   CKL();
   CK(cudaEventRecord(c->ev1, st));
   CK(cudaEventRecord(c->evs[9], st));
@@ -946,6 +987,9 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   P->captured = captured;
   if (!captured) {  // the captured path records no stage events
     for (int k = 0; k < 10; ++k) cudaEventElapsedTime(&P->stageMs[k], c->evs[k], c->evs[k + 1]);
+    // evs[11] splits step 8: the final refit, then the continuous-readout step
+    cudaEventElapsedTime(&P->stageMs[8], c->evs[8], c->evs[11]);
+    cudaEventElapsedTime(&P->stageMs[16], c->evs[11], c->evs[9]);
     cudaEventElapsedTime(&P->stageMs[12], c->evWait, c->evs[0]);
     cudaEventElapsedTime(&P->stageMs[14], c->evTl[0], c->evTl[1]);
     cudaEventElapsedTime(&P->stageMs[15], c->evTl[2], c->evTl[3]);
@@ -955,6 +999,9 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   cudaEventElapsedTime(&devMs, c->ev0, c->ev1);
   const long long nLaunch = pp.launches;
   const bool inputBad = (*hErr & kErrInput) != 0;
+  // more membrane candidate pairs than the buffer holds (2 per sector track):
+  // the links would be incomplete, so the batch's TFs report ETOOBIG
+  const bool memOverflow = (*hErr & kErrMembrane) != 0;
   cudaStream_t dl = c->dlStream;
   CK(cudaEventCreate(&P->dl0));
   CK(cudaEventCreate(&P->dl1));
@@ -968,7 +1015,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     const int t0 = hTrkTf[i], t1 = hTrkTf[i + 1];
     const size_t nt = (size_t)(t1 - t0);
     const size_t ncl = (size_t)(hOff[t1] - hOff[t0]);
-    const size_t bytes = r16(8 * (nt + 1)) + r16(4 * ncl) + 5 * r16(4 * nt) + r16(20 * nt) + r16(60 * nt) +
+    const size_t bytes = r16(8 * (nt + 1)) + r16(4 * ncl) + 11 * r16(4 * nt) + r16(20 * nt) + r16(60 * nt) +
                          2 * r16(nt) + 64;
     J.host = c->pinned_get(bytes, &J.hostBytes);
     char* q = static_cast<char*>(J.host);
@@ -1010,6 +1057,12 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     R.zeta_ref = reinterpret_cast<const uint32_t*>(take(ob.zref + t0, 4 * nt));
     R.sector = reinterpret_cast<const uint8_t*>(take(ob.sector + t0, nt));
     R.flags = reinterpret_cast<const uint8_t*>(take(ob.flags + t0, nt));
+    R.t0 = reinterpret_cast<const float*>(take(ob.t0 + t0, 4 * nt));
+    R.t0_err = reinterpret_cast<const float*>(take(ob.t0err + t0, 4 * nt));
+    R.t0_lo = reinterpret_cast<const float*>(take(ob.t0lo + t0, 4 * nt));
+    R.t0_hi = reinterpret_cast<const float*>(take(ob.t0hi + t0, 4 * nt));
+    R.mate = reinterpret_cast<const int32_t*>(take(ob.mate + t0, 4 * nt));
+    R.collision = reinterpret_cast<const int32_t*>(take(ob.coll + t0, 4 * nt));
     for (size_t k = 0; k <= nt; ++k) off64[k] = (uint64_t)(hOff[t0 + k] - hOff[t0]);
     R.user_tag = J.tf.user_tag;
     R.stats.n_clusters = J.tf.n;
@@ -1020,7 +1073,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     R.stats.ms_queue = (float)(J.t_start - J.t_submit);
     R.stats.ms_device = devMs;
     R.stats.n_launches = (uint64_t)nLaunch;
-    J.status = inputBad ? O2TPC_EINVAL : O2TPC_OK;
+    J.status = inputBad ? O2TPC_EINVAL : (memOverflow ? O2TPC_ETOOBIG : O2TPC_OK);
     R.status = J.status;
     J.tfIndex = i;
   }
@@ -1233,7 +1286,7 @@ void finisher_main(Ctx* c) {
         uint64_t fb = 0;
         for (uint64_t k = 0; k < R.n_tracks; ++k) fb += (R.flags[k] & 1) ? 1 : 0;
         R.stats.n_fp64_fallback = fb;
-        for (int k = 0; k < 16; ++k) R.stats.ms_stage[k] = P->stageMs[k];
+        for (int k = 0; k < 18; ++k) R.stats.ms_stage[k] = P->stageMs[k];
         R.stats.ms_stage[10] = dlMs;
         R.stats.ms_stage[11] = (float)P->hostPrepMs;
         R.stats.captured = P->captured ? 1u : 0u;
@@ -1385,6 +1438,13 @@ static int check_tf(const Ctx* c, const o2tpc_tf* tf) {
     if (tf->format == O2TPC_FMT_FIXED && !tf->packed) return O2TPC_EINVAL;
     if (tf->format == O2TPC_FMT_FLOAT && (!tf->sector || !tf->row || !tf->y || (!tf->z && !tf->time)))
       return O2TPC_EINVAL;
+  }
+  if (tf->n_coll > 0) {
+    if (!tf->coll_time || tf->n_coll >= (1u << 24)) return O2TPC_EINVAL;
+    for (uint64_t i = 0; i < tf->n_coll; ++i) {
+      const double v = tf->coll_time[i];
+      if (!std::isfinite(v) || (i > 0 && v < tf->coll_time[i - 1])) return O2TPC_EINVAL;
+    }
   }
   if (tf->n >= kMaxBatchHits) return O2TPC_ETOOBIG;
   if (footprint_of(tf->n) > c->cfg.mem_budget) return O2TPC_ETOOBIG;

@@ -38,6 +38,7 @@ GraphCaps graph_caps(long long maxClusters, int maxTFs, bool tight) {
   k.pairCap = 2 * k.stCap;
   if (tight) k.tlCap = k.stCap = k.headCap = k.pairCap = 16;
   k.nKeys = k.BCap * kNSec * 2;
+  k.collCap = 4096 * k.BCap;
   return k;
 }
 
@@ -137,7 +138,19 @@ size_t graph_carve(GraphArena& A, char* base) {
   take(A.ob.zref, k.headCap);
   take(A.ob.nFallback, 1);
   take(A.ob.fallback, k.headCap);
+  take(A.ob.ends, k.headCap);
+  take(A.ob.endsR, k.headCap);
+  take(A.ob.t0, k.headCap);
+  take(A.ob.t0err, k.headCap);
+  take(A.ob.t0lo, k.headCap);
+  take(A.ob.t0hi, k.headCap);
+  take(A.ob.mate, k.headCap);
+  take(A.ob.coll, k.headCap);
   take(A.trkTfBegin, k.BCap + 1);
+  take(A.coll, k.collCap);
+  take(A.memNext, k.headCap);
+  take(A.memPrev, k.headCap);
+  take(A.memPairs, 1);
   A.mb.nSt = k.stCap;
   A.mb.pairCap = k.pairCap;
   A.mb.cnt = A.cnt;
@@ -197,6 +210,12 @@ void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, bool nf
   scan_exclusive(A.trkNcl, A.ob.off, k.headCap, &C->nHeads, A.scratch, st);
   launch_final_refit(k.headCap, &C->nHeads, A.heads, A.sb, A.mb, A.syz, A.sorig, A.tfs, G, forceFp64, A.ob, st);
   launch_lower_bounds(A.heads, &C->nHeads, A.stTfBegin, k.BCap + 1, A.trkTfBegin, st);
+  // continuous readout
+  MergeBufs mm = A.mb;
+  mm.next = A.memNext;
+  mm.prev = A.memPrev;
+  mm.pairCount = A.memPairs;
+  launch_continuous(k.headCap, &C->nHeads, k.nKeys, A.ob, mm, G, A.tfs, A.coll, A.trkTfBegin, A.err, A.scratch, st);
 }
 
 }  // namespace o2tpc

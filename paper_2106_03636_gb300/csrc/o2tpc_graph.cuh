@@ -12,6 +12,7 @@ struct GraphCaps {
   int nCap, BCap, tileSize, nTilesCap, nRows;
   long long cellsCap;
   int tlCap, stCap, stHitsCap, headCap, pairCap, nKeys;
+  int collCap;  // interaction times per batch
 };
 
 // Every buffer of a batch, carved from one allocation.
@@ -45,6 +46,8 @@ struct GraphArena {
   int *headFlag, *heads, *trkNcl;
   OutBufs ob;
   int* trkTfBegin;
+  double* coll;                       // interaction times of the batch
+  int *memNext, *memPrev, *memPairs;  // membrane links and their pair count
 };
 
 GraphCaps graph_caps(long long maxClusters, int maxTFs, bool tight = false);

@@ -52,6 +52,7 @@ struct GeomConst {
   float zunit;      // cm per drift-time unit (0.003125 us * v_drift)
   float kz;         // 1 / zunit as float (float-input quantisation)
   double bzc_d, zunit_d;
+  double vd_d;      // drift velocity, cm/us
 };
 
 // ------------------------------------------------------------ tables
@@ -76,11 +77,12 @@ struct TFDesc {
   int inBase;        // first batch-global input index of this TF
   int tileBase;      // first tile of this TF
   int nTiles;
-  int pad;
+  int nColl;         // interaction times of this TF (ascending, us)
+  int collBase;      // first of them in the batch's array
 };
 
 // Device error word bits
-enum : unsigned { kErrInput = 1u, kErrOverflow = 2u, kErrTimeout = 4u };
+enum : unsigned { kErrInput = 1u, kErrOverflow = 2u, kErrTimeout = 4u, kErrMembrane = 8u };
 
 // ------------------------------------------------------------ helpers
 // floor(a / b) for b > 0 in 32-bit arithmetic.

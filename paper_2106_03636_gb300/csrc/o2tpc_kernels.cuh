@@ -160,9 +160,33 @@ struct OutBufs {
   int* zref;
   int* nFallback;   // [1]
   int* fallback;    // [nTrk] tracks queued for the FP64 refit
+  // ends of each track, written by the final refit for the continuous-readout
+  // stage: {zeta min, zeta max of the two end clusters, zeta of the first
+  // cluster, of the last} and
+  // {first row | last row << 8 | first sector << 16 | last sector << 24, TF}
+  int4* ends;
+  int2* endsR;
+  // continuous-readout results
+  float* t0;        // us
+  float* t0err;
+  float* t0lo;
+  float* t0hi;
+  int* mate;        // track linked across the central membrane, or -1
+  int* coll;        // interaction time index inside the TF, or -1
 };
 void launch_final_refit(int nHeads, const int* nHeadsDev, const int* heads, const SectorTrackBufs sb, MergeBufs mb,
                         const int2* syz, const int* sorig, const TFDesc* tfs, const GeomConst* G, int forceFp64,
                         OutBufs ob, cudaStream_t st);
+// Sorts every list of mb (listStart, listKey, listItems) by key, then item.
+void launch_list_sort(int nKeys, MergeBufs mb, cudaStream_t st);
+// Continuous-readout stage over the batch's nTrk (capacity) tracks.  mb: the
+// merger's buffers, free by then, except next / prev / pairCount, which must
+// be the stage's own (nTrk links, one count); pairCap bounds the membrane
+// pairs (more set kErrMembrane in err).  coll: the batch's interaction times
+// (TFDesc ranges); trkTfBegin: first track of each TF (partners are written
+// as indices inside their TF).
+void launch_continuous(int nTrk, const int* nTrkDev, int nKeys, OutBufs ob, MergeBufs mb, const GeomConst* G,
+                       const TFDesc* tfs, const double* coll, const int* trkTfBegin, unsigned* err, int* scratch,
+                       cudaStream_t st);
 
 }  // namespace o2tpc

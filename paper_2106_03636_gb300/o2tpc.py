@@ -88,6 +88,8 @@ class o2tpc_tf(ctypes.Structure):
         ("time", ctypes.c_void_p),
         ("packed", ctypes.c_void_p),
         ("user_tag", ctypes.c_uint64),
+        ("coll_time", ctypes.c_void_p),
+        ("n_coll", ctypes.c_uint64),
     ]
 
 
@@ -103,13 +105,14 @@ class o2tpc_stats(ctypes.Structure):
         ("ms_batch", ctypes.c_float),
         ("ms_device", ctypes.c_float),
         ("n_launches", ctypes.c_uint64),
-        ("ms_stage", ctypes.c_float * 16),
+        ("ms_stage", ctypes.c_float * 18),
         ("captured", ctypes.c_uint32),
         ("reserved", ctypes.c_uint32),
     ]
 
 STAGES = ("ingest", "sort", "neighbours", "clean_starts", "tracklets", "selection", "sector_fit", "merge",
-          "refit", "sizes", "download", "host_prep", "upload", "upload_wait", "tl_out", "tl_in")
+          "refit", "sizes", "download", "host_prep", "upload", "upload_wait", "tl_out", "tl_in", "continuous",
+          "reserved")
 
 
 class o2tpc_result(ctypes.Structure):
@@ -126,6 +129,12 @@ class o2tpc_result(ctypes.Structure):
         ("sector", ctypes.POINTER(ctypes.c_uint8)),
         ("flags", ctypes.POINTER(ctypes.c_uint8)),
         ("zeta_ref", ctypes.POINTER(ctypes.c_uint32)),
+        ("t0", ctypes.POINTER(ctypes.c_float)),
+        ("t0_err", ctypes.POINTER(ctypes.c_float)),
+        ("t0_lo", ctypes.POINTER(ctypes.c_float)),
+        ("t0_hi", ctypes.POINTER(ctypes.c_float)),
+        ("mate", ctypes.POINTER(ctypes.c_int32)),
+        ("collision", ctypes.POINTER(ctypes.c_int32)),
         ("stats", o2tpc_stats),
         ("user_tag", ctypes.c_uint64),
         ("status", ctypes.c_int32),
@@ -265,15 +274,21 @@ def result_to_dict(r: o2tpc_result) -> dict:
         par=_np(r.par, 5 * n, np.float32, (n, 5)), cov=_np(r.cov, 15 * n, np.float32, (n, 15)),
         chi2=_np(r.chi2, n, np.float32), ndf=_np(r.ndf, n, np.int32), sector=_np(r.sector, n, np.uint8),
         flags=_np(r.flags, n, np.uint8), zeta_ref=_np(r.zeta_ref, n, np.uint32),
+        t0=_np(r.t0, n, np.float32), t0_err=_np(r.t0_err, n, np.float32), t0_lo=_np(r.t0_lo, n, np.float32),
+        t0_hi=_np(r.t0_hi, n, np.float32), mate=_np(r.mate, n, np.int32), collision=_np(r.collision, n, np.int32),
         status=int(r.status), user_tag=int(r.user_tag),
         stats={k: (list(getattr(r.stats, k)) if k == "ms_stage" else getattr(r.stats, k))
                for k, _ in o2tpc_stats._fields_},
     )
 
 
-def make_tf(tf, location: int = O2TPC_LOC_HOST, arrays: dict | None = None, user_tag: int = 0) -> o2tpc_tf:
+def make_tf(tf, location: int = O2TPC_LOC_HOST, arrays: dict | None = None, user_tag: int = 0,
+            coll_time=None) -> o2tpc_tf:
     """Builds an ``o2tpc_tf`` from a ``synth.TimeFrame`` (host numpy arrays)
-    or from ``arrays`` (numpy or torch tensors, host or device)."""
+    or from ``arrays`` (numpy or torch tensors, host or device).  The
+    interaction times come from ``coll_time``, else ``arrays["coll_time"]``,
+    else the TF's ``coll_time`` (host, ascending us; an empty array: none);
+    the returned struct keeps them alive in its ``_coll`` attribute."""
     src = arrays if arrays is not None else {k: getattr(tf, k, None) for k in ("sector", "row", "y", "z", "time",
                                                                             "packed")}
     t = o2tpc_tf()
@@ -289,6 +304,12 @@ def make_tf(tf, location: int = O2TPC_LOC_HOST, arrays: dict | None = None, user
         else:
             t.time = _ptr(src["time"])
     t.user_tag = user_tag
+    ct = coll_time if coll_time is not None else (arrays or {}).get("coll_time", getattr(tf, "coll_time", None))
+    if ct is not None and len(ct):
+        ct = np.ascontiguousarray(np.asarray(ct, dtype=np.float64))
+        t._coll = ct
+        t.coll_time = ct.ctypes.data
+        t.n_coll = len(ct)
     return t
 
 
@@ -347,12 +368,13 @@ class Tracker:
             raise O2TPCError(rc, "o2tpc_create")
         self._pending = {}
 
-    def submit(self, tf, location: int = O2TPC_LOC_HOST, arrays: dict | None = None, user_tag: int = 0) -> int:
-        t = make_tf(tf, location, arrays, user_tag)
+    def submit(self, tf, location: int = O2TPC_LOC_HOST, arrays: dict | None = None, user_tag: int = 0,
+               coll_time=None) -> int:
+        t = make_tf(tf, location, arrays, user_tag, coll_time)
         rc, ticket = o2tpc_submit_tf(self.ctx, t)
         if rc != O2TPC_OK:
             raise O2TPCError(rc, "o2tpc_submit_tf")
-        self._pending[ticket] = (tf, arrays)  # inputs are borrowed until polled
+        self._pending[ticket] = (tf, arrays, t)  # inputs are borrowed until polled
         return ticket
 
     def submit_many(self, tfs, location: int = O2TPC_LOC_HOST, arrays: list | None = None) -> list[int]:
@@ -363,8 +385,8 @@ class Tracker:
         rc, tickets = o2tpc_submit_many(self.ctx, ts)
         if rc != O2TPC_OK:
             raise O2TPCError(rc, "o2tpc_submit_many")
-        for tk, tf, a in zip(tickets, tfs, arrays):
-            self._pending[tk] = (tf, a)
+        for tk, tf, a, t in zip(tickets, tfs, arrays, ts):
+            self._pending[tk] = (tf, a, t)
         return tickets
 
     def poll(self, ticket: int, timeout_ms: int = -1, keep: bool = False):

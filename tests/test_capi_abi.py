@@ -6,6 +6,8 @@ import re
 
 from paper_2106_03636_gb300 import _build, o2tpc
 
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "o2tpc.h")
 
 
@@ -35,9 +37,36 @@ def test_strerror_without_gpu():
 
 def test_binding_structures_match_header_sizes():
     # 64-bit layout of the C structs as the header defines them
-    assert ctypes.sizeof(o2tpc.o2tpc_tf) == 8 + 4 + 4 + 6 * 8 + 8
-    assert ctypes.sizeof(o2tpc.o2tpc_stats) == 5 * 8 + 4 * 4 + 8 + 16 * 4 + 2 * 4
+    assert ctypes.sizeof(o2tpc.o2tpc_tf) == 8 + 4 + 4 + 6 * 8 + 8 + 8 + 8
+    assert ctypes.sizeof(o2tpc.o2tpc_stats) == 5 * 8 + 4 * 4 + 8 + 18 * 4 + 2 * 4
     # device, budget, inflight, batch, bz, vdrift, flags(+pad), 2 callbacks, user, stream, batch_full,
     # two launch shapes
     assert ctypes.sizeof(o2tpc.o2tpc_config) == 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 * 4 + 8 + 4 + 4 + 8 + 8 + 8
     assert ctypes.sizeof(o2tpc.o2tpc_tuning) == 5 * 4 + 9 * 4
+
+
+def test_binding_layout_matches_the_compiled_header(tmp_path):
+    """sizeof / offsetof of every public struct, from the header compiled by
+    gcc, against the ctypes mirror."""
+    import subprocess
+
+    structs = {"o2tpc_tf": o2tpc.o2tpc_tf, "o2tpc_stats": o2tpc.o2tpc_stats, "o2tpc_result": o2tpc.o2tpc_result,
+               "o2tpc_config": o2tpc.o2tpc_config, "o2tpc_tuning": o2tpc.o2tpc_tuning}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "o2tpc.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n")
+               if line)
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"

@@ -10,6 +10,8 @@ from paper_2106_03636_gb300 import o2tpc, synth
 pytestmark = pytest.mark.gpu
 
 ZUNIT = 0.003125 * 2.58
+RESULT_KEYS = ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref", "t0", "t0_err", "t0_lo",
+               "t0_hi", "mate", "collision")
 
 
 @pytest.fixture(scope="module")
@@ -101,7 +103,7 @@ def test_batch_equals_alone():
         mix = [b.poll(t) for t in tickets]
     assert all(m["stats"]["batch_size"] == len(tfs) for m in mix)
     for x, y in zip(alone, mix):
-        for k in ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref"):
+        for k in RESULT_KEYS:
             assert np.array_equal(x[k], y[k]), k
 
 
@@ -162,7 +164,7 @@ def test_uploads_ahead_equal_in_stream_uploads():
         assert y["status"] == 0
         st = y["stats"]["ms_stage"]
         assert np.isfinite(st[12]) and np.isfinite(st[13]) and st[12] >= 0 and st[13] >= 0
-        for k in ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref"):
+        for k in RESULT_KEYS:
             assert np.array_equal(x[k], y[k]), k
 
 
@@ -182,7 +184,7 @@ def test_launch_shapes_and_autotuner_leave_results_unchanged():
     threads per row) and the autotuner's choice change no result bit."""
     tf = synth.full_tpc_1ms(seed=21, n_coll=3)
     assert tf.n >= 1 << 20
-    keys = ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref")
+    keys = RESULT_KEYS
     with o2tpc.Tracker() as a:
         ref = a.track(tf)
         assert a.tuning()["tuned"] is False
@@ -208,7 +210,7 @@ def test_captured_path_equals_regular_path():
     results as the regular path, on two different batches in a row (the
     second a replay of the graph); with token capacities every batch
     overflows and reruns on the regular path, again with the same results."""
-    keys = ("offsets", "cluster_idx", "par", "cov", "chi2", "ndf", "flags", "zeta_ref")
+    keys = RESULT_KEYS
     sets = [synth.chunk_mix(seed=41, n_chunks=5) + [synth.single_sector(seed=42)],
             synth.chunk_mix(seed=43, n_chunks=7)]
     with o2tpc.Tracker() as r:
