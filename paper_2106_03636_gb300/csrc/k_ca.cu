@@ -559,6 +559,13 @@ __global__ void k_iota(int* __restrict__ out, int n) {
   if (i < n) out[i] = i;
 }
 
+__global__ void k_stream_tail() {}
+
+void launch_stream_tail(cudaStream_t st) {
+  k_stream_tail<<<1, 32, 0, st>>>();
+  ++g_launch_count;
+}
+
 void launch_iota(int* out, int n, cudaStream_t st) {
   if (n > 0) {
     k_iota<<<(n + 255) / 256, 256, 0, st>>>(out, n);

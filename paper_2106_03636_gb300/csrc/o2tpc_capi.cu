@@ -120,12 +120,16 @@ struct Pending {
   std::vector<std::shared_ptr<Job>> jobs;
   std::shared_ptr<BatchMem> out;  // device result arrays, freed once copied
   cudaEvent_t dl0 = nullptr, dl1 = nullptr;
+  cudaEvent_t trS = nullptr, trE = nullptr;  // timeline: batch start and compute end on the stream
+  double hS = 0.0, hD = 0.0;                 // host clock: batch start, downloads issued
   float stageMs[18] = {};
   double hostPrepMs = 0;
   bool captured = false;
   ~Pending() {
     if (dl0) cudaEventDestroy(dl0);
     if (dl1) cudaEventDestroy(dl1);
+    if (trS) cudaEventDestroy(trS);
+    if (trE) cudaEventDestroy(trE);
   }
 };
 
@@ -172,8 +176,10 @@ struct Ctx {
   std::condition_variable cvFin;
   std::deque<std::shared_ptr<Pending>> finQueue;
   bool finStop = false;
-  bool traceCopies = false;  // O2TPC_TRACE_COPIES=1: time every result copy (stderr)
-  int traceMode = 0;
+  bool traceCopies = false;  // O2TPC_TRACE_COPIES=1: time every result copy (stderr);
+  int traceMode = 0;         // =2: per-batch device timeline (stderr)
+  cudaEvent_t evRef = nullptr;  // timeline origin
+  double hostRef = 0.0;         // host clock when evRef was recorded
   // pinned staging for descriptors and results
   void* hStage = nullptr;
   size_t hStageBytes = 0;
@@ -933,6 +939,13 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   M.nTF = B;
   M.nRows = nRows;
   CK(cudaEventRecord(c->ev0, st));
+  cudaEvent_t trS = nullptr, trE = nullptr;
+  if (c->traceMode == 2) {
+    CK(cudaEventCreate(&trS));
+    CK(cudaEventCreate(&trE));
+    CK(cudaEventRecord(trS, st));
+  }
+  const double hS = now_ms();
   g_launch_count = 0;
   // inputs uploaded ahead: the batch waits for their copies and owns their memory
   for (auto& jp : jobs) {
@@ -970,6 +983,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   int* hStTf = hTrkTf + B + 1;
   int* hTlTf = hStTf + B + 1;
   unsigned* hErr = reinterpret_cast<unsigned*>(hTlTf + B + 1);
+  if (trE) CK(cudaEventRecord(trE, st));
   CK(cudaMemcpyAsync(hOff, ob.off, sizeof(int) * (nT + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(hTrkTf, trkTfBegin, sizeof(int) * (B + 1), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(hStTf, stTfBegin, sizeof(int) * (B + 1), cudaMemcpyDeviceToHost, st));
@@ -979,12 +993,16 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   for (int i = 0; i < B; ++i) CK(cudaMemcpyAsync(&tfFirstRow[i], grid + (size_t)i * kRowsPerTF, sizeof(RowGrid),
                                                  cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(c->evs[10], st));
+  launch_stream_tail(st);
   CK(cudaStreamSynchronize(st));
 
   auto P = std::make_shared<Pending>();
   P->jobs = jobs;
   P->out = pp.outMem;
   P->captured = captured;
+  P->trS = trS;
+  P->trE = trE;
+  P->hS = hS - c->hostRef;
   if (!captured) {  // the captured path records no stage events
     for (int k = 0; k < 10; ++k) cudaEventElapsedTime(&P->stageMs[k], c->evs[k], c->evs[k + 1]);
     // evs[11] splits step 8: the final refit, then the continuous-readout step
@@ -1080,6 +1098,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   CK(cudaEventRecord(P->dl1, dl));
   if (captured) CK(cudaEventRecord(c->graphDl, dl));  // the next replay reuses the result arrays
   P->hostPrepMs = now_ms() - tPrep;
+  P->hD = now_ms() - c->hostRef;
 
   M.tfHitBase.resize(B);
   M.tfHitEnd.resize(B);
@@ -1278,6 +1297,17 @@ void finisher_main(Ctx* c) {
     const cudaError_t e = cudaEventSynchronize(P->dl1);
     float dlMs = 0.f;
     if (e == cudaSuccess) cudaEventElapsedTime(&dlMs, P->dl0, P->dl1);
+    if (e == cudaSuccess && P->trS && c->evRef) {
+      float a = 0.f, b = 0.f, d0 = 0.f, d1 = 0.f;
+      cudaEventElapsedTime(&a, c->evRef, P->trS);
+      cudaEventElapsedTime(&b, c->evRef, P->trE);
+      cudaEventElapsedTime(&d0, c->evRef, P->dl0);
+      cudaEventElapsedTime(&d1, c->evRef, P->dl1);
+      std::fprintf(stderr,
+                   "o2tpc timeline: batch start %.3f compute end %.3f download %.3f - %.3f ms (host: start %.3f, "
+                   "downloads issued %.3f, done seen %.3f)\n",
+                   a, b, d0, d1, P->hS, P->hD, now_ms() - c->hostRef);
+    }
     const double tEnd = now_ms();
     P->out.reset();
     if (e == cudaSuccess) {
@@ -1393,6 +1423,12 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
       x->upAheadLimit = c.mem_budget / 8;
     }
     for (auto& e : x->evs) CK(cudaEventCreate(&e));
+    if (x->traceMode == 2) {
+      CK(cudaEventCreate(&x->evRef));
+      CK(cudaEventRecord(x->evRef, x->stream));
+      CK(cudaEventSynchronize(x->evRef));
+      x->hostRef = now_ms();
+    }
     for (auto& e : x->evTl) CK(cudaEventCreate(&e));
     fill_geom(x->hGeom, c.bz_tesla, c.vdrift_cm_us);
     x->dGeom = static_cast<GeomConst*>(x->dev_alloc(sizeof(GeomConst)));
@@ -1578,6 +1614,7 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->evWait) cudaEventDestroy(c->evWait);
+  if (c->evRef) cudaEventDestroy(c->evRef);
   if (c->upStream) {
     cudaStreamSynchronize(c->upStream);
     cudaStreamDestroy(c->upStream);

@@ -64,6 +64,10 @@ void launch_ballot_compact(int n, const int* nDev, const int* flag, const int* t
 void launch_count_at(const int* arr, const int* idx, int* dst, int cap, int* overflow, cudaStream_t st,
                      const int* arr2 = nullptr, int* dst2 = nullptr, int cap2 = 0, int* endBase = nullptr);
 void launch_iota(int* out, int n, cudaStream_t st);  // out[i] = i
+// An empty kernel: ends a stream's work of a batch on the compute engine, so
+// that the stream's next operations do not queue behind copies of other
+// streams on the copy engine that served its last copy.
+void launch_stream_tail(cudaStream_t st);
 void launch_tf_ranges(int nTF, const RowGrid* grid, const int* list, const int* nListDev, int* tfBegin,
                       cudaStream_t st);
 void launch_lower_bounds(const int* list, const int* nListDev, const int* keys, int nKeys, int* out,
