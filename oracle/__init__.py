@@ -15,15 +15,16 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "o2tpc_oracle.c")
+CTF_SRC = os.path.join(HERE, "o2tpc_ctf.c")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
-    deps = [SRC, os.path.join(HERE, "o2tpc_oracle.h")]
+    deps = [SRC, CTF_SRC, os.path.join(HERE, "o2tpc_oracle.h")]
     if force or not os.path.exists(SO) or any(os.path.getmtime(d) > os.path.getmtime(SO) for d in deps):
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", SO + ".tmp", SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", SO + ".tmp", SRC, CTF_SRC, "-lm"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("oracle build failed:\n" + r.stdout + r.stderr)
@@ -47,6 +48,7 @@ class _Input(ctypes.Structure):
         ("reverse_tracklet_order", ctypes.c_int32),
         ("coll_time", ctypes.c_void_p),
         ("n_coll", ctypes.c_int64),
+        ("compress", ctypes.c_int32),
     ]
 
 
@@ -71,6 +73,23 @@ def _load():
         lib.oracle_update.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
         lib.oracle_rotate.restype = ctypes.c_int32
         lib.oracle_rotate.argtypes = [dp, dp, dp, ctypes.c_double]
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.oracle_ctf_encode.restype = ctypes.c_int64
+        lib.oracle_ctf_encode.argtypes = [ctypes.c_int64, i32p, i32p, i32p, i32p, ctypes.c_int64, i64p, i32p, dp,
+                                          i32p, ctypes.c_int64, ctypes.POINTER(u8p)]
+        lib.oracle_ctf_decode.restype = ctypes.c_int64
+        lib.oracle_ctf_decode.argtypes = [u8p, ctypes.c_int64] + [ctypes.POINTER(i32p)] * 4 + [
+            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i64p)]
+        lib.oracle_ctf_normalize.restype = None
+        lib.oracle_ctf_normalize.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint16)]
+        lib.oracle_rans_encode.restype = ctypes.c_int64
+        lib.oracle_rans_encode.argtypes = [u8p, ctypes.c_int64, ctypes.POINTER(u8p)]
+        lib.oracle_rans_decode.restype = ctypes.c_int64
+        lib.oracle_rans_decode.argtypes = [u8p, ctypes.c_int64, ctypes.POINTER(u8p)]
+        lib.oracle_buffer_free.restype = None
+        lib.oracle_buffer_free.argtypes = [ctypes.c_void_p]
         lib.oracle_dca_arc.restype = ctypes.c_double
         lib.oracle_dca_arc.argtypes = [ctypes.c_double] * 4
         lib.oracle_fit_points.restype = ctypes.c_int32
@@ -79,7 +98,7 @@ def _load():
     return _lib
 
 
-_DT = {0: np.int32, 1: np.int64, 2: np.float64}
+_DT = {0: np.int32, 1: np.int64, 2: np.float64, 3: np.uint8}
 
 FIELDS = [
     "yu", "zu", "rid", "sorted_orig", "sorted_rid", "sorted_y", "sorted_z", "sorted_cell",
@@ -88,7 +107,7 @@ FIELDS = [
     "tl_hits", "tl_state", "st_sector", "st_tracklet", "st_zref", "st_off", "st_hits", "st_in", "st_out",
     "st_next", "st_prev", "pair_ab", "pair_chi2", "trk_off", "trk_cl", "trk_x", "trk_alpha", "trk_par",
     "trk_cov", "trk_chi2", "trk_ndf", "trk_sector", "trk_flags", "trk_zref", "trk_head", "trk_nseg",
-    "trk_t0", "trk_t0err", "trk_t0lo", "trk_t0hi", "trk_mate", "trk_coll", "mpair_ab", "mpair_chi2",
+    "trk_t0", "trk_t0err", "trk_t0lo", "trk_t0hi", "trk_mate", "trk_coll", "mpair_ab", "mpair_chi2", "ctf",
 ]
 
 
@@ -100,10 +119,12 @@ def _vp(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=None, coll_time=None) -> dict:
+def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=None, coll_time=None,
+        compress: bool = False) -> dict:
     """Runs the oracle on a ``synth.TimeFrame``-like object (attributes n,
     fmt, sector, row, y, z, packed, bz, vdrift, and optionally coll_time,
-    the TF's interaction times in us).  ``coll_time`` overrides the TF's.
+    the TF's interaction times in us).  ``coll_time`` overrides the TF's;
+    ``compress`` also builds the compressed TF (field ``ctf``, bytes).
     Returns a dict of numpy arrays (copies) named as in ``FIELDS``."""
     lib = _load()
     inp = _Input()
@@ -124,6 +145,7 @@ def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=N
     inp.vdrift = tf.vdrift
     inp.sector_mask = sector_mask
     inp.reverse_tracklet_order = int(reverse_tracklet_order)
+    inp.compress = int(compress)
     ct = coll_time if coll_time is not None else getattr(tf, "coll_time", None)
     if ct is not None and len(ct):
         ct = np.ascontiguousarray(np.asarray(ct, dtype=np.float64))
@@ -209,3 +231,72 @@ def dca_arc(x0: float, y0: float, snp: float, k: float) -> float:
     """Signed transverse arc length from (x0, y0), sin(phi) = snp, curvature
     k = dphi/ds, to the closest approach to the origin."""
     return float(_load().oracle_dca_arc(x0, y0, snp, k))
+
+
+def _take(lib, ptr, n, dtype):
+    out = np.ctypeslib.as_array(ptr, shape=(n,)).copy() if n > 0 else np.zeros(0, dtype)
+    lib.oracle_buffer_free(ctypes.cast(ptr, ctypes.c_void_p))
+    return out.astype(dtype, copy=False)
+
+
+def rans_encode(sym) -> np.ndarray:
+    """One byte stream through the CTF's entropy coder (table, chunk sizes,
+    payloads)."""
+    lib = _load()
+    a = np.ascontiguousarray(np.asarray(sym, dtype=np.uint8))
+    out = ctypes.POINTER(ctypes.c_uint8)()
+    n = lib.oracle_rans_encode(a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), len(a), ctypes.byref(out))
+    return _take(lib, out, n, np.uint8)
+
+
+def rans_decode(blob):
+    lib = _load()
+    a = np.ascontiguousarray(np.asarray(blob, dtype=np.uint8))
+    out = ctypes.POINTER(ctypes.c_uint8)()
+    n = lib.oracle_rans_decode(a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), len(a), ctypes.byref(out))
+    if n < 0:
+        raise OracleError("malformed rANS stream")
+    return _take(lib, out, n, np.uint8)
+
+
+def ctf_normalize(count) -> np.ndarray:
+    lib = _load()
+    c = np.ascontiguousarray(np.asarray(count, dtype=np.uint64))
+    assert len(c) == 256
+    f = np.zeros(256, np.uint16)
+    lib.oracle_ctf_normalize(c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                             f.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)))
+    return f
+
+
+def ctf_encode(sector, row, y, z, trk_off, trk_cl, trk_qpt, sorted_orig) -> np.ndarray:
+    """The compressed TF of the given clusters (integer units) and tracks."""
+    lib = _load()
+    i32 = lambda v: np.ascontiguousarray(np.asarray(v, dtype=np.int32))
+    sector, row, y, z, trk_cl, sorted_orig = map(i32, (sector, row, y, z, trk_cl, sorted_orig))
+    trk_off = np.ascontiguousarray(np.asarray(trk_off, dtype=np.int64))
+    trk_qpt = np.ascontiguousarray(np.asarray(trk_qpt, dtype=np.float64))
+    P = lambda a, t: a.ctypes.data_as(ctypes.POINTER(t))
+    out = ctypes.POINTER(ctypes.c_uint8)()
+    n = lib.oracle_ctf_encode(len(sector), P(sector, ctypes.c_int32), P(row, ctypes.c_int32), P(y, ctypes.c_int32),
+                              P(z, ctypes.c_int32), len(trk_off) - 1, P(trk_off, ctypes.c_int64),
+                              P(trk_cl, ctypes.c_int32), P(trk_qpt, ctypes.c_double),
+                              P(sorted_orig, ctypes.c_int32), len(sorted_orig), ctypes.byref(out))
+    return _take(lib, out, n, np.uint8)
+
+
+def ctf_decode(blob) -> dict:
+    """The cluster sequence of a compressed TF: sector, row, y, zeta arrays
+    and the kept tracks' cluster counts (the tracks come first)."""
+    lib = _load()
+    a = np.ascontiguousarray(np.asarray(blob, dtype=np.uint8))
+    ptrs = [ctypes.POINTER(ctypes.c_int32)() for _ in range(4)]
+    nt = ctypes.c_int64()
+    lens = ctypes.POINTER(ctypes.c_int64)()
+    n = lib.oracle_ctf_decode(a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), len(a), *[ctypes.byref(p) for p in ptrs],
+                              ctypes.byref(nt), ctypes.byref(lens))
+    if n < 0:
+        raise OracleError("malformed compressed TF")
+    out = {k: _take(lib, p, n, np.int32) for k, p in zip(("sector", "row", "y", "z"), ptrs)}
+    out["track_len"] = _take(lib, lens, nt.value, np.int64)
+    return out

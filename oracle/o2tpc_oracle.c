@@ -116,6 +116,8 @@ struct oracle_result {
   double *trk_t0, *trk_t0err, *trk_t0lo, *trk_t0hi;
   int32_t *trk_mate, *trk_coll;
   int64_t nmpair; int32_t* mpair_ab; double* mpair_chi2;
+  /* compressed TF */
+  uint8_t* ctf; int64_t ctf_bytes;
   o_field fields[80]; int nf;
 };
 
@@ -1057,6 +1059,17 @@ oracle_result* oracle_run(const oracle_input* in, int32_t* status) {
   o_merge(R, in->sector_mask);
   o_final(R);
   o_continuous(R, in);
+  if (in->compress) {
+    int64_t n = R->n;
+    int32_t* sec = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    int32_t* row = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+    double* qpt = (double*)malloc(sizeof(double) * ((size_t)R->ntrk + 1));
+    for (int64_t i = 0; i < n; ++i) { sec[i] = R->rid[i] / O_NROW; row[i] = R->rid[i] % O_NROW; }
+    for (int64_t t = 0; t < R->ntrk; ++t) qpt[t] = R->trk_par[5 * t + 4];
+    R->ctf_bytes = oracle_ctf_encode(n, sec, row, R->yu, R->zu, R->ntrk, R->trk_off, R->trk_cl, qpt, R->s_orig,
+                                     R->nsel, &R->ctf);
+    free(sec); free(row); free(qpt);
+  }
   o_add(R, "yu", R->yu, R->n, 0); o_add(R, "zu", R->zu, R->n, 0); o_add(R, "rid", R->rid, R->n, 0);
   o_add(R, "sorted_orig", R->s_orig, R->nsel, 0); o_add(R, "sorted_rid", R->s_rid, R->nsel, 0);
   o_add(R, "sorted_y", R->s_y, R->nsel, 0); o_add(R, "sorted_z", R->s_z, R->nsel, 0); o_add(R, "sorted_cell", R->s_cell, R->nsel, 0);
@@ -1087,6 +1100,7 @@ oracle_result* oracle_run(const oracle_input* in, int32_t* status) {
   o_add(R, "trk_t0lo", R->trk_t0lo, R->ntrk, 2); o_add(R, "trk_t0hi", R->trk_t0hi, R->ntrk, 2);
   o_add(R, "trk_mate", R->trk_mate, R->ntrk, 0); o_add(R, "trk_coll", R->trk_coll, R->ntrk, 0);
   o_add(R, "mpair_ab", R->mpair_ab, R->nmpair * 2, 0); o_add(R, "mpair_chi2", R->mpair_chi2, R->nmpair, 2);
+  o_add(R, "ctf", R->ctf, R->ctf_bytes, 3);
   *status = 0;
   return R;
 }
@@ -1105,7 +1119,7 @@ void oracle_free(oracle_result* R) {
                 R->st_in, R->st_out, R->st_next, R->st_prev, R->pair_ab, R->pair_chi2, R->trk_off, R->trk_cl,
                 R->trk_x, R->trk_alpha, R->trk_par, R->trk_cov, R->trk_chi2, R->trk_ndf, R->trk_sector,
                 R->trk_flags, R->trk_zref, R->trk_head, R->trk_nseg, R->trk_t0, R->trk_t0err, R->trk_t0lo,
-                R->trk_t0hi, R->trk_mate, R->trk_coll, R->mpair_ab, R->mpair_chi2};
+                R->trk_t0hi, R->trk_mate, R->trk_coll, R->mpair_ab, R->mpair_chi2, R->ctf};
   for (size_t i = 0; i < sizeof(ps) / sizeof(ps[0]); ++i) free(ps[i]);
   free(R);
 }

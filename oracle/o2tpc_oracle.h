@@ -28,6 +28,7 @@ typedef struct {
   int32_t reverse_tracklet_order; /* 1: build tracklets in reverse order (selection order-independence test) */
   const double* coll_time; /* interaction times of the TF, us, ascending (may be NULL) */
   int64_t n_coll;
+  int32_t compress;        /* 1: also build the compressed TF ("ctf", o2tpc_ctf.c) */
 } oracle_input;
 
 typedef struct oracle_result oracle_result;
@@ -37,7 +38,7 @@ oracle_result* oracle_run(const oracle_input* in, int32_t* status);
 void oracle_free(oracle_result* r);
 /* Named outputs (see o2tpc_oracle.c, oracle_get).  Returns the element count
  * (-1 if unknown name); *ptr points into the result (owned by it);
- * *type: 0 int32, 1 int64, 2 double. */
+ * *type: 0 int32, 1 int64, 2 double, 3 uint8. */
 int64_t oracle_get(oracle_result* r, const char* name, const void** ptr, int32_t* type);
 
 /* Building blocks, exposed so that the tests can pin them one by one. */
@@ -48,6 +49,22 @@ int32_t oracle_rotate(double* x, double* p5, double* c15, double dalpha);
  * seeds y and zeta, (sin phi, t, q/pT) come from p5; the initial covariance is
  * c15 if c15[0] > 0, else the tracker's initial diagonal.  Returns the state
  * and covariance at the last point in p5, c15. */
+/* Compressed TF (o2tpc_ctf.c): encoder over plain arrays (per input cluster
+ * sector, row, y, zeta in integer units; tracks as offsets + input indices;
+ * q/pT per track; the sorted-hit order), decoder back to the cluster
+ * sequence, and the entropy coder alone.  Buffers returned through out
+ * pointers are malloc'd; the caller frees them.  Decoders return -1 on a
+ * malformed input. */
+int64_t oracle_ctf_encode(int64_t n_clusters, const int32_t* sector, const int32_t* row, const int32_t* y,
+                          const int32_t* z, int64_t n_tracks, const int64_t* trk_off, const int32_t* trk_cl,
+                          const double* trk_qpt, const int32_t* sorted_orig, int64_t n_sorted, uint8_t** out);
+int64_t oracle_ctf_decode(const uint8_t* blob, int64_t bytes, int32_t** sector, int32_t** row, int32_t** y,
+                          int32_t** z, int64_t* n_tracks, int64_t** trk_len);
+void oracle_ctf_normalize(const uint64_t* count, uint16_t* freq);
+int64_t oracle_rans_encode(const uint8_t* sym, int64_t n, uint8_t** out);
+int64_t oracle_rans_decode(const uint8_t* blob, int64_t bytes, uint8_t** out);
+void oracle_buffer_free(void* p);
+
 /* Signed transverse arc length from (x0, y0) with sin(phi) = snp and
  * curvature k = dphi/ds to the closest approach to the origin. */
 double oracle_dca_arc(double x0, double y0, double snp, double k);
