@@ -390,10 +390,10 @@ def run_chunks(args, rank, world, local):
                         "gpu_launches": l_b, "captured_graph": captured_b == [1],
                         "graph_launches_per_step": 1 if captured_b == [1] else 0},
             "plain": {"value": world * n / (ms_p / 1e3), "ms_per_step": ms_p, "gpu_launches": l_p,
-                      "stage_ms": {names[i]: round(float(stage_p[i]), 3) for i in range(len(o2tpc.STAGES) - 1)}},
+                      "stage_ms": {names[i]: round(float(stage_p[i]), 3) for i in range(len(o2tpc.STAGES))}},
             "speedup_batched_vs_plain": ms_p / ms_b,
             "stage_ms_source": "regular path, same batch" if captured_b == [1] else "batched arm",
-            "stage_ms": {names[i]: round(float(stage_b[i]), 3) for i in range(len(o2tpc.STAGES) - 1)},
+            "stage_ms": {names[i]: round(float(stage_b[i]), 3) for i in range(len(o2tpc.STAGES))},
             "roofline": roofline(stage_b, names, n, peak, peak_kind),
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "peak": peak,
                               "frac": n / (ms_b / 1e3) * PATH_BYTES / 1e9 / peak},
@@ -541,6 +541,7 @@ def main():
     ap.add_argument("--seed", type=int, default=20210609)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compress", action="store_true", help="skip the compressed-TF measurement")
     ap.add_argument("--trace", action="store_true", help="per-TF stage times on stderr")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
     ap.add_argument("--no-graph", action="store_true", help="chunks: batched arm on the regular path, not captured")
@@ -591,7 +592,7 @@ def main():
         if args.trace:
             st = r["stats"]["ms_stage"]
             print(f"{tag}: batch {r['stats']['batch_size']} device {r['stats']['ms_device']:.2f} ms, "
-                  + ", ".join(f"{o2tpc.STAGES[i]} {st[i]:.2f}" for i in range(len(o2tpc.STAGES) - 1)), file=sys.stderr, flush=True)
+                  + ", ".join(f"{o2tpc.STAGES[i]} {st[i]:.2f}" for i in range(len(o2tpc.STAGES))), file=sys.stderr, flush=True)
 
     def step(location, arrays):
         r = trk.wait(trk.submit(tf, location=location, arrays=arrays))
@@ -680,14 +681,46 @@ def main():
         ms_hs, lat_hs, sizes_hs, _ = served(o2tpc.O2TPC_LOC_HOST, pin, n_served, args.inflight)
         h2d = 12 * n if tf.fmt == 1 else 10 * n
         nt, ncl = rh["n_tracks"], rh["n_cluster_refs"]
-        d2h = 8 * (nt + 1) + 4 * ncl + nt * (4 * 2 + 20 + 60 + 4 + 4 + 1 + 1 + 4)
+        # offsets, cluster indices; x, alpha, par, cov, chi2, ndf, sector, flags, zeta_ref,
+        # t0 / error / bounds, membrane partner, collision
+        d2h = 8 * (nt + 1) + 4 * ncl + nt * (4 * 2 + 20 + 60 + 4 + 4 + 1 + 1 + 4 + 16 + 4 + 4)
         e2e = {"value": world * n * n_served / (ms_hs / 1e3), "unit": "clusters/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "mode": "served from pinned host memory",
                "ms_per_step": ms_hs / n_served, "p50_ms": float(np.percentile(lat_hs, 50)),
                "p99_ms": float(np.percentile(lat_hs, 99)), "batch_sizes": sizes_hs,
                "plain": {"value": world * n / (ms_h / args.steps / 1e3), "ms_per_step": ms_h / args.steps,
                          "p50_ms": float(np.percentile(lat_h, 50)), "p99_ms": float(np.percentile(lat_h, 99)),
-                         "stage_ms": {o2tpc.STAGES[i]: round(float(stage_h[i]), 3) for i in range(len(o2tpc.STAGES) - 1)}}}
+                         "stage_ms": {o2tpc.STAGES[i]: round(float(stage_h[i]), 3) for i in range(len(o2tpc.STAGES))}}}
+
+    tuning = trk.tuning()
+    trk.close()  # its memory pool goes before the next context's
+    # the compressed TF (Sec. 2.2) on the same TF: one TF at a time, device input
+    compressed = None
+    if not args.no_compress:
+        ctk = o2tpc.Tracker(device=local, flags=tune | o2tpc.O2TPC_FLAG_COMPRESS)
+        for _ in range(2):
+            rc = ctk.wait(ctk.submit(tf, location=o2tpc.O2TPC_LOC_DEVICE, arrays=dev))
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(3, min(args.steps, 5))
+        cst = np.zeros(len(o2tpc.STAGES))
+        c0.record(ctk.stream)
+        for _ in range(k):
+            rc = ctk.wait(ctk.submit(tf, location=o2tpc.O2TPC_LOC_DEVICE, arrays=dev))
+            if rc["status"] != 0:
+                raise RuntimeError(o2tpc.o2tpc_strerror(rc["status"]))
+            cst += np.asarray(rc["stats"]["ms_stage"])
+        c1.record(ctk.stream)
+        torch.cuda.synchronize()
+        cms = device_max(c0.elapsed_time(c1), world, local) / k
+        cst /= k
+        compressed = {"value": world * n / (cms / 1e3), "unit": "clusters/s", "ms_per_step": cms,
+                      "mode": "plain, one TF at a time, tracking + compressed TF",
+                      "ctf_bytes": rc["ctf_bytes"], "ctf_bytes_per_cluster": rc["ctf_bytes"] / n,
+                      "ratio_vs_12B_records": 12.0 * n / max(1, rc["ctf_bytes"]),
+                      "stage_ms_compress": round(float(cst[o2tpc.STAGES.index("compress")]), 3),
+                      "compress_clusters_per_s": n / (float(cst[o2tpc.STAGES.index("compress")]) / 1e3)}
+        ctk.close()
 
     peak, peak_kind = peaks()
     names = o2tpc.STAGES
@@ -716,13 +749,12 @@ def main():
             "plain": {"value": plain_value, "tf_per_s": world / (ms_step / 1e3), "ms_per_step": ms_step,
                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                       "steps": args.steps},
-            "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(len(o2tpc.STAGES) - 1)},
+            "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(len(o2tpc.STAGES))},
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "frac": path_frac, "peak": peak},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_s, "clocks": clocks,
-            "autotune": trk.tuning()}
+            "autotune": tuning, "compressed": compressed}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    trk.close()
     if world > 1:
         dist.destroy_process_group()
 

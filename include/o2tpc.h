@@ -87,10 +87,17 @@ enum {
                                        time the launch shapes of the tunable
                                        steps on that batch and keep the fastest
                                        (see o2tpc_get_tuning)                  */
-  O2TPC_FLAG_GRAPH_TIGHT = 1u << 4  /* captured path with token capacities (16
+  O2TPC_FLAG_GRAPH_TIGHT = 1u << 4, /* captured path with token capacities (16
                                        tracklets, sector tracks, pairs): batches
                                        overflow and rerun on the regular path
                                        (testing aid)                           */
+  O2TPC_FLAG_COMPRESS = 1u << 5     /* also build each TF's compressed form
+                                       (o2tpc_result.ctf; Sec. 2.2: clusters of
+                                       tracks with pT < 0.1 GeV removed, a
+                                       straight-line integer track model, rANS;
+                                       format in csrc/k_ctf.cu).  Batches take
+                                       the regular path; 48 more device bytes
+                                       per cluster                             */
 };
 
 typedef struct {
@@ -205,7 +212,7 @@ typedef struct {
    * inputs that were uploaded ahead on the context's copy stream; 14 and 15
    * the outward and the inward following passes inside step 4; 16 the
    * continuous-readout step (t0, membrane links, collision assignment) that
-   * follows step 8; 17 reserved (0) */
+   * follows step 8; 17 the compressed-TF step (O2TPC_FLAG_COMPRESS) */
   float ms_stage[18];
   uint32_t captured;         /* 1: the batch ran as one CUDA graph launch (the
                                 captured path: ms_stage holds only 10-13)     */
@@ -245,6 +252,12 @@ typedef struct {
   const float* t0_hi;          /* [n_tracks] us                                      */
   const int32_t* mate;         /* [n_tracks] the other half across the membrane, -1 */
   const int32_t* collision;    /* [n_tracks] interaction index, -1                   */
+  /* With O2TPC_FLAG_COMPRESS: the TF's compressed form (NULL / 0 otherwise).
+   * Lossless for the kept clusters' integer coordinates (sector, row, y in
+   * 1/160 cm, zeta in 1/64 time bin); clusters of tracks with pT < 0.1 GeV
+   * are left out.                                                           */
+  const uint8_t* ctf;
+  uint64_t ctf_bytes;
   o2tpc_stats stats;
   uint64_t user_tag;
   int32_t status;              /* O2TPC_OK or the error of this TF                    */

@@ -30,6 +30,7 @@ CUDA_SOURCES = [
     "k_track.cu",
     "k_merge.cu",
     "k_cont.cu",
+    "k_ctf.cu",
     "o2tpc_static.cu",
     "o2tpc_graph.cu",
 ]

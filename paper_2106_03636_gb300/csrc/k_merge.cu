@@ -314,7 +314,6 @@ __global__ void k_head_flags(MergeBufs mb, int* __restrict__ headFlag) {
   if (i < nSt) headFlag[i] = mb.prev[i] < 0;
 }
 
-constexpr int kMaxChain = 64;  // segments per chain, at most
 
 __global__ void k_chain_counts(const int* __restrict__ nHeadsDev, const int* __restrict__ heads, SectorTrackBufs sb,
                                MergeBufs mb,

@@ -152,6 +152,7 @@ struct Ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evWait = nullptr;
   cudaEvent_t evs[12] = {};
   cudaEvent_t evTl[4] = {};  // ends of the four tracklet passes
+  cudaEvent_t evCtf[2] = {};  // the compression step
   o2tpc_tuning tune{};       // launch shapes in use (autotuner results)
   // captured path: arena, graph, and the event after the last replay's
   // result copies (the next replay overwrites the result arrays)
@@ -256,7 +257,10 @@ T* dalloc(BatchMem& m, size_t count) {
   return static_cast<T*>(m.alloc(sizeof(T) * std::max<size_t>(count, 1)));
 }
 
-uint64_t footprint_of(uint64_t n) { return 160ull * n + (64ull << 20); }
+// Device bytes a TF may take: 160 per cluster (+ 48 with the compressed TF)
+uint64_t footprint_of(uint64_t n, bool compress = false) {
+  return (compress ? 208ull : 160ull) * n + (64ull << 20);
+}
 
 // Device layout of a host-resident TF's copy: the packed records, or
 // sector[n] u8 | row[n] u8 | pad to 16 B | y[n] f32 | z[n] f32.
@@ -401,10 +405,13 @@ struct Pipe {
   const int *trkTfBegin = nullptr, *stTfBegin = nullptr, *tlTfBegin = nullptr;
   const unsigned* dErr = nullptr;
   std::shared_ptr<BatchMem> outMem;  // result arrays freed after the download (regular path)
+  uint8_t* ctf = nullptr;            // compressed TFs of the batch, at ctfOff[i]
+  std::vector<long long> ctfOff;
 };
 
 // A batch runs on the captured path when it fits the arena.
 bool graph_fits(const Ctx* c, const std::vector<std::shared_ptr<Job>>& jobs) {
+  if (c->cfg.flags & O2TPC_FLAG_COMPRESS) return false;  // the compressed TF reads its blob size back
   const GraphCaps& k = c->graph->caps;
   if ((int)jobs.size() > k.BCap) return false;
   long long n = 0, nc = 0;
@@ -845,6 +852,48 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
     launch_continuous(nHeads, &C->nHeads, nKeys, ob, mm, G, dTF, dColl, trkTfBegin, dErr, scratch, st);
   }
   CKL();
+  // ---- compressed TF: hit removal, track model, rANS (one size read for the blob)
+  if (c->cfg.flags & O2TPC_FLAG_COMPRESS) {
+    CK(cudaEventRecord(c->evCtf[0], st));
+    CtfBufs cb{};
+    cb.nSeqCap = n;
+    cb.nTrkCap = nHeads;
+    cb.chunkCap = ctf_chunk_cap(n, nHeads, B);
+    cb.onTrack = dalloc<uint8_t>(M, (size_t)n + 1);
+    cb.firstFlag = dalloc<int>(M, (size_t)n + 1);
+    cb.trkAtFirst = dalloc<int>(M, n);
+    cb.unFlag = dalloc<int>(M, (size_t)n + 1);
+    cb.canonFirst = dalloc<int>(M, nHeads);
+    cb.canonTrk = dalloc<int>(M, nHeads);
+    cb.len = dalloc<int>(M, (size_t)nHeads + 1);
+    cb.lenScan = dalloc<int>(M, (size_t)nHeads + 1);
+    cb.unList = dalloc<int>(M, n);
+    cb.inBase = dalloc<int>(M, B + 1);
+    cb.tfKt = dalloc<int>(M, B + 1);
+    cb.tfUn = dalloc<int>(M, B + 1);
+    cb.counts = dalloc<int>(M, 4);
+    cb.tfCounts = dalloc<int>(M, 3 * B);
+    cb.sd = dalloc<CtfStream>(M, 10 * B);
+    cb.sym = dalloc<uint8_t>(M, 8 * (size_t)n + 2 * (size_t)nHeads + 16);
+    cb.hist = dalloc<unsigned>(M, 2560 * (size_t)B);
+    cb.freq = dalloc<uint16_t>(M, 2560 * (size_t)B);
+    cb.cum = dalloc<unsigned>(M, 2570 * (size_t)B);
+    cb.scratch = dalloc<uint8_t>(M, (size_t)cb.chunkCap * kCtfChunkBytes);
+    cb.bytes = dalloc<int>(M, (size_t)cb.chunkCap + 1);
+    cb.payOff = dalloc<int>(M, (size_t)cb.chunkCap + 1);
+    cb.tfBlob = dalloc<long long>(M, B + 1);
+    cb.tfHead = dalloc<long long>(M, B);
+    launch_ctf_symbols(n, &C->n, nHeads, &C->nHeads, B, dTF, grid, nRows, syz, sorig, heads, sb, mb, ob, cb, tileCnt,
+                       tileOff, &C->overflow, scratch, st);
+    CKL();
+    pp.ctfOff.resize(B + 1);
+    CK(cudaMemcpyAsync(pp.ctfOff.data(), cb.tfBlob, sizeof(long long) * (B + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));  // sync 5
+    pp.ctf = dalloc<uint8_t>(OM, (size_t)pp.ctfOff[B] + 16);
+    launch_ctf_blob(B, cb, pp.ctf, st);
+    CKL();
+    CK(cudaEventRecord(c->evCtf[1], st));
+  }
   CK(cudaEventRecord(c->ev1, st));
   CK(cudaEventRecord(c->evs[9], st));
 
@@ -1007,7 +1056,8 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     for (int k = 0; k < 10; ++k) cudaEventElapsedTime(&P->stageMs[k], c->evs[k], c->evs[k + 1]);
     // evs[11] splits step 8: the final refit, then the continuous-readout step
     cudaEventElapsedTime(&P->stageMs[8], c->evs[8], c->evs[11]);
-    cudaEventElapsedTime(&P->stageMs[16], c->evs[11], c->evs[9]);
+    cudaEventElapsedTime(&P->stageMs[16], c->evs[11], (c->cfg.flags & O2TPC_FLAG_COMPRESS) ? c->evCtf[0] : c->evs[9]);
+    if (c->cfg.flags & O2TPC_FLAG_COMPRESS) cudaEventElapsedTime(&P->stageMs[17], c->evCtf[0], c->evCtf[1]);
     cudaEventElapsedTime(&P->stageMs[12], c->evWait, c->evs[0]);
     cudaEventElapsedTime(&P->stageMs[14], c->evTl[0], c->evTl[1]);
     cudaEventElapsedTime(&P->stageMs[15], c->evTl[2], c->evTl[3]);
@@ -1033,8 +1083,9 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     const int t0 = hTrkTf[i], t1 = hTrkTf[i + 1];
     const size_t nt = (size_t)(t1 - t0);
     const size_t ncl = (size_t)(hOff[t1] - hOff[t0]);
+    const size_t nctf = pp.ctf ? (size_t)(pp.ctfOff[i + 1] - pp.ctfOff[i]) : 0;
     const size_t bytes = r16(8 * (nt + 1)) + r16(4 * ncl) + 11 * r16(4 * nt) + r16(20 * nt) + r16(60 * nt) +
-                         2 * r16(nt) + 64;
+                         2 * r16(nt) + r16(nctf) + 64;
     J.host = c->pinned_get(bytes, &J.hostBytes);
     char* q = static_cast<char*>(J.host);
     auto take = [&](const void* dsrc, size_t nb) -> char* {
@@ -1081,6 +1132,8 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     R.t0_hi = reinterpret_cast<const float*>(take(ob.t0hi + t0, 4 * nt));
     R.mate = reinterpret_cast<const int32_t*>(take(ob.mate + t0, 4 * nt));
     R.collision = reinterpret_cast<const int32_t*>(take(ob.coll + t0, 4 * nt));
+    R.ctf = nctf ? reinterpret_cast<const uint8_t*>(take(pp.ctf + pp.ctfOff[i], nctf)) : nullptr;
+    R.ctf_bytes = (uint64_t)nctf;
     for (size_t k = 0; k <= nt; ++k) off64[k] = (uint64_t)(hOff[t0 + k] - hOff[t0]);
     R.user_tag = J.tf.user_tag;
     R.stats.n_clusters = J.tf.n;
@@ -1430,6 +1483,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
       x->hostRef = now_ms();
     }
     for (auto& e : x->evTl) CK(cudaEventCreate(&e));
+    for (auto& e : x->evCtf) CK(cudaEventCreate(&e));
     fill_geom(x->hGeom, c.bz_tesla, c.vdrift_cm_us);
     x->dGeom = static_cast<GeomConst*>(x->dev_alloc(sizeof(GeomConst)));
     x->dCounts = static_cast<Counts*>(x->dev_alloc(sizeof(Counts)));
@@ -1483,7 +1537,7 @@ static int check_tf(const Ctx* c, const o2tpc_tf* tf) {
     }
   }
   if (tf->n >= kMaxBatchHits) return O2TPC_ETOOBIG;
-  if (footprint_of(tf->n) > c->cfg.mem_budget) return O2TPC_ETOOBIG;
+  if (footprint_of(tf->n, (c->cfg.flags & O2TPC_FLAG_COMPRESS) != 0) > c->cfg.mem_budget) return O2TPC_ETOOBIG;
   return O2TPC_OK;
 }
 
@@ -1497,7 +1551,7 @@ int o2tpc_submit_many(o2tpc_ctx* ctx, const o2tpc_tf* tfs, uint32_t n, uint64_t*
     if (rc != O2TPC_OK) return rc;
     js[i] = std::make_shared<Job>();
     js[i]->tf = tfs[i];
-    js[i]->footprint = footprint_of(tfs[i].n);
+    js[i]->footprint = footprint_of(tfs[i].n, (c->cfg.flags & O2TPC_FLAG_COMPRESS) != 0);
     js[i]->t_submit = t;
   }
   {
@@ -1610,6 +1664,8 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
   for (auto& e : c->evs)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->evTl)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->evCtf)
     if (e) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);

@@ -141,6 +141,7 @@ struct MergeBufs {
   int* reached;      // [nSt]
   const Counts* cnt; // device sizes (nSt, nKeys)
 };
+constexpr int kMaxChain = 64;  // segments per merged chain, at most
 void launch_merge_keys(int nSt, const SectorTrackBufs sb, const GeomConst* G, MergeBufs mb, int nKeys, int* scratch,
                        cudaStream_t st);
 void launch_merge_pairs(int nSt, const SectorTrackBufs sb, const GeomConst* G, MergeBufs mb, unsigned* err,
@@ -181,6 +182,49 @@ struct OutBufs {
 void launch_final_refit(int nHeads, const int* nHeadsDev, const int* heads, const SectorTrackBufs sb, MergeBufs mb,
                         const int2* syz, const int* sorig, const TFDesc* tfs, const GeomConst* G, int forceFp64,
                         OutBufs ob, cudaStream_t st);
+// Compressed TF (csrc/k_ctf.cu).  Stream table entry: first symbol, symbol
+// count, first chunk, chunk count.
+struct CtfStream {
+  long long start, count;
+  int chunk0, nChunks;
+};
+constexpr int kCtfChunkBytes = 24640;  // >= 4 + 1.5 * 16384: a coded chunk at most
+struct CtfBufs {
+  uint8_t* onTrack;    // [n + 1] input cluster on a track
+  int* firstFlag;      // [n + 1] input index of a kept track's first cluster
+  int* trkAtFirst;     // [n]
+  int* unFlag;         // [n + 1] sorted hit on no track
+  int* canonFirst;     // [nTrk] first-cluster input indices of kept tracks, ascending
+  int* canonTrk;       // [nTrk] the tracks in that order
+  int* len;            // [nTrk + 1] their cluster counts
+  int* lenScan;        // [nTrk + 1]
+  int* unList;         // [n] sorted hits on no track, ascending
+  int* inBase;         // [nTF + 1]
+  int* tfKt;           // [nTF + 1] kept-track list range of each TF
+  int* tfUn;           // [nTF + 1] free-cluster list range of each TF
+  int* counts;         // [4] kept tracks, free clusters, chunks
+  int* tfCounts;       // [nTF * 3] header counts
+  CtfStream* sd;       // [nTF * 10]
+  uint8_t* sym;        // [8 nSeqCap + 2 nTrkCap] byte planes
+  long long nSeqCap, nTrkCap;
+  int chunkCap;
+  unsigned* hist;      // [nTF * 10 * 256]
+  uint16_t* freq;      // [nTF * 10 * 256]
+  unsigned* cum;       // [nTF * 10 * 257]
+  uint8_t* scratch;    // [chunkCap * kCtfChunkBytes]
+  int* bytes;          // [chunkCap + 1] coded chunk sizes
+  int* payOff;         // [chunkCap + 1]
+  long long* tfBlob;   // [nTF + 1] blob offset of each TF, total at nTF
+  long long* tfHead;   // [nTF] header bytes of each TF
+};
+int ctf_chunk_cap(long long nSeqCap, long long nTrkCap, int nTF);
+// Everything up to the blob sizes (cb.tfBlob); then, with the blob
+// allocated, the headers and payload copies.
+void launch_ctf_symbols(int n, const int* nDev, int nTrk, const int* nTrkDev, int nTF, const TFDesc* tfs,
+                        const RowGrid* grid, int nRows, const int2* syz, const int* sorig, const int* heads,
+                        SectorTrackBufs sb, MergeBufs mb, OutBufs ob, CtfBufs cb, int* tileCnt, int* tileOff,
+                        int* overflow, int* scratch, cudaStream_t st);
+void launch_ctf_blob(int nTF, CtfBufs cb, uint8_t* blob, cudaStream_t st);
 // Sorts every list of mb (listStart, listKey, listItems) by key, then item.
 void launch_list_sort(int nKeys, MergeBufs mb, cudaStream_t st);
 // Continuous-readout stage over the batch's nTrk (capacity) tracks.  mb: the

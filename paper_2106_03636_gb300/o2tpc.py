@@ -34,6 +34,7 @@ O2TPC_LOC_DEVICE = 1
 O2TPC_FLAG_KEEP_STAGES = 1 << 0
 O2TPC_FLAG_AUTOTUNE = 1 << 3
 O2TPC_FLAG_GRAPH_TIGHT = 1 << 4
+O2TPC_FLAG_COMPRESS = 1 << 5
 O2TPC_FLAG_NO_BATCHING = 1 << 1
 O2TPC_FLAG_FORCE_FP64 = 1 << 2
 
@@ -112,7 +113,7 @@ class o2tpc_stats(ctypes.Structure):
 
 STAGES = ("ingest", "sort", "neighbours", "clean_starts", "tracklets", "selection", "sector_fit", "merge",
           "refit", "sizes", "download", "host_prep", "upload", "upload_wait", "tl_out", "tl_in", "continuous",
-          "reserved")
+          "compress")
 
 
 class o2tpc_result(ctypes.Structure):
@@ -135,6 +136,8 @@ class o2tpc_result(ctypes.Structure):
         ("t0_hi", ctypes.POINTER(ctypes.c_float)),
         ("mate", ctypes.POINTER(ctypes.c_int32)),
         ("collision", ctypes.POINTER(ctypes.c_int32)),
+        ("ctf", ctypes.POINTER(ctypes.c_uint8)),
+        ("ctf_bytes", ctypes.c_uint64),
         ("stats", o2tpc_stats),
         ("user_tag", ctypes.c_uint64),
         ("status", ctypes.c_int32),
@@ -276,6 +279,7 @@ def result_to_dict(r: o2tpc_result) -> dict:
         flags=_np(r.flags, n, np.uint8), zeta_ref=_np(r.zeta_ref, n, np.uint32),
         t0=_np(r.t0, n, np.float32), t0_err=_np(r.t0_err, n, np.float32), t0_lo=_np(r.t0_lo, n, np.float32),
         t0_hi=_np(r.t0_hi, n, np.float32), mate=_np(r.mate, n, np.int32), collision=_np(r.collision, n, np.int32),
+        ctf=_np(r.ctf, int(r.ctf_bytes), np.uint8),
         status=int(r.status), user_tag=int(r.user_tag),
         stats={k: (list(getattr(r.stats, k)) if k == "ms_stage" else getattr(r.stats, k))
                for k, _ in o2tpc_stats._fields_},
@@ -416,7 +420,7 @@ class Tracker:
             raise O2TPCError(rc, "o2tpc_poll")
         r = res.contents
         n = int(r.n_tracks)
-        out = dict(status=int(r.status), n_tracks=n, n_cluster_refs=int(r.offsets[n]),
+        out = dict(status=int(r.status), n_tracks=n, n_cluster_refs=int(r.offsets[n]), ctf_bytes=int(r.ctf_bytes),
                    stats={k: (list(getattr(r.stats, k)) if k == "ms_stage" else getattr(r.stats, k))
                           for k, _ in o2tpc_stats._fields_})
         o2tpc_result_release(self.ctx, res)

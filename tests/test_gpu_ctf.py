@@ -1,0 +1,111 @@
+"""Compressed Time Frame of the CUDA path (Sec. 2.2: hit removal, track-model
+compression, ANS coding) through the C-ABI.
+
+* Byte-exact parity: where the CUDA path and the oracle find the same tracks
+  (identical cluster sets, so identical removal decisions and sequence), the
+  two blobs are the same bytes.
+* Lossless: the oracle's decoder turns the CUDA blob back into exactly the
+  clusters of the kept tracks (in track order, tracks by first input index)
+  followed by the clusters on no track in sorted order, with the integer
+  coordinates of the input.
+* Size: within 0.5 % of the oracle's blob where a few tracks differ.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from parity import track_sets
+from paper_2106_03636_gb300 import o2tpc, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(tf):
+    with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_COMPRESS) as t:
+        r = t.track(tf)
+    assert r["status"] == 0 and r["stats"]["captured"] == 0
+    return r
+
+
+def same_tracks(r, o):
+    g = set(track_sets(r["offsets"].astype(np.int64), r["cluster_idx"].astype(np.int64)))
+    k = set(track_sets(o["trk_off"], o["trk_cl"]))
+    return g == k
+
+
+def expected_sequence(r, o):
+    """Cluster sequence of the format from the CUDA tracks, the sorted order
+    and the ingested integer coordinates (both bit-exact with the oracle)."""
+    off, cl, q = r["offsets"].astype(np.int64), r["cluster_idx"].astype(np.int64), r["par"][:, 4]
+    on = np.zeros(len(o["yu"]), bool)
+    kept = []
+    for t in range(r["n_tracks"]):
+        on[cl[off[t]:off[t + 1]]] = True
+        if off[t + 1] > off[t] and -10.0 <= q[t] <= 10.0:
+            kept.append(t)
+    kept.sort(key=lambda t: cl[off[t]])
+    idx = [c for t in kept for c in cl[off[t]:off[t + 1]]]
+    idx += [h for h in o["sorted_orig"] if not on[h]]
+    return np.asarray(idx, np.int64), np.asarray([off[t + 1] - off[t] for t in kept])
+
+
+def check_lossless(r, o):
+    d = oracle.ctf_decode(r["ctf"])
+    idx, lens = expected_sequence(r, o)
+    assert np.array_equal(d["track_len"], lens)
+    assert np.array_equal(d["sector"], o["rid"][idx] // 152) and np.array_equal(d["row"], o["rid"][idx] % 152)
+    assert np.array_equal(d["y"], o["yu"][idx]) and np.array_equal(d["z"], o["zu"][idx])
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_ctf_byte_exact_on_identical_tracks(seed):
+    tf = synth.single_sector(seed=seed)
+    r = run_gpu(tf)
+    o = oracle.run(tf, compress=True)
+    assert same_tracks(r, o)
+    assert np.array_equal(r["ctf"], o["ctf"])
+    check_lossless(r, o)
+
+
+def test_ctf_dense_frames():
+    """Dense single-sector frames: byte-exact wherever the track sets agree
+    (most of them), lossless and the same size within 0.5 % everywhere."""
+    exact = 0
+    for seed in range(77, 83):
+        tf = synth.single_sector(seed=seed, ntracks=1500)
+        r = run_gpu(tf)
+        o = oracle.run(tf, compress=True)
+        check_lossless(r, o)
+        if same_tracks(r, o):
+            assert np.array_equal(r["ctf"], o["ctf"])
+            exact += 1
+        assert abs(len(r["ctf"]) - len(o["ctf"])) <= 0.005 * len(o["ctf"])
+    assert exact >= 1
+
+
+def test_ctf_full_tpc_frame_and_batches():
+    tfs = [synth.full_tpc_1ms(seed=33, n_coll=3), synth.single_sector(seed=34)]
+    with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_COMPRESS, max_batch=4) as t:
+        rs = [t.poll(k) for k in t.submit_many(tfs)]
+    assert rs[0]["stats"]["batch_size"] == 2
+    for tf, r in zip(tfs, rs):
+        o = oracle.run(tf, compress=True)
+        check_lossless(r, o)
+        assert abs(len(r["ctf"]) - len(o["ctf"])) <= 0.005 * len(o["ctf"])
+        if tf.n > 100000:  # below that the 5.2 kB of tables dominate
+            assert len(r["ctf"]) < 3.0 * tf.n
+    # the same TF alone gives the same blob
+    alone = run_gpu(tfs[1])
+    assert np.array_equal(alone["ctf"], rs[1]["ctf"])
+    # without the flag there is no blob
+    with o2tpc.Tracker() as t:
+        assert t.track(tfs[1])["ctf"].size == 0
+
+
+def test_ctf_empty_tf():
+    from helpers import float_tf
+    with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_COMPRESS) as t:
+        r = t.track(float_tf([], [], [], []))
+    assert r["status"] == 0
+    d = oracle.ctf_decode(r["ctf"])
+    assert len(d["sector"]) == 0 and len(d["track_len"]) == 0
