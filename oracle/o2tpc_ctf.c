@@ -31,7 +31,7 @@
  *  rANS      per stream a static table of 256 frequencies summing to 4096
  *            (counts scaled down with floor, at least 1 for a present
  *            symbol; the surplus or deficit goes to the largest entries,
- *            ties to the lower symbol); chunks of 16384 symbols, each coded
+ *            ties to the lower symbol); chunks of 4096 symbols, each coded
  *            independently (32-bit state in [2^23, 2^31), byte-wise
  *            renormalisation, symbols coded last to first; a chunk is its
  *            final state, 4 bytes little endian, followed by the emitted
@@ -52,7 +52,7 @@
 #define C_SCALE_BITS 12
 #define C_M (1u << C_SCALE_BITS)
 #define C_L (1u << 23)
-#define C_CHUNK 16384
+#define C_CHUNK 4096
 #define C_NSTREAM 10
 #define C_NROW 152
 

@@ -19,7 +19,7 @@
 //  * ten byte planes (sector, row, y lo/hi, zeta bytes 0-3, count lo/hi),
 //    each coded with a static 256-entry table summing to 4096 (floor-scaled
 //    counts, at least 1 for a present symbol, the difference to 4096 taken by
-//    the largest entries, lower symbol first) in independent chunks of 16384
+//    the largest entries, lower symbol first) in independent chunks of 4096
 //    symbols (32-bit state in [2^23, 2^31), byte renormalisation, symbols
 //    coded last to first; a chunk is its final state, 4 bytes little endian,
 //    then the emitted bytes in decoding order);
@@ -42,7 +42,7 @@ namespace {
 constexpr int kCtfScaleBits = 12;
 constexpr unsigned kCtfM = 1u << kCtfScaleBits;
 constexpr unsigned kCtfL = 1u << 23;
-constexpr int kCtfChunk = 16384;
+constexpr int kCtfChunk = 4096;
 constexpr int kCtfStreams = 10;
 constexpr float kCtfMaxQpt = 10.f;  // 1 / GeV
 
@@ -181,32 +181,73 @@ __global__ void k_ctf_streams(int nTF, const int* __restrict__ tfKt, const int* 
   *nChunks = chunk;
 }
 
-// Symbols of the kept tracks' clusters: one thread per track walks its chain.
-__global__ void k_ctf_emit_tracks(const int* __restrict__ nKeptDev, const int* __restrict__ canonTrk,
-                                  const int* __restrict__ lenScan, const int* __restrict__ tfKt,
-                                  const int* __restrict__ tfUn, OutBufs ob, const int* __restrict__ heads,
-                                  SectorTrackBufs sb, MergeBufs mb, long long nSeq, uint8_t* __restrict__ sym) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= *nKeptDev) return;
+// Symbols of the kept tracks' clusters: one warp per track walks its chain,
+// 32 consecutive clusters of a segment at a time (coalesced loads and byte
+// stores).  Within a sector segment the rows ascend, and neighbouring
+// segments of a chain lie in different sectors, so a cluster has the two
+// same-segment predecessors of the track model exactly when it is at least
+// the third of its segment.
+__global__ void __launch_bounds__(128) k_ctf_emit_tracks(const int* __restrict__ nKeptDev,
+                                                         const int* __restrict__ canonTrk,
+                                                         const int* __restrict__ lenScan,
+                                                         const int* __restrict__ tfKt, const int* __restrict__ tfUn,
+                                                         OutBufs ob, const int* __restrict__ heads, SectorTrackBufs sb,
+                                                         MergeBufs mb, long long nSeq, uint8_t* __restrict__ sym) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (k >= *nKeptDev) return;  // uniform over the warp
   const int t = canonTrk[k];
   const int tf = ob.endsR[t].y;
-  Clu prev{0, 0, 0, 0};
+  Clu prev{0, 0, 0, 0};  // previous cluster of the sequence
   if (k > tfKt[tf]) prev = track_last(canonTrk[k - 1], heads, sb, mb.next);
   long long pos = (long long)lenScan[k] + tfUn[tf];
-  Clu c0{}, c1{};
-  int q = 0;
   int c = heads[t];
   for (int j = 0; c >= 0 && j < kMaxChain; c = mb.next[c], ++j) {
     const int sec = sb.sector[c];
-    for (int i = sb.off[c]; i < sb.off[c + 1]; ++i, ++q, ++pos) {
-      const int2 p = sb.yz[i];
-      const Clu cu{sec, sb.rows[i], p.x, p.y};
-      const bool has2 = q >= 2 && c0.sec == sec && c1.sec == sec && c0.row < c1.row && c1.row < cu.row;
-      emit(sym, nSeq, pos, cu, prev, has2, c0, c1);
-      c0 = c1;
-      c1 = cu;
-      prev = cu;
+    const int a = sb.off[c], b = sb.off[c + 1];
+    Clu l1 = prev, l2 = prev;  // the two clusters before the current group
+    for (int g = a; g < b; g += 32) {
+      const int i = g + lane;
+      const bool valid = i < b;
+      const int2 p = valid ? sb.yz[i] : make_int2(0, 0);
+      const int rw = valid ? (int)sb.rows[i] : 0;
+      const Clu cu{sec, rw, p.x, p.y};
+      // cluster i - 1 and i - 2 of the sequence
+      Clu m1, m2;
+      m1.sec = sec;
+      m1.y = __shfl_up_sync(full, cu.y, 1);
+      m1.z = __shfl_up_sync(full, cu.z, 1);
+      m1.row = __shfl_up_sync(full, cu.row, 1);
+      m2.sec = sec;
+      m2.y = __shfl_up_sync(full, cu.y, 2);
+      m2.z = __shfl_up_sync(full, cu.z, 2);
+      m2.row = __shfl_up_sync(full, cu.row, 2);
+      if (lane == 0) {
+        m1 = l1;
+        m2 = l2;
+      } else if (lane == 1) {
+        m2 = l1;
+      }
+      const int qs = i - a;  // index inside the segment
+      if (valid) emit(sym, nSeq, pos + qs, cu, m1, qs >= 2, m2, m1);
+      // carry the last two clusters of the group
+      const int nv = min(32, b - g);
+      Clu n1, n2;
+      n1.sec = sec;
+      n1.y = __shfl_sync(full, cu.y, nv - 1);
+      n1.z = __shfl_sync(full, cu.z, nv - 1);
+      n1.row = __shfl_sync(full, cu.row, nv - 1);
+      n2.sec = sec;
+      n2.y = __shfl_sync(full, cu.y, max(nv - 2, 0));
+      n2.z = __shfl_sync(full, cu.z, max(nv - 2, 0));
+      n2.row = __shfl_sync(full, cu.row, max(nv - 2, 0));
+      if (nv < 2) n2 = l1;
+      l2 = n2;
+      l1 = n1;
     }
+    prev = l1;
+    pos += b - a;
   }
 }
 
@@ -266,7 +307,7 @@ __global__ void __launch_bounds__(256) k_ctf_hist(const int* __restrict__ nChunk
 
 // One thread per (TF, stream): the normalised table and its cumulative sums.
 __global__ void k_ctf_norm(int nSd, const unsigned* __restrict__ hist, uint16_t* __restrict__ freq,
-                           unsigned* __restrict__ cum) {
+                           unsigned* __restrict__ cum, int* __restrict__ degen) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nSd) return;
   const unsigned* c = hist + s * 256;
@@ -299,21 +340,26 @@ __global__ void k_ctf_norm(int nSd, const unsigned* __restrict__ hist, uint16_t*
     }
   }
   unsigned acc = 0;
+  int dg = 0;
   for (int k = 0; k < 256; ++k) {
     cum[s * 257 + k] = acc;
     acc += f[k];
+    dg |= f[k] == kCtfM;
   }
   cum[s * 257 + 256] = acc;
+  degen[s] = dg;
 }
 
 // One thread per chunk: rANS from the last symbol to the first; the emitted
-// bytes go backwards from the end of the chunk's scratch slot, the final state
-// in front of them.  bytes[c] = 4 + emitted.
+// bytes go backwards from the end of the chunk's scratch slot (gathered into
+// 32-bit words), the final state in front of them.  bytes[c] = 4 + emitted.
+// A table with one symbol of frequency 4096 codes nothing: the state stays
+// at its initial value.
 __global__ void __launch_bounds__(128) k_ctf_encode(const int* __restrict__ nChunksDev, const CtfStream* __restrict__ sd,
                                                     int nSd, const uint8_t* __restrict__ sym,
                                                     const uint16_t* __restrict__ freq,
-                                                    const unsigned* __restrict__ cum, uint8_t* __restrict__ scratch,
-                                                    int* __restrict__ bytes) {
+                                                    const unsigned* __restrict__ cum, const int* __restrict__ degen,
+                                                    uint8_t* __restrict__ scratch, int* __restrict__ bytes) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= *nChunksDev) return;
   int s;
@@ -329,21 +375,31 @@ __global__ void __launch_bounds__(128) k_ctf_encode(const int* __restrict__ nChu
   const CtfStream d = sd[s];
   const long long a = (long long)(c - d.chunk0) * kCtfChunk;
   const int n = (int)min((long long)kCtfChunk, d.count - a);
-  const uint8_t* p = sym + d.start + a;
-  const uint16_t* f = freq + s * 256;
-  const unsigned* cm = cum + s * 257;
   uint8_t* out = scratch + (size_t)c * kCtfChunkBytes;
-  int q = kCtfChunkBytes;  // emitted bytes fill [q, kCtfChunkBytes)
   unsigned x = kCtfL;
-  for (int i = n - 1; i >= 0; --i) {
-    const unsigned sy = p[i];
-    const unsigned fs = f[sy], cs = cm[sy];
-    const unsigned xmax = ((kCtfL >> kCtfScaleBits) << 8) * fs;
-    while (x >= xmax) {
-      out[--q] = (uint8_t)(x & 0xff);
-      x >>= 8;
+  int q = kCtfChunkBytes;  // emitted bytes fill [q, kCtfChunkBytes)
+  if (!degen[s]) {
+    const uint8_t* p = sym + d.start + a;
+    const uint16_t* f = freq + s * 256;
+    const unsigned* cm = cum + s * 257;
+    unsigned w = 0;  // bytes not yet stored, the latest emitted in the low byte
+    int nw = 0;
+    for (int i = n - 1; i >= 0; --i) {
+      const unsigned sy = p[i];
+      const unsigned fs = f[sy], cs = cm[sy];
+      const unsigned xmax = ((kCtfL >> kCtfScaleBits) << 8) * fs;
+      while (x >= xmax) {
+        w = (w << 8) | (x & 0xffu);
+        x >>= 8;
+        if (++nw == 4) {
+          q -= 4;
+          *reinterpret_cast<unsigned*>(out + q) = w;
+          nw = 0;
+        }
+      }
+      x = ((x / fs) << kCtfScaleBits) + (x % fs) + cs;
     }
-    x = ((x / fs) << kCtfScaleBits) + (x % fs) + cs;
+    for (int k = 0; k < nw; ++k) out[--q] = (uint8_t)(w >> (8 * (nw - 1 - k)));
   }
   out[q - 4] = (uint8_t)x;
   out[q - 3] = (uint8_t)(x >> 8);
@@ -475,8 +531,8 @@ void launch_ctf_symbols(int n, const int* nDev, int nTrk, const int* nTrkDev, in
                                  cb.tfCounts);
   ++g_launch_count;
   if (nTrk > 0) {
-    k_ctf_emit_tracks<<<(nTrk + 127) / 128, 128, 0, st>>>(cb.counts, cb.canonTrk, cb.lenScan, cb.tfKt, cb.tfUn, ob,
-                                                            heads, sb, mb, cb.nSeqCap, cb.sym);
+    k_ctf_emit_tracks<<<(int)(((long long)nTrk * 32 + 127) / 128), 128, 0, st>>>(
+        cb.counts, cb.canonTrk, cb.lenScan, cb.tfKt, cb.tfUn, ob, heads, sb, mb, cb.nSeqCap, cb.sym);
     k_ctf_emit_len<<<(nTrk + 255) / 256, 256, 0, st>>>(cb.counts, cb.len, cb.nSeqCap, cb.nTrkCap, cb.sym);
     g_launch_count += 2;
   }
@@ -488,9 +544,9 @@ void launch_ctf_symbols(int n, const int* nDev, int nTrk, const int* nTrkDev, in
   const int nSd = nTF * kCtfStreams;
   cudaMemsetAsync(cb.hist, 0, sizeof(unsigned) * 256 * nSd, st);
   k_ctf_hist<<<cb.chunkCap, 256, 0, st>>>(cb.counts + 2, cb.sd, nSd, cb.sym, cb.hist);
-  k_ctf_norm<<<(nSd + 63) / 64, 64, 0, st>>>(nSd, cb.hist, cb.freq, cb.cum);
+  k_ctf_norm<<<(nSd + 63) / 64, 64, 0, st>>>(nSd, cb.hist, cb.freq, cb.cum, cb.degen);
   k_ctf_encode<<<(cb.chunkCap + 127) / 128, 128, 0, st>>>(cb.counts + 2, cb.sd, nSd, cb.sym, cb.freq, cb.cum,
-                                                          cb.scratch, cb.bytes);
+                                                          cb.degen, cb.scratch, cb.bytes);
   g_launch_count += 3;
   scan_exclusive(cb.bytes, cb.payOff, cb.chunkCap, cb.counts + 2, scratch, st);
   k_ctf_layout<<<1, 1, 0, st>>>(nTF, cb.sd, cb.payOff, cb.tfBlob, cb.tfHead);

@@ -878,6 +878,7 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
     cb.hist = dalloc<unsigned>(M, 2560 * (size_t)B);
     cb.freq = dalloc<uint16_t>(M, 2560 * (size_t)B);
     cb.cum = dalloc<unsigned>(M, 2570 * (size_t)B);
+    cb.degen = dalloc<int>(M, 10 * (size_t)B);
     cb.scratch = dalloc<uint8_t>(M, (size_t)cb.chunkCap * kCtfChunkBytes);
     cb.bytes = dalloc<int>(M, (size_t)cb.chunkCap + 1);
     cb.payOff = dalloc<int>(M, (size_t)cb.chunkCap + 1);

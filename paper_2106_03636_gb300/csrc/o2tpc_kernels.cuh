@@ -188,7 +188,7 @@ struct CtfStream {
   long long start, count;
   int chunk0, nChunks;
 };
-constexpr int kCtfChunkBytes = 24640;  // >= 4 + 1.5 * 16384: a coded chunk at most
+constexpr int kCtfChunkBytes = 6160;  // >= 4 + 1.5 * 4096 + 4: a coded chunk at most (multiple of 16)
 struct CtfBufs {
   uint8_t* onTrack;    // [n + 1] input cluster on a track
   int* firstFlag;      // [n + 1] input index of a kept track's first cluster
@@ -211,6 +211,7 @@ struct CtfBufs {
   unsigned* hist;      // [nTF * 10 * 256]
   uint16_t* freq;      // [nTF * 10 * 256]
   unsigned* cum;       // [nTF * 10 * 257]
+  int* degen;          // [nTF * 10] 1: one symbol holds the whole table (nothing to code)
   uint8_t* scratch;    // [chunkCap * kCtfChunkBytes]
   int* bytes;          // [chunkCap + 1] coded chunk sizes
   int* payOff;         // [chunkCap + 1]
