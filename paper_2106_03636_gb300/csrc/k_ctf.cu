@@ -278,36 +278,66 @@ __global__ void k_ctf_emit_len(const int* __restrict__ nKeptDev, const int* __re
   sym[8 * nSeqCap + nTrkCap + k] = (uint8_t)(len[k] >> 8);
 }
 
+// Stream of chunk c (the first stream whose chunk range ends after c).
+__device__ inline int stream_of_chunk(const CtfStream* __restrict__ sd, int nSd, int c) {
+  int lo = 0, hi = nSd;
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (sd[m].chunk0 + sd[m].nChunks <= c) lo = m + 1;
+    else hi = m;
+  }
+  return lo;
+}
+
+// One block per kCtfHistChunks consecutive chunks (mostly one stream): a
+// shared-memory histogram, flushed to the stream's global one whenever the
+// stream changes.
+constexpr int kCtfHistChunks = 32;
 __global__ void __launch_bounds__(256) k_ctf_hist(const int* __restrict__ nChunksDev, const CtfStream* __restrict__ sd,
                                                   int nSd, const uint8_t* __restrict__ sym,
                                                   unsigned* __restrict__ hist) {
   __shared__ unsigned h[256];
-  const int c = blockIdx.x;
-  if (c >= *nChunksDev) return;
+  const int nCh = *nChunksDev;
+  const int c0 = blockIdx.x * kCtfHistChunks;
+  if (c0 >= nCh) return;
+  const int c1 = min(nCh, c0 + kCtfHistChunks);
+  int s = stream_of_chunk(sd, nSd, c0);
   h[threadIdx.x] = 0;
   __syncthreads();
-  int s = 0;
-  {
-    int lo = 0, hi = nSd;
-    while (lo < hi) {
-      const int m = (lo + hi) >> 1;
-      if (sd[m].chunk0 + sd[m].nChunks <= c) lo = m + 1;
-      else hi = m;
+  for (int c = c0; c < c1;) {
+    while (sd[s].chunk0 + sd[s].nChunks <= c) ++s;
+    const CtfStream d = sd[s];
+    const int ce = min(c1, d.chunk0 + d.nChunks);  // this stream's part of the range
+    const long long a = (long long)(c - d.chunk0) * kCtfChunk;
+    const long long e = min(d.count, (long long)(ce - d.chunk0) * kCtfChunk);
+    const uint8_t* p = sym + d.start;
+    // runs of equal symbols seen by a thread are added at once (most byte
+    // planes are dominated by one symbol)
+    unsigned cur = 256u, run = 0;
+    for (long long i = a + threadIdx.x; i < e; i += blockDim.x) {
+      const unsigned v = p[i];
+      if (v == cur) {
+        ++run;
+      } else {
+        if (run) atomicAdd(&h[cur], run);
+        cur = v;
+        run = 1;
+      }
     }
-    s = lo;
+    if (run) atomicAdd(&h[cur], run);
+    __syncthreads();
+    if (h[threadIdx.x]) {
+      atomicAdd(&hist[s * 256 + threadIdx.x], h[threadIdx.x]);
+      h[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    c = ce;
   }
-  const CtfStream d = sd[s];
-  const long long a = (long long)(c - d.chunk0) * kCtfChunk;
-  const long long n = min((long long)kCtfChunk, d.count - a);
-  const uint8_t* p = sym + d.start + a;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&h[p[i]], 1u);
-  __syncthreads();
-  if (h[threadIdx.x]) atomicAdd(&hist[s * 256 + threadIdx.x], h[threadIdx.x]);
 }
 
 // One thread per (TF, stream): the normalised table and its cumulative sums.
 __global__ void k_ctf_norm(int nSd, const unsigned* __restrict__ hist, uint16_t* __restrict__ freq,
-                           unsigned* __restrict__ cum, int* __restrict__ degen) {
+                           uint2* __restrict__ enc, int* __restrict__ degen) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nSd) return;
   const unsigned* c = hist + s * 256;
@@ -339,14 +369,14 @@ __global__ void k_ctf_norm(int nSd, const unsigned* __restrict__ hist, uint16_t*
       dlt += take;
     }
   }
+  // coding entries: cumulative start | frequency << 16, and 1 / frequency
   unsigned acc = 0;
   int dg = 0;
   for (int k = 0; k < 256; ++k) {
-    cum[s * 257 + k] = acc;
+    enc[s * 256 + k] = make_uint2(acc | ((unsigned)f[k] << 16), __float_as_uint(f[k] ? 1.0f / (float)f[k] : 0.f));
     acc += f[k];
     dg |= f[k] == kCtfM;
   }
-  cum[s * 257 + 256] = acc;
   degen[s] = dg;
 }
 
@@ -357,21 +387,11 @@ __global__ void k_ctf_norm(int nSd, const unsigned* __restrict__ hist, uint16_t*
 // at its initial value.
 __global__ void __launch_bounds__(128) k_ctf_encode(const int* __restrict__ nChunksDev, const CtfStream* __restrict__ sd,
                                                     int nSd, const uint8_t* __restrict__ sym,
-                                                    const uint16_t* __restrict__ freq,
-                                                    const unsigned* __restrict__ cum, const int* __restrict__ degen,
+                                                    const uint2* __restrict__ enc, const int* __restrict__ degen,
                                                     uint8_t* __restrict__ scratch, int* __restrict__ bytes) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= *nChunksDev) return;
-  int s;
-  {
-    int lo = 0, hi = nSd;
-    while (lo < hi) {
-      const int m = (lo + hi) >> 1;
-      if (sd[m].chunk0 + sd[m].nChunks <= c) lo = m + 1;
-      else hi = m;
-    }
-    s = lo;
-  }
+  const int s = stream_of_chunk(sd, nSd, c);
   const CtfStream d = sd[s];
   const long long a = (long long)(c - d.chunk0) * kCtfChunk;
   const int n = (int)min((long long)kCtfChunk, d.count - a);
@@ -380,13 +400,12 @@ __global__ void __launch_bounds__(128) k_ctf_encode(const int* __restrict__ nChu
   int q = kCtfChunkBytes;  // emitted bytes fill [q, kCtfChunkBytes)
   if (!degen[s]) {
     const uint8_t* p = sym + d.start + a;
-    const uint16_t* f = freq + s * 256;
-    const unsigned* cm = cum + s * 257;
+    const uint2* tab = enc + s * 256;
     unsigned w = 0;  // bytes not yet stored, the latest emitted in the low byte
     int nw = 0;
     for (int i = n - 1; i >= 0; --i) {
-      const unsigned sy = p[i];
-      const unsigned fs = f[sy], cs = cm[sy];
+      const uint2 e = tab[p[i]];
+      const unsigned fs = e.x >> 16, cs = e.x & 0xffffu;
       const unsigned xmax = ((kCtfL >> kCtfScaleBits) << 8) * fs;
       while (x >= xmax) {
         w = (w << 8) | (x & 0xffu);
@@ -397,7 +416,19 @@ __global__ void __launch_bounds__(128) k_ctf_encode(const int* __restrict__ nChu
           nw = 0;
         }
       }
-      x = ((x / fs) << kCtfScaleBits) + (x % fs) + cs;
+      // x / fs: here x < 2^19 fs, so the quotient is below 2^19 and the
+      // single-precision estimate (relative error < 2^-22) is off by at most
+      // one, which one remainder test corrects
+      unsigned qt = __float2uint_rz(__uint2float_rn(x) * __uint_as_float(e.y));
+      int r = (int)(x - qt * fs);
+      if (r < 0) {
+        --qt;
+        r += (int)fs;
+      } else if (r >= (int)fs) {
+        ++qt;
+        r -= (int)fs;
+      }
+      x = (qt << kCtfScaleBits) + (unsigned)r + cs;
     }
     for (int k = 0; k < nw; ++k) out[--q] = (uint8_t)(w >> (8 * (nw - 1 - k)));
   }
@@ -463,12 +494,12 @@ __global__ void k_ctf_header(int nTF, const CtfStream* __restrict__ sd, const in
       h[8 + 2 * k] = (uint8_t)v;
       h[9 + 2 * k] = (uint8_t)(v >> 8);
     }
-    for (int k = threadIdx.x; k < d.nChunks; k += blockDim.x) put32(h + 520 + 4 * k, (unsigned)bytes[d.chunk0 + k]);
-    o += 8 + 512 + 4ll * d.nChunks;
+    o += 8 + 512 + 4ll * d.nChunks;  // the chunk sizes are written by k_ctf_copy
   }
 }
 
-// One block per chunk: its payload from the scratch slot into the blob.
+// One block per chunk: its size into the stream's header, its payload from
+// the scratch slot into the blob.
 __global__ void k_ctf_copy(const int* __restrict__ nChunksDev, int nTF, const CtfStream* __restrict__ sd,
                            const int* __restrict__ bytes, const int* __restrict__ payOff,
                            const long long* __restrict__ tfBlob, const long long* __restrict__ tfHead,
@@ -489,6 +520,12 @@ __global__ void k_ctf_copy(const int* __restrict__ nChunksDev, int nTF, const Ct
   const int first = sd[tf * kCtfStreams].chunk0;
   uint8_t* dst = blob + tfBlob[tf] + tfHead[tf] + (payOff[c] - payOff[first]);
   const int nb = bytes[c];
+  if (threadIdx.x == 0) {
+    const int s = stream_of_chunk(sd, nTF * kCtfStreams, c);
+    long long h = 24;
+    for (int k = tf * kCtfStreams; k < s; ++k) h += 8 + 512 + 4ll * sd[k].nChunks;
+    put32(blob + tfBlob[tf] + h + 520 + 4ll * (c - sd[s].chunk0), (unsigned)nb);
+  }
   const uint8_t* src = scratch + (size_t)c * kCtfChunkBytes + (kCtfChunkBytes - nb);
   for (int i = threadIdx.x; i < nb; i += blockDim.x) dst[i] = src[i];
 }
@@ -543,10 +580,11 @@ void launch_ctf_symbols(int n, const int* nDev, int nTrk, const int* nTrkDev, in
   }
   const int nSd = nTF * kCtfStreams;
   cudaMemsetAsync(cb.hist, 0, sizeof(unsigned) * 256 * nSd, st);
-  k_ctf_hist<<<cb.chunkCap, 256, 0, st>>>(cb.counts + 2, cb.sd, nSd, cb.sym, cb.hist);
-  k_ctf_norm<<<(nSd + 63) / 64, 64, 0, st>>>(nSd, cb.hist, cb.freq, cb.cum, cb.degen);
-  k_ctf_encode<<<(cb.chunkCap + 127) / 128, 128, 0, st>>>(cb.counts + 2, cb.sd, nSd, cb.sym, cb.freq, cb.cum,
-                                                          cb.degen, cb.scratch, cb.bytes);
+  k_ctf_hist<<<(cb.chunkCap + kCtfHistChunks - 1) / kCtfHistChunks, 256, 0, st>>>(cb.counts + 2, cb.sd, nSd, cb.sym,
+                                                                                  cb.hist);
+  k_ctf_norm<<<(nSd + 63) / 64, 64, 0, st>>>(nSd, cb.hist, cb.freq, cb.enc, cb.degen);
+  k_ctf_encode<<<(cb.chunkCap + 127) / 128, 128, 0, st>>>(cb.counts + 2, cb.sd, nSd, cb.sym, cb.enc, cb.degen,
+                                                          cb.scratch, cb.bytes);
   g_launch_count += 3;
   scan_exclusive(cb.bytes, cb.payOff, cb.chunkCap, cb.counts + 2, scratch, st);
   k_ctf_layout<<<1, 1, 0, st>>>(nTF, cb.sd, cb.payOff, cb.tfBlob, cb.tfHead);

@@ -877,7 +877,7 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
     cb.sym = dalloc<uint8_t>(M, 8 * (size_t)n + 2 * (size_t)nHeads + 16);
     cb.hist = dalloc<unsigned>(M, 2560 * (size_t)B);
     cb.freq = dalloc<uint16_t>(M, 2560 * (size_t)B);
-    cb.cum = dalloc<unsigned>(M, 2570 * (size_t)B);
+    cb.enc = dalloc<uint2>(M, 2560 * (size_t)B);
     cb.degen = dalloc<int>(M, 10 * (size_t)B);
     cb.scratch = dalloc<uint8_t>(M, (size_t)cb.chunkCap * kCtfChunkBytes);
     cb.bytes = dalloc<int>(M, (size_t)cb.chunkCap + 1);

@@ -210,7 +210,7 @@ struct CtfBufs {
   int chunkCap;
   unsigned* hist;      // [nTF * 10 * 256]
   uint16_t* freq;      // [nTF * 10 * 256]
-  unsigned* cum;       // [nTF * 10 * 257]
+  uint2* enc;          // [nTF * 10 * 256] coding entries (start | freq << 16, 1 / freq)
   int* degen;          // [nTF * 10] 1: one symbol holds the whole table (nothing to code)
   uint8_t* scratch;    // [chunkCap * kCtfChunkBytes]
   int* bytes;          // [chunkCap + 1] coded chunk sizes
