@@ -16,15 +16,16 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "o2tpc_oracle.c")
 CTF_SRC = os.path.join(HERE, "o2tpc_ctf.c")
+CLU_SRC = os.path.join(HERE, "o2tpc_clu.c")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
     os.makedirs(LIBDIR, exist_ok=True)
-    deps = [SRC, CTF_SRC, os.path.join(HERE, "o2tpc_oracle.h")]
+    deps = [SRC, CTF_SRC, CLU_SRC, os.path.join(HERE, "o2tpc_oracle.h")]
     if force or not os.path.exists(SO) or any(os.path.getmtime(d) > os.path.getmtime(SO) for d in deps):
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", SO + ".tmp", SRC, CTF_SRC, "-lm"]
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", SO + ".tmp", SRC, CTF_SRC, CLU_SRC, "-lm"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("oracle build failed:\n" + r.stdout + r.stderr)
@@ -90,6 +91,8 @@ def _load():
         lib.oracle_rans_decode.argtypes = [u8p, ctypes.c_int64, ctypes.POINTER(u8p)]
         lib.oracle_buffer_free.restype = None
         lib.oracle_buffer_free.argtypes = [ctypes.c_void_p]
+        lib.oracle_clusterize.restype = ctypes.c_int64
+        lib.oracle_clusterize.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.POINTER(u8p)]
         lib.oracle_dca_arc.restype = ctypes.c_double
         lib.oracle_dca_arc.argtypes = [ctypes.c_double] * 4
         lib.oracle_fit_points.restype = ctypes.c_int32
@@ -300,3 +303,17 @@ def ctf_decode(blob) -> dict:
     out = {k: _take(lib, p, n, np.int32) for k, p in zip(("sector", "row", "y", "z"), ptrs)}
     out["track_len"] = _take(lib, lens, nt.value, np.int64)
     return out
+
+
+def clusterize(digits) -> np.ndarray:
+    """12-byte cluster records (uint8 [n, 12]) of sorted raw digits (an object
+    with sector, row, pad, time, adc arrays)."""
+    lib = _load()
+    arrs = [np.ascontiguousarray(np.asarray(getattr(digits, k), dtype=t)) for k, t in
+            (("sector", np.uint8), ("row", np.uint8), ("pad", np.uint8), ("time", np.uint32), ("adc", np.uint16))]
+    out = ctypes.POINTER(ctypes.c_uint8)()
+    n = lib.oracle_clusterize(len(arrs[0]), *[a.ctypes.data for a in arrs], ctypes.byref(out))
+    if n < 0:
+        lib.oracle_buffer_free(ctypes.cast(out, ctypes.c_void_p))
+        raise OracleError("digits not sorted or out of range")
+    return _take(lib, out, 12 * n, np.uint8).reshape(-1, 12)

@@ -64,6 +64,11 @@ void oracle_ctf_normalize(const uint64_t* count, uint16_t* freq);
 int64_t oracle_rans_encode(const uint8_t* sym, int64_t n, uint8_t** out);
 int64_t oracle_rans_decode(const uint8_t* blob, int64_t bytes, uint8_t** out);
 void oracle_buffer_free(void* p);
+/* Clusterizer (o2tpc_clu.c): digits sorted by (sector, row, time, pad) to
+ * 12-byte cluster records; returns the cluster count, -1 on an unsorted or
+ * out-of-range input. */
+int64_t oracle_clusterize(int64_t n, const uint8_t* sector, const uint8_t* row, const uint8_t* pad,
+                          const uint32_t* time, const uint16_t* adc, uint8_t** out);
 
 /* Signed transverse arc length from (x0, y0) with sin(phi) = snp and
  * curvature k = dphi/ds to the closest approach to the origin. */

@@ -70,9 +70,10 @@ def _stale(target: str, sources: list[str]) -> bool:
 def build_gen(force: bool = False) -> str:
     os.makedirs(LIB, exist_ok=True)
     src = os.path.join(PKG, "synth", "o2gen.c")
-    if force or _stale(GEN_SO, [src]):
+    dig = os.path.join(PKG, "synth", "o2digits.c")
+    if force or _stale(GEN_SO, [src, dig]):
         _run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
-              "-o", GEN_SO + ".tmp", src, "-lm"])
+              "-o", GEN_SO + ".tmp", src, dig, "-lm"])
         os.replace(GEN_SO + ".tmp", GEN_SO)
     return GEN_SO
 

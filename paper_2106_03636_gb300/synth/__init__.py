@@ -86,6 +86,12 @@ def _load():
         lib.o2gen_truth.argtypes = [ctypes.c_void_p] * 4
         lib.o2gen_free.restype = None
         lib.o2gen_free.argtypes = [ctypes.c_void_p]
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        lib.o2dig_run.restype = ctypes.c_int64
+        lib.o2dig_run.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_int32] + [pp] * 5
+        lib.o2dig_free.restype = None
+        lib.o2dig_free.argtypes = [ctypes.c_void_p]
         _lib = lib
     return _lib
 
@@ -279,3 +285,38 @@ def float_time_from_fixed(tf: TimeFrame) -> TimeFrame:
     return TimeFrame(n=tf.n, fmt=FMT_FLOAT, sector=sector, row=row, y=(yu / 160.0).astype(np.float32),
                      time=(t64.astype(np.float64) / 320.0).astype(np.float32), bz=tf.bz, vdrift=tf.vdrift,
                      name=tf.name + "_time", coll_time=tf.coll_time)
+
+
+@dataclass
+class Digits:
+    """Zero-suppressed raw ADC digits, sorted by (sector, row, time, pad)."""
+    n: int
+    sector: np.ndarray
+    row: np.ndarray
+    pad: np.ndarray
+    time: np.ndarray
+    adc: np.ndarray
+    name: str = ""
+
+
+def digits_from(tf: TimeFrame, seed: int = 1, sigma_pad: float = 0.7, sigma_time: float = 0.8,
+                noise: float = 0.6, threshold: int = 2) -> Digits:
+    """Raw ADC digits of a fixed-format TF's clusters (see o2digits.c):
+    Gaussian charge spread over 5 x 5 pad x time cells, summed, noise added,
+    rounded, zero-suppressed below ``threshold``."""
+    assert tf.fmt == FMT_FIXED
+    lib = _load()
+    ptrs = [ctypes.c_void_p() for _ in range(5)]
+    rec = np.ascontiguousarray(tf.packed)
+    nd = lib.o2dig_run(tf.n, rec.ctypes.data, seed, sigma_pad, sigma_time, noise, threshold,
+                       *[ctypes.byref(p) for p in ptrs])
+    out = []
+    for p, dt in zip(ptrs, (np.uint8, np.uint8, np.uint8, np.uint32, np.uint16)):
+        if nd > 0:
+            buf = (ctypes.c_char * (nd * np.dtype(dt).itemsize)).from_address(p.value)
+            out.append(np.frombuffer(buf, dtype=dt).copy())
+        else:
+            out.append(np.zeros(0, dt))
+        lib.o2dig_free(p)
+    return Digits(n=int(nd), sector=out[0], row=out[1], pad=out[2], time=out[3], adc=out[4],
+                  name=tf.name + "_digits")
