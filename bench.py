@@ -159,6 +159,65 @@ def make_workload(name: str, seed: int):
     raise SystemExit(f"unknown workload {name}")
 
 
+def run_raw(args, rank, world, local):
+    """Clusterizer on raw ADC digits: the digits of a 20-collision 1 ms frame
+    (fixed point) resident on the device; one step = o2tpc_clusterize over
+    all of them.  value = digits per second; the records are then tracked
+    once to show the chain (not timed)."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2106_03636_gb300 import o2tpc, synth
+
+    tf = synth.full_tpc_1ms(seed=replica_seed(args.seed, rank), n_coll=20, fmt=synth.FMT_FIXED)
+    d = synth.digits_from(tf, seed=11)
+    arr = {k: torch.from_numpy(np.ascontiguousarray(getattr(d, k))).to(f"cuda:{local}")
+           for k in ("sector", "row", "pad", "time", "adc")}
+    st = torch.cuda.Stream()
+    out = torch.empty((d.n, 12), dtype=torch.uint8, device=f"cuda:{local}")
+    dg = o2tpc.o2tpc_digits(n=d.n, sector=arr["sector"].data_ptr(), row=arr["row"].data_ptr(),
+                            pad=arr["pad"].data_ptr(), time=arr["time"].data_ptr(), adc=arr["adc"].data_ptr())
+    for _ in range(args.warmup):
+        rc, nc = o2tpc.o2tpc_clusterize(dg, out.data_ptr(), d.n, st.cuda_stream)
+        assert rc == 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(st)
+        for _ in range(args.steps):
+            rc, nc = o2tpc.o2tpc_clusterize(dg, out.data_ptr(), d.n, st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+    ms = device_max(e0.elapsed_time(e1), world, local) / args.steps
+    peak, peak_kind = peaks()
+    # algorithmic bytes: read the 9-byte digit once, write a 12-byte record per cluster
+    alg = 9.0 * d.n + 12.0 * nc
+    with o2tpc.Tracker(device=local) as trk:
+        tf2 = synth.TimeFrame(n=nc, fmt=synth.FMT_FIXED, sector=np.zeros(nc, np.uint8), row=np.zeros(nc, np.uint8),
+                              packed=np.zeros((1, 12), np.uint8), bz=tf.bz, vdrift=tf.vdrift)
+        res = trk.wait(trk.submit(tf2, location=o2tpc.O2TPC_LOC_DEVICE, arrays={"packed": out[:nc]}))
+    line = {"metric": "TPC raw digits/s through the clusterizer on 1 GB300", "value": world * d.n / (ms / 1e3),
+            "unit": "digits/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "raw_digits_1ms_20coll", "digits": int(d.n), "clusters_in": int(tf.n),
+                       "clusters_out": int(nc), "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas x{world}"},
+            "clusters_per_s": world * nc / (ms / 1e3),
+            "roofline": {"bound": "hbm", "kernel": "o2tpc_clusterize (k_clu_keys + k_clu_flags + compaction + "
+                                                    "k_clu_records)",
+                         "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                         "bytes_per_digit": alg / d.n},
+            "tracked_after": {"status": res["status"], "tracks": res["n_tracks"]},
+            "clocks": clk.summary(), "gpu_launches": 9 * args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def cpu_baseline(tf, sector: int = 0):
     """The oracle as it stands on one sector of the workload."""
     from types import SimpleNamespace
@@ -534,7 +593,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="full_tf", choices=["full_tf", "full_tpc_1ms", "chunks", "serving"])
+    ap.add_argument("--workload", default="full_tf", choices=["full_tf", "full_tpc_1ms", "chunks", "serving", "raw"])
     ap.add_argument("--rate-hz", type=float, default=50.0, help="serving: Poisson arrival rate of TFs")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: arrival window")
     ap.add_argument("--max-queue", type=int, default=16, help="serving: TFs admitted at once (more are dropped)")
@@ -572,6 +631,8 @@ def main():
         return run_chunks(args, rank, world, local)
     if args.workload == "serving":
         return run_serving(args, rank, world, local)
+    if args.workload == "raw":
+        return run_raw(args, rank, world, local)
 
     tf, cfg = make_workload(args.workload, replica_seed(args.seed, rank))
     n = tf.n

@@ -263,6 +263,35 @@ typedef struct {
   int32_t status;              /* O2TPC_OK or the error of this TF                    */
 } o2tpc_result;
 
+/* Raw ADC digits for the clusterizer (Sec. 2.2: raw ADC values are turned
+ * into hits before tracking).  DEVICE arrays of n entries, zero-suppressed,
+ * sorted strictly ascending by (sector, row, time, pad); sector < 36,
+ * row < 152, time < 2^24 (200 ns bins). */
+typedef struct {
+  uint64_t n;
+  const uint8_t* sector;
+  const uint8_t* row;
+  const uint8_t* pad;      /* pad in its row, 0 at the pad-plane edge          */
+  const uint32_t* time;    /* time bin                                          */
+  const uint16_t* adc;     /* ADC counts                                        */
+} o2tpc_digits;
+
+/* Clusterizer: one 12-byte cluster record (the O2TPC_FMT_FIXED layout: u32
+ * time64, u16 pad64, u16 charge, u8 row, u8 sector, u16 0) per charge peak,
+ * in the order of the peaks, written to the DEVICE buffer records (4-byte
+ * aligned, room for cap records; its output can be submitted as a TF).  A
+ * peak is a digit with ADC >= 3 larger than each of its up to eight pad/time
+ * neighbours of the same row that come before it in the sorted order and not
+ * smaller than each that comes after it; its record carries the charge sum
+ * and the centre of gravity of the 3 x 3 cells around it, rounded half up in
+ * 1/64 pad and 1/64 time bin.  Runs on `stream` (a cudaStream_t, NULL for the
+ * default stream) with scratch from the stream-ordered allocator and returns
+ * when the records are written.  *n_clusters: the number of peaks (also when
+ * it exceeds cap).  Returns O2TPC_OK, O2TPC_EINVAL (null pointers, misaligned
+ * records, unsorted or out-of-range digits), O2TPC_ETOOBIG (n >= 2^31, or more
+ * peaks than cap: nothing written), O2TPC_ENOMEM, O2TPC_ECUDA. */
+int o2tpc_clusterize(const o2tpc_digits* digits, void* records, uint64_t cap, uint64_t* n_clusters, void* stream);
+
 /* Creates a context on cfg->device (cfg may be NULL: all defaults).
  * *out is set on success.  Returns O2TPC_EINVAL, O2TPC_ECUDA or O2TPC_ENOMEM. */
 int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out);

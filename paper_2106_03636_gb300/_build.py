@@ -31,6 +31,7 @@ CUDA_SOURCES = [
     "k_merge.cu",
     "k_cont.cu",
     "k_ctf.cu",
+    "k_clu.cu",
     "o2tpc_static.cu",
     "o2tpc_graph.cu",
 ]

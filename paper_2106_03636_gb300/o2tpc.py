@@ -144,6 +144,17 @@ class o2tpc_result(ctypes.Structure):
     ]
 
 
+class o2tpc_digits(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("sector", ctypes.c_void_p),
+        ("row", ctypes.c_void_p),
+        ("pad", ctypes.c_void_p),
+        ("time", ctypes.c_void_p),
+        ("adc", ctypes.c_void_p),
+    ]
+
+
 class O2TPCError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -182,6 +193,9 @@ def load(build: bool = True) -> ctypes.CDLL:
                                              ctypes.c_uint64, vp]
         lib.o2tpc_get_tuning.restype = ctypes.c_int
         lib.o2tpc_get_tuning.argtypes = [vp, ctypes.POINTER(o2tpc_tuning)]
+        lib.o2tpc_clusterize.restype = ctypes.c_int
+        lib.o2tpc_clusterize.argtypes = [ctypes.POINTER(o2tpc_digits), vp, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_uint64), vp]
         lib.o2tpc_get_stage.restype = ctypes.c_int
         lib.o2tpc_get_stage.argtypes = [vp, ctypes.c_uint64, ctypes.c_char_p, vp, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_uint64)]
@@ -248,6 +262,28 @@ def o2tpc_sort_tf_static(tf: o2tpc_tf, vdrift: float, sorted_orig, sorted_yz, ro
     buffer the caller owns; nothing is allocated by the call."""
     return load().o2tpc_sort_tf_static(ctypes.byref(tf), vdrift, sorted_orig, sorted_yz, row_grid, cell_start,
                                        cell_capacity, stream)
+
+
+def o2tpc_clusterize(digits: o2tpc_digits, records, cap: int, stream):
+    n = ctypes.c_uint64()
+    rc = load().o2tpc_clusterize(ctypes.byref(digits), records, cap, ctypes.byref(n), stream)
+    return rc, n.value
+
+
+def clusterize(arrays: dict, stream=None, cap: int | None = None):
+    """Clusterizer over device tensors ``sector, row, pad, time, adc``
+    (sorted digits); returns (status, records as a uint8 [n, 12] device
+    tensor).  ``stream``: a torch.cuda.Stream (default: the current one)."""
+    import torch
+
+    n = int(arrays["adc"].numel())
+    cap = n if cap is None else cap
+    out = torch.empty((max(cap, 1), 12), dtype=torch.uint8, device=arrays["adc"].device)
+    d = o2tpc_digits(n=n, sector=_ptr(arrays["sector"]), row=_ptr(arrays["row"]), pad=_ptr(arrays["pad"]),
+                     time=_ptr(arrays["time"]), adc=_ptr(arrays["adc"]))
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc, nc = o2tpc_clusterize(d, out.data_ptr(), cap, st.cuda_stream)
+    return rc, (out[:nc] if rc == O2TPC_OK else out[:0]), nc
 
 
 # ---------------------------------------------------------- helpers

@@ -51,7 +51,8 @@ def test_binding_layout_matches_the_compiled_header(tmp_path):
     import subprocess
 
     structs = {"o2tpc_tf": o2tpc.o2tpc_tf, "o2tpc_stats": o2tpc.o2tpc_stats, "o2tpc_result": o2tpc.o2tpc_result,
-               "o2tpc_config": o2tpc.o2tpc_config, "o2tpc_tuning": o2tpc.o2tpc_tuning}
+               "o2tpc_config": o2tpc.o2tpc_config, "o2tpc_tuning": o2tpc.o2tpc_tuning,
+               "o2tpc_digits": o2tpc.o2tpc_digits}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "o2tpc.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
