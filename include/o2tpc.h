@@ -97,7 +97,8 @@ enum {
                                        straight-line integer track model, rANS;
                                        format in csrc/k_ctf.cu).  Batches take
                                        the regular path; 48 more device bytes
-                                       per cluster                             */
+                                       per cluster; a TF above 250 M clusters
+                                       is refused with ETOOBIG                 */
 };
 
 typedef struct {

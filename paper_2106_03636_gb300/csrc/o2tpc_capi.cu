@@ -36,6 +36,10 @@ namespace {
 constexpr int kTileMin = 65536;           // clusters per ingest tile, at least
 constexpr int kTilesPerTFMax = 4096;
 constexpr uint64_t kMaxBatchHits = 2000000000ull;
+// With the compressed TF: the blob offsets are 32-bit, and a coded cluster
+// takes at most about 8.2 bytes (ten byte planes at <= 8 bits plus table
+// rounding), so batches stay below 250 M clusters.
+constexpr uint64_t kMaxCompressHits = 250000000ull;
 // Default for o2tpc_config::batch_full_clusters: this many clusters fill the
 // GPU; larger batches would only add latency (the TFs left out wait, uploaded
 // ahead).
@@ -1272,7 +1276,8 @@ void worker_main(Ctx* c) {
         // a TF joins only if the batch stays within the size that fills the
         // GPU: small TFs share batches, a large one runs alone and never
         // holds small ones back (FIFO order kept: stop at the first misfit)
-        if (!batch.empty() && (fp + j->footprint > c->cfg.mem_budget || hits + j->tf.n > kMaxBatchHits ||
+        const uint64_t maxHits = (c->cfg.flags & O2TPC_FLAG_COMPRESS) ? kMaxCompressHits : kMaxBatchHits;
+        if (!batch.empty() && (fp + j->footprint > c->cfg.mem_budget || hits + j->tf.n > maxHits ||
                                hits + j->tf.n > c->cfg.batch_full_clusters))
           break;
         // with a captured path, batches stay within its arena where they can
@@ -1538,6 +1543,7 @@ static int check_tf(const Ctx* c, const o2tpc_tf* tf) {
     }
   }
   if (tf->n >= kMaxBatchHits) return O2TPC_ETOOBIG;
+  if ((c->cfg.flags & O2TPC_FLAG_COMPRESS) && tf->n > kMaxCompressHits) return O2TPC_ETOOBIG;
   if (footprint_of(tf->n, (c->cfg.flags & O2TPC_FLAG_COMPRESS) != 0) > c->cfg.mem_budget) return O2TPC_ETOOBIG;
   return O2TPC_OK;
 }
