@@ -293,6 +293,30 @@ typedef struct {
  * peaks than cap: nothing written), O2TPC_ENOMEM, O2TPC_ECUDA. */
 int o2tpc_clusterize(const o2tpc_digits* digits, void* records, uint64_t cap, uint64_t* n_clusters, void* stream);
 
+/* A compressed TF decoded on the host (o2tpc_ctf_decode): the cluster
+ * sequence of the format - the kept tracks' clusters first (track by track,
+ * n_tracks tracks of track_len[i] clusters), then the clusters on no track -
+ * as integer coordinates: sector, row, y in 1/160 cm, zeta in 1/64 time bin
+ * (the fixed format's pad64 = y + 32 nPads(row), time64 = zeta).  Arrays are
+ * owned by the library until o2tpc_ctf_free. */
+typedef struct {
+  uint64_t n;
+  uint64_t n_tracks;
+  const int32_t* sector;
+  const int32_t* row;
+  const int32_t* y;
+  const int32_t* zeta;
+  const uint32_t* track_len;
+} o2tpc_ctf_clusters;
+
+/* Decodes a compressed TF (o2tpc_result.ctf) on the host; no device work, no
+ * context needed.  Returns O2TPC_OK, O2TPC_EINVAL (not a compressed TF, or
+ * damaged: every chunk's coder must end in its initial state with its bytes
+ * used up, and the payloads must end the blob), O2TPC_ENOMEM.  *out is
+ * zeroed on error. */
+int o2tpc_ctf_decode(const uint8_t* blob, uint64_t bytes, o2tpc_ctf_clusters* out);
+void o2tpc_ctf_free(o2tpc_ctf_clusters* clusters);
+
 /* Creates a context on cfg->device (cfg may be NULL: all defaults).
  * *out is set on success.  Returns O2TPC_EINVAL, O2TPC_ECUDA or O2TPC_ENOMEM. */
 int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out);

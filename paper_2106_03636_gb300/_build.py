@@ -32,6 +32,7 @@ CUDA_SOURCES = [
     "k_cont.cu",
     "k_ctf.cu",
     "k_clu.cu",
+    "o2tpc_ctf_host.cu",
     "o2tpc_static.cu",
     "o2tpc_graph.cu",
 ]

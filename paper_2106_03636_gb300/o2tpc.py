@@ -155,6 +155,18 @@ class o2tpc_digits(ctypes.Structure):
     ]
 
 
+class o2tpc_ctf_clusters(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("n_tracks", ctypes.c_uint64),
+        ("sector", ctypes.POINTER(ctypes.c_int32)),
+        ("row", ctypes.POINTER(ctypes.c_int32)),
+        ("y", ctypes.POINTER(ctypes.c_int32)),
+        ("zeta", ctypes.POINTER(ctypes.c_int32)),
+        ("track_len", ctypes.POINTER(ctypes.c_uint32)),
+    ]
+
+
 class O2TPCError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -196,6 +208,10 @@ def load(build: bool = True) -> ctypes.CDLL:
         lib.o2tpc_clusterize.restype = ctypes.c_int
         lib.o2tpc_clusterize.argtypes = [ctypes.POINTER(o2tpc_digits), vp, ctypes.c_uint64,
                                          ctypes.POINTER(ctypes.c_uint64), vp]
+        lib.o2tpc_ctf_decode.restype = ctypes.c_int
+        lib.o2tpc_ctf_decode.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(o2tpc_ctf_clusters)]
+        lib.o2tpc_ctf_free.restype = None
+        lib.o2tpc_ctf_free.argtypes = [ctypes.POINTER(o2tpc_ctf_clusters)]
         lib.o2tpc_get_stage.restype = ctypes.c_int
         lib.o2tpc_get_stage.argtypes = [vp, ctypes.c_uint64, ctypes.c_char_p, vp, ctypes.c_uint64,
                                         ctypes.POINTER(ctypes.c_uint64)]
@@ -284,6 +300,24 @@ def clusterize(arrays: dict, stream=None, cap: int | None = None):
     st = stream if stream is not None else torch.cuda.current_stream()
     rc, nc = o2tpc_clusterize(d, out.data_ptr(), cap, st.cuda_stream)
     return rc, (out[:nc] if rc == O2TPC_OK else out[:0]), nc
+
+
+def ctf_decode(blob) -> dict:
+    """Host decoder of a compressed TF (numpy uint8 array): the cluster
+    sequence as numpy arrays (sector, row, y, zeta) and the kept tracks'
+    cluster counts (track_len).  Raises O2TPCError on a damaged blob."""
+    a = np.ascontiguousarray(np.asarray(blob, dtype=np.uint8))
+    c = o2tpc_ctf_clusters()
+    rc = load().o2tpc_ctf_decode(a.ctypes.data, len(a), ctypes.byref(c))
+    if rc != O2TPC_OK:
+        raise O2TPCError(rc, "o2tpc_ctf_decode")
+    try:
+        n, nt = int(c.n), int(c.n_tracks)
+        out = {k: _np(getattr(c, k), n, np.int32) for k in ("sector", "row", "y", "zeta")}
+        out["track_len"] = _np(c.track_len, nt, np.uint32)
+    finally:
+        load().o2tpc_ctf_free(ctypes.byref(c))
+    return out
 
 
 # ---------------------------------------------------------- helpers

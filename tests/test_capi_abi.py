@@ -52,7 +52,7 @@ def test_binding_layout_matches_the_compiled_header(tmp_path):
 
     structs = {"o2tpc_tf": o2tpc.o2tpc_tf, "o2tpc_stats": o2tpc.o2tpc_stats, "o2tpc_result": o2tpc.o2tpc_result,
                "o2tpc_config": o2tpc.o2tpc_config, "o2tpc_tuning": o2tpc.o2tpc_tuning,
-               "o2tpc_digits": o2tpc.o2tpc_digits}
+               "o2tpc_digits": o2tpc.o2tpc_digits, "o2tpc_ctf_clusters": o2tpc.o2tpc_ctf_clusters}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "o2tpc.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')

@@ -51,6 +51,10 @@ def expected_sequence(r, o):
 
 def check_lossless(r, o):
     d = oracle.ctf_decode(r["ctf"])
+    # the library's own host decoder reads the same sequence
+    h = o2tpc.ctf_decode(r["ctf"])
+    assert all(np.array_equal(h[a], d[b]) for a, b in (("sector", "sector"), ("row", "row"), ("y", "y"),
+                                                       ("zeta", "z")))
     idx, lens = expected_sequence(r, o)
     assert np.array_equal(d["track_len"], lens)
     assert np.array_equal(d["sector"], o["rid"][idx] // 152) and np.array_equal(d["row"], o["rid"][idx] % 152)
