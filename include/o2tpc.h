@@ -316,6 +316,12 @@ typedef struct {
  * zeroed on error. */
 int o2tpc_ctf_decode(const uint8_t* blob, uint64_t bytes, o2tpc_ctf_clusters* out);
 void o2tpc_ctf_free(o2tpc_ctf_clusters* clusters);
+/* The decoded clusters as O2TPC_FMT_FIXED records (12 bytes each, host
+ * buffer of 12 n bytes; charge 0): pad64 = y + 32 nPads(row), nPads(row) =
+ * floor(2 x_row tan(10 deg) / 0.4 cm), time64 = zeta; a decoded TF can be
+ * submitted again.  Returns O2TPC_OK or O2TPC_EINVAL (a value out of the
+ * record's range). */
+int o2tpc_ctf_records(const o2tpc_ctf_clusters* clusters, void* records);
 
 /* Creates a context on cfg->device (cfg may be NULL: all defaults).
  * *out is set on success.  Returns O2TPC_EINVAL, O2TPC_ECUDA or O2TPC_ENOMEM. */

@@ -13,6 +13,7 @@
 // cluster counts (lo/hi); residuals are zigzag-mapped, against the straight
 // line through the two previous clusters of the same sector segment of a
 // track (rows ascending) or else against the previous cluster.
+#include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -186,4 +187,32 @@ extern "C" void o2tpc_ctf_free(o2tpc_ctf_clusters* c) {
   std::free(const_cast<int32_t*>(c->zeta));
   std::free(const_cast<uint32_t*>(c->track_len));
   std::memset(c, 0, sizeof(*c));
+}
+
+extern "C" int o2tpc_ctf_records(const o2tpc_ctf_clusters* c, void* records) {
+  if (!c || (c->n > 0 && !records)) return O2TPC_EINVAL;
+  // pads per row: floor(2 x_r tan(10 deg) / 0.4 cm), x_r = 85 + r 160/151 cm
+  int npads[kRows];
+  for (int r = 0; r < kRows; ++r)
+    npads[r] = (int)std::floor(2.0 * (85.0 + r * 160.0 / 151.0) * std::tan(10.0 * 3.14159265358979323846 / 180.0) / 0.4);
+  uint8_t* o = static_cast<uint8_t*>(records);
+  for (uint64_t i = 0; i < c->n; ++i, o += 12) {
+    const int r = c->row[i];
+    const long long pad64 = (long long)c->y[i] + 32ll * npads[r];
+    const long long t64 = c->zeta[i];
+    if (r < 0 || r >= kRows || c->sector[i] < 0 || c->sector[i] >= 36 || pad64 < 0 || pad64 > 0xffff || t64 < 0 ||
+        t64 >= (1ll << 30))
+      return O2TPC_EINVAL;
+    o[0] = (uint8_t)t64;
+    o[1] = (uint8_t)(t64 >> 8);
+    o[2] = (uint8_t)(t64 >> 16);
+    o[3] = (uint8_t)(t64 >> 24);
+    o[4] = (uint8_t)pad64;
+    o[5] = (uint8_t)(pad64 >> 8);
+    o[6] = o[7] = 0;  // charges are not stored
+    o[8] = (uint8_t)r;
+    o[9] = (uint8_t)c->sector[i];
+    o[10] = o[11] = 0;
+  }
+  return O2TPC_OK;
 }

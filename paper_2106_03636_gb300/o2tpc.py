@@ -210,6 +210,8 @@ def load(build: bool = True) -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_uint64), vp]
         lib.o2tpc_ctf_decode.restype = ctypes.c_int
         lib.o2tpc_ctf_decode.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(o2tpc_ctf_clusters)]
+        lib.o2tpc_ctf_records.restype = ctypes.c_int
+        lib.o2tpc_ctf_records.argtypes = [ctypes.POINTER(o2tpc_ctf_clusters), vp]
         lib.o2tpc_ctf_free.restype = None
         lib.o2tpc_ctf_free.argtypes = [ctypes.POINTER(o2tpc_ctf_clusters)]
         lib.o2tpc_get_stage.restype = ctypes.c_int
@@ -304,8 +306,9 @@ def clusterize(arrays: dict, stream=None, cap: int | None = None):
 
 def ctf_decode(blob) -> dict:
     """Host decoder of a compressed TF (numpy uint8 array): the cluster
-    sequence as numpy arrays (sector, row, y, zeta) and the kept tracks'
-    cluster counts (track_len).  Raises O2TPCError on a damaged blob."""
+    sequence as numpy arrays (sector, row, y, zeta), as fixed-format records
+    (records, uint8 [n, 12]) and the kept tracks' cluster counts (track_len).
+    Raises O2TPCError on a damaged blob."""
     a = np.ascontiguousarray(np.asarray(blob, dtype=np.uint8))
     c = o2tpc_ctf_clusters()
     rc = load().o2tpc_ctf_decode(a.ctypes.data, len(a), ctypes.byref(c))
@@ -315,6 +318,11 @@ def ctf_decode(blob) -> dict:
         n, nt = int(c.n), int(c.n_tracks)
         out = {k: _np(getattr(c, k), n, np.int32) for k in ("sector", "row", "y", "zeta")}
         out["track_len"] = _np(c.track_len, nt, np.uint32)
+        rec = np.zeros((max(n, 1), 12), np.uint8)
+        rc = load().o2tpc_ctf_records(ctypes.byref(c), rec.ctypes.data)
+        if rc != O2TPC_OK:
+            raise O2TPCError(rc, "o2tpc_ctf_records")
+        out["records"] = rec[:n]
     finally:
         load().o2tpc_ctf_free(ctypes.byref(c))
     return out

@@ -36,3 +36,22 @@ def test_empty_and_damaged():
     flipped[len(blob) // 2] ^= 0x40
     with pytest.raises(o2tpc.O2TPCError):
         o2tpc.ctf_decode(flipped)
+
+
+def test_decoded_tf_tracks_like_the_original():
+    """Compress, decode to fixed-format records, track again (oracle): the
+    kept tracks come back with the same cluster positions."""
+    tf = synth.full_tpc_1ms(seed=25, n_coll=2, fmt=synth.FMT_FIXED)
+    o = oracle.run(tf, compress=True)
+    d = o2tpc.ctf_decode(o["ctf"])
+    rec = d["records"]
+    # the kept clusters' records equal the input records up to the charge
+    tf_pos = {tuple(r) for r in np.concatenate([tf.packed[:, :6], tf.packed[:, 8:10]], axis=1).tolist()}
+    dec_pos = [tuple(r) for r in np.concatenate([rec[:, :6], rec[:, 8:10]], axis=1).tolist()]
+    assert all(p in tf_pos for p in dec_pos)
+    tf2 = synth.TimeFrame(n=len(rec), fmt=synth.FMT_FIXED, sector=rec[:, 9].copy(), row=rec[:, 8].copy(),
+                          packed=np.ascontiguousarray(rec), bz=tf.bz, vdrift=tf.vdrift)
+    o2 = oracle.run(tf2, fields=["trk_off", "trk_par"])
+    kept = np.abs(o["trk_par"][:, 4]) <= 10.0
+    n_kept, n2 = int(kept.sum()), len(o2["trk_off"]) - 1
+    assert abs(n2 - n_kept) <= 0.02 * n_kept
