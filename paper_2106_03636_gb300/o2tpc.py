@@ -401,13 +401,15 @@ class Tracker:
     ``torch_memory``: allocate the library's device buffers from PyTorch's
     caching allocator (host-resident inputs are then copied in the batch's
     stream); otherwise the library's own memory pool and copy stream serve
-    them and uploads of queued TFs overlap earlier batches."""
+    them and uploads of queued TFs overlap earlier batches.  ``fail_alloc``
+    (with ``torch_memory``): called with each request's size; True makes that
+    allocation fail (fault tests)."""
 
     def __init__(self, device: int = 0, bz: float = 0.5, vdrift: float = 2.58, flags: int = 0,
                  mem_budget: int = 0, max_inflight: int = 0, max_batch: int = 0, torch_memory: bool = False,
                  batch_full_clusters: int = 0, nf_hits_per_block: int = 0, sort_threads_per_row: int = 0,
                  graph_max_clusters: int = 0, graph_max_tfs: int = 0, nf_staged: bool = False,
-                 tune_cache_path: str | None = None):
+                 tune_cache_path: str | None = None, fail_alloc=None):
         self.cfg = o2tpc_config()
         self.cfg.device = device
         self.cfg.bz_tesla = bz
@@ -435,6 +437,8 @@ class Tracker:
             st = self.stream
 
             def _alloc(nbytes, user):
+                if fail_alloc is not None and fail_alloc(int(nbytes)):
+                    return None
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
                 except Exception:
