@@ -217,7 +217,9 @@ typedef struct {
   float ms_stage[18];
   uint32_t captured;         /* 1: the batch ran as one CUDA graph launch (the
                                 captured path: ms_stage holds only 10-13)     */
-  uint32_t reserved;
+  uint32_t events;           /* bit0: a bounded device wait ran out in the batch
+                                (the NeighboursFinder's staged copy; the step
+                                then read global memory, results complete)  */
 } o2tpc_stats;
 
 /* Result of one TF; library-owned memory, valid until o2tpc_result_release. */

@@ -1075,6 +1075,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
   // more membrane candidate pairs than the buffer holds (2 per sector track):
   // the links would be incomplete, so the batch's TFs report ETOOBIG
   const bool memOverflow = (*hErr & kErrMembrane) != 0;
+  const uint32_t events = (*hErr & kErrTimeout) ? 1u : 0u;
   cudaStream_t dl = c->dlStream;
   CK(cudaEventCreate(&P->dl0));
   CK(cudaEventCreate(&P->dl1));
@@ -1149,6 +1150,7 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     R.stats.ms_queue = (float)(J.t_start - J.t_submit);
     R.stats.ms_device = devMs;
     R.stats.n_launches = (uint64_t)nLaunch;
+    R.stats.events = events;
     J.status = inputBad ? O2TPC_EINVAL : (memOverflow ? O2TPC_ETOOBIG : O2TPC_OK);
     R.status = J.status;
     J.tfIndex = i;

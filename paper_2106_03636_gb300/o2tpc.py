@@ -108,7 +108,7 @@ class o2tpc_stats(ctypes.Structure):
         ("n_launches", ctypes.c_uint64),
         ("ms_stage", ctypes.c_float * 18),
         ("captured", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32),
+        ("events", ctypes.c_uint32),
     ]
 
 STAGES = ("ingest", "sort", "neighbours", "clean_starts", "tracklets", "selection", "sector_fit", "merge",
