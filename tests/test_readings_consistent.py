@@ -51,3 +51,18 @@ def test_clusterizer_constants():
     o = src("oracle", "o2tpc_clu.c")
     k = src("paper_2106_03636_gb300", "csrc", "k_clu.cu")
     assert c_define(o, "U_PEAK_MIN") == cu_const(k, "kPeakMin") == 3
+
+
+def test_tracking_constants():
+    o = src("oracle", "o2tpc_oracle.c")
+    k = src("paper_2106_03636_gb300", "csrc", "o2tpc_internal.cuh")
+    pairs = [("O_CY", "kCellY"), ("O_T", "kHitsPerCell"), ("O_WY", "kWinY"), ("O_WZ", "kWinZ"),
+             ("O_SY", "kSigY"), ("O_SZ", "kSigZ"), ("O_G", "kMaxMiss"), ("O_NMIN", "kMinHits"),
+             ("O_CHI2_FOLLOW", "kChi2Follow"), ("O_SIN_FOLLOW", "kSinFollow"), ("O_SIN_PROP", "kSinProp"),
+             ("O_EDGE", "kEdgeBand"), ("O_DZETA_PRE", "kMergeDZeta"), ("O_CHI2_MERGE", "kChi2Merge")]
+    for a, b in pairs:
+        assert c_define(o, a) == cu_const(k, b), (a, b)
+    # the integer metric: weights and cut
+    assert re.search(r"#define O_AY 2077LL", o) and cu_const(k, "kWeightY") == 2077
+    assert re.search(r"#define O_AZ 1536LL", o) and cu_const(k, "kWeightZ") == 1536
+    assert "#define O_DMAX (16LL * 1536LL * 2077LL)" in o and "kMaxMetric = 16 * 1536 * 2077;" in k
