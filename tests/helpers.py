@@ -64,3 +64,23 @@ class Helix:
         s, ph = best
         y = yc - self.h * self.R * math.cos(ph)
         return y, math.sin(ph), s, self.zv + s * self.tanl
+
+
+class Line:
+    """A particle from (0, 0, zv) at time t0 in a field-free TPC (Bz = 0): a
+    straight line at azimuth phi0.  Independent closed form for the pulls
+    of the field-free fit."""
+
+    def __init__(self, eta, phi0, zv=0.0, t0=0.0):
+        self.eta, self.phi0, self.zv, self.t0 = eta, phi0, zv, t0
+        self.tanl = math.sinh(eta)
+
+    def at_local_x(self, alpha, x):
+        """(y, sin phi_local, arc length, z) at local x in the frame alpha;
+        None if the line runs away from that x."""
+        ph = self.phi0 - alpha
+        c = math.cos(ph)
+        if c <= 0:
+            return None
+        s = x / c
+        return x * math.tan(ph), math.sin(ph), s, self.zv + s * self.tanl

@@ -232,3 +232,43 @@ def test_empty_input():
     tf = float_tf([], [], [], [])
     o = oracle.run(tf)
     assert len(o["sorted_orig"]) == 0 and len(o["trk_x"]) == 0 and o["trk_off"].tolist() == [0]
+
+
+def test_grid_dimensions_handworked_golden():
+    """Grid dimensions (ny, nz, cz, zeta_min) and cell indices of listed hits
+    against values worked out by hand (tests/golden/grid_handworked.json):
+    a wrong pad count, a wrong cell width, nz off by one or cz rounded the
+    wrong way changes at least one of them."""
+    g = json.load(open(os.path.join(GOLDEN, "grid_handworked.json")))
+    sec, row, pad, tim, listed = [], [], [], [], []
+    for r in g["rows"]:
+        base = len(sec)
+        listed.append(list(range(base, base + len(r["pad64"]))))
+        sec += [r["sector"]] * len(r["pad64"])
+        row += [r["row"]] * len(r["pad64"])
+        pad += r["pad64"]
+        tim += r["time64"]
+        f = r["fillers"]
+        if f:
+            k = np.arange(f["count"])
+            a, b = (int(v) for v in f["pad64"].replace("(", "").replace(")", "").replace(" k", "").split(" mod "))
+            c0, c1 = (int(v) for v in f["time64"].replace(" k", "").split(" + "))
+            sec += [r["sector"]] * f["count"]
+            row += [r["row"]] * f["count"]
+            pad += ((a * k) % b).tolist()
+            tim += (c0 + c1 * k).tolist()
+    tf = fixed_tf(sec, row, pad, tim)
+    o = oracle.run(tf)
+    inv = np.argsort(o["sorted_orig"])
+    for r, idx in zip(g["rows"], listed):
+        rid = r["sector"] * 152 + r["row"]
+        e = r["expected"]
+        got = (int(o["row_count"][rid]), int(o["row_ny"][rid]), int(o["row_nz"][rid]), int(o["row_cz"][rid]),
+               int(o["row_zmin"][rid]))
+        assert got == (e["count"], e["ny"], e["nz"], e["cz"], e["zmin"]), (r["name"], got)
+        assert [int(o["sorted_cell"][inv[i]]) for i in idx] == e["cells"], r["name"]
+    for r in g["empty_rows"]:
+        rid = r["sector"] * 152 + r["row"]
+        e = r["expected"]
+        got = (int(o["row_count"][rid]), int(o["row_ny"][rid]), int(o["row_nz"][rid]))
+        assert got == (e["count"], e["ny"], e["nz"]), (r, got)

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import Helix, VDRIFT
+from helpers import Helix, Line, VDRIFT
 from paper_2106_03636_gb300 import synth
 
 ZUNIT = 0.003125 * VDRIFT
@@ -84,34 +84,70 @@ def test_noise_free_helices_recovered_exactly():
         assert abs(d[0]) < 0.004 and abs(d[1]) < 0.008
 
 
-@pytest.mark.slow
-def test_fit_pulls_unit_width():
-    """Pull widths of all five parameters are 1 within 0.06 and means 0
-    within 0.1.  A wrong covariance term moves a width by far more.  The
-    means carry the extended filter's second-order linearisation bias (about
-    +0.07 sigma in tan(lambda), +0.04 in zeta; it vanishes at Bz = 0).  The
-    collision sits at t0 = 20 us so that no cluster meets the start of the
-    readout window, where a cut on the smeared time would bias zeta."""
-    pulls = []
+def pulls(bz, n_min, seed0):
+    """Fit pulls (fitted - truth) / sigma of the five parameters on
+    single-sector collisions at t0 = 20 us (no cluster meets the start of the
+    readout window, where a cut on the smeared time would bias zeta), over
+    tracks whose clusters all come from one particle."""
+    out = []
     ev = 0
-    while len(pulls) < 10000:
-        tf = synth.single_sector(seed=1000 + ev, ntracks=200, t0=20.0)
+    while len(out) < n_min:
+        tf = synth.single_sector(seed=seed0 + ev, ntracks=200, t0=20.0, bz=bz)
         o = oracle.run(tf)
         for i, (tid, pur) in enumerate(match_tracks(tf, o)):
             if tid < 0 or pur < 1.0:
                 continue
-            tr = truth_state(tf, tid, o, i)
+            tr = truth_state(tf, tid, o, i) if bz != 0 else line_state(tf, tid, o, i)
             if tr is None:
                 continue
             d = fitted(o, i) - tr
             c = o["trk_cov"][i]
             sig = np.sqrt([c[0], c[2], c[5], c[9], c[14]])
-            pulls.append(d / sig)
+            out.append(d / sig)
         ev += 1
-    P = np.array(pulls)
+    return np.array(out)
+
+
+def line_state(tf, tid, o, i):
+    """Truth (y, zeta, sin phi, tan lambda) of a straight track at the output
+    x and frame (Bz = 0), with q/pT = 0: without a field the filter cannot
+    move q/pT from the centre of its prior."""
+    T = tf.truth
+    ln = Line(T["eta"][tid], T["phi0"][tid], T["zv"][tid], T["t0"][tid])
+    r = ln.at_local_x(o["trk_alpha"][i], o["trk_x"][i])
+    if r is None:
+        return None
+    y, s, arc, z = r
+    side = 1 if o["trk_sector"][i] < 18 else -1
+    zeta = VDRIFT * ln.t0 + 250.0 - side * z
+    return np.array([y, zeta, s, ln.tanl, 0.0])
+
+
+@pytest.mark.slow
+def test_fit_pulls_unit_width():
+    """Pull widths of all five parameters are 1 within 0.03 at Bz = 0.5 T
+    (10^4 tracks resolve a width to about 0.007; a wrong covariance term
+    moves it by far more).  The means carry the extended filter's
+    second-order linearisation bias (about +0.06 sigma in tan(lambda), +0.04
+    in zeta), so they are bounded here only loosely; the field-free test
+    below pins them."""
+    P = pulls(0.5, 10000, 1000)
     mean, width = P.mean(axis=0), P.std(axis=0)
+    assert np.all(np.abs(width - 1.0) < 0.03), width
     assert np.all(np.abs(mean) < 0.1), mean
-    assert np.all(np.abs(width - 1.0) < 0.06), width
+
+
+@pytest.mark.slow
+def test_fit_pull_means_field_free():
+    """At Bz = 0 the tracks are straight lines, the curvature terms of the
+    transport vanish and with them the linearisation bias: the pull means of
+    y, zeta, sin(phi) and tan(lambda) are 0 within 0.03 (statistical error
+    0.01 on 10^4 tracks); q/pT is not observable without a field and its
+    estimate stays exactly at the prior's centre, 0."""
+    P = pulls(0.0, 10000, 1000)
+    mean = P[:, :4].mean(axis=0)
+    assert np.all(np.abs(mean) < 0.03), mean
+    assert np.all(P[:, 4] == 0.0)
 
 
 def efficiency(tf, o, min_cl=10):
