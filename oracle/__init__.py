@@ -50,6 +50,8 @@ class _Input(ctypes.Structure):
         ("coll_time", ctypes.c_void_p),
         ("n_coll", ctypes.c_int64),
         ("compress", ctypes.c_int32),
+        ("row_step2", ctypes.c_int32),
+        ("angular_errors", ctypes.c_int32),
     ]
 
 
@@ -123,11 +125,13 @@ def _vp(a):
 
 
 def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=None, coll_time=None,
-        compress: bool = False) -> dict:
+        compress: bool = False, row_step2: bool = False, angular_errors: bool = False) -> dict:
     """Runs the oracle on a ``synth.TimeFrame``-like object (attributes n,
     fmt, sector, row, y, z, packed, bz, vdrift, and optionally coll_time,
     the TF's interaction times in us).  ``coll_time`` overrides the TF's;
-    ``compress`` also builds the compressed TF (field ``ctf``, bytes).
+    ``compress`` also builds the compressed TF (field ``ctf``, bytes);
+    ``row_step2`` lets the NeighboursFinder link across one missing pad row;
+    ``angular_errors`` makes the cluster errors grow with the track angles.
     Returns a dict of numpy arrays (copies) named as in ``FIELDS``."""
     lib = _load()
     inp = _Input()
@@ -149,6 +153,8 @@ def run(tf, sector_mask: int = 0, reverse_tracklet_order: bool = False, fields=N
     inp.sector_mask = sector_mask
     inp.reverse_tracklet_order = int(reverse_tracklet_order)
     inp.compress = int(compress)
+    inp.row_step2 = int(row_step2)
+    inp.angular_errors = int(angular_errors)
     ct = coll_time if coll_time is not None else getattr(tf, "coll_time", None)
     if ct is not None and len(ct):
         ct = np.ascontiguousarray(np.asarray(ct, dtype=np.float64))

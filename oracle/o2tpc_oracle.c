@@ -61,6 +61,12 @@
 #define O_EDGE 5.0          /* border-track band, cm                             */
 #define O_DZETA_PRE 20.0    /* merge prefilter on endpoint zeta, cm              */
 #define O_CHI2_MERGE 30.0
+/* Angle-dependent cluster errors (reading, optional): a track crossing the
+ * pad row at an angle spreads its charge over the pad length L (the row
+ * pitch, 160/151 cm) times tan(phi) along y and times tan(lambda) along the
+ * drift; the centroid's variance grows by (L tan)^2 / 12 (a uniform spread
+ * of that width). */
+#define O_LPAD2_12 ((160.0 / 151.0) * (160.0 / 151.0) / 12.0)
 
 static double o_rowx(int r) { return 85.0 + (double)r * 160.0 / 151.0; }
 static int o_npads(int r) { return (int)floor(2.0 * o_rowx(r) * tan(10.0 * O_PI / 180.0) / 0.4); }
@@ -84,6 +90,8 @@ typedef struct { const char* name; const void* ptr; int64_t n; int32_t type; } o
 struct oracle_result {
   int64_t n, nsel;
   double zunit, bzc;
+  int angerr;   /* angle-dependent cluster errors */
+  int rowstep2; /* NeighboursFinder also links across one missing pad row */
   /* per input cluster */
   int32_t *yu, *zu, *rid;
   /* per sorted hit */
@@ -186,11 +194,26 @@ static int o_prop(ost* t, double x2, double bzc) {
   return 0;
 }
 
-/* Kalman update with a (y, zeta) measurement of errors (O_SY, O_SZ). */
-static int o_update(ost* t, double ym, double zm, double* chi2) {
+/* Measurement variances (y, zeta) of a cluster on a track with the state's
+ * angles: the constant O_SY^2, O_SZ^2, plus with angerr the pad-length terms
+ * (L tan(phi))^2 / 12 and (L tan(lambda))^2 / 12, tan^2(phi) = s^2 / (1 - s^2)
+ * from sin(phi) = s, tan(lambda) = |dzeta/ds| = |t|. */
+static void o_meas_var(int angerr, const ost* t, double* vy, double* vz) {
+  *vy = O_SY * O_SY;
+  *vz = O_SZ * O_SZ;
+  if (angerr) {
+    double s2 = t->p[2] * t->p[2];
+    double tan2 = s2 < 1.0 ? s2 / (1.0 - s2) : 1e6;
+    *vy += O_LPAD2_12 * tan2;
+    *vz += O_LPAD2_12 * t->p[3] * t->p[3];
+  }
+}
+
+/* Kalman update with a (y, zeta) measurement of variances (vy, vz). */
+static int o_update_v(ost* t, double ym, double zm, double vy, double vz, double* chi2) {
   double* C = t->C;
   double r0 = ym - t->p[0], r1 = zm - t->p[1];
-  double S00 = C[0] + O_SY * O_SY, S01 = C[1], S11 = C[2] + O_SZ * O_SZ;
+  double S00 = C[0] + vy, S01 = C[1], S11 = C[2] + vz;
   double det = S00 * S11 - S01 * S01;
   if (!(det > 0.0)) return -1;
   double I00 = S11 / det, I01 = -S01 / det, I11 = S00 / det;
@@ -201,6 +224,11 @@ static int o_update(ost* t, double ym, double zm, double* chi2) {
   for (int i = 0; i < 5; ++i) t->p[i] += K0[i] * r0 + K1[i] * r1;
   for (int i = 0; i < 5; ++i) for (int j = 0; j <= i; ++j) C[o_ix(i, j)] -= K0[i] * Cy[j] + K1[i] * Cz[j];
   return 0;
+}
+
+/* Kalman update with the constant cluster errors (O_SY, O_SZ). */
+static int o_update(ost* t, double ym, double zm, double* chi2) {
+  return o_update_v(t, ym, zm, O_SY * O_SY, O_SZ * O_SZ, chi2);
 }
 
 /* Rotation of the frame by dalpha (new alpha = old alpha + dalpha). */
@@ -407,7 +435,73 @@ static int o_cellrange(const oracle_result* R, int rid, int64_t ylo, int64_t yhi
   return 1;
 }
 
+/* Fit helpers of the tracker: measurement variances follow R->angerr. */
+static int o_upd(const oracle_result* R, ost* t, double ym, double zm, double* chi2) {
+  double vy, vz;
+  o_meas_var(R->angerr, t, &vy, &vz);
+  return o_update_v(t, ym, zm, vy, vz, chi2);
+}
+/* Fresh covariance: the initial diagonal, its (y, zeta) entries the cluster
+ * variances at the state's angles. */
+static void o_reset_cov(const oracle_result* R, ost* t) {
+  memcpy(t->C, O_CINIT, sizeof(O_CINIT));
+  o_meas_var(R->angerr, t, &t->C[0], &t->C[2]);
+}
+static void o_init(const oracle_result* R, ost* t, double x, double y, double z, double s, double tz, double q) {
+  o_init_state(t, x, y, z, s, tz, q);
+  o_reset_cov(R, t);
+}
+
 /* ------------------------------------------------------ NeighboursFinder */
+/* Row step 2 (reading, optional): when hit h on row r has no accepted pair
+ * on the adjacent rows, it may link across one missing row: up on row r + a,
+ * down on row r - b, (a, b) in {(2,1), (1,2), (2,2)}, inside rows 0..151.
+ * The straight-line residual generalises to e = (a + b) h - b u - a d (in y
+ * and in zeta), whose variance is f = (a + b)^2 + a^2 + b^2 times a cluster's
+ * (f = 6 for a = b = 1), so D = 2077 e_y^2 + 1536 e_zeta^2 scaled by 6 / f is
+ * the same 2-dof chi2 as before: accepted if 6 D <= 16 * 1536 * 2077 * f;
+ * windows a * 1.5 cm, a * 2 cm up and b times those down.  The best pair
+ * minimises 6 D / f (compared exactly as D1 f2 < D2 f1), ties to the smaller
+ * sorted u, then d. */
+static void o_neighbours_gap(const oracle_result* R, int64_t h, int64_t* bu_out, int64_t* bd_out) {
+  int rid = R->s_rid[h];
+  int r = rid % O_NROW;
+  int64_t yh = R->s_y[h], zh = R->s_z[h];
+  int64_t bD = -1, bf = 1, bu = -1, bd = -1;
+  static const int steps[3][2] = {{2, 1}, {1, 2}, {2, 2}};
+  for (int k = 0; k < 3; ++k) {
+    int a = steps[k][0], b = steps[k][1];
+    if (r + a > O_NROW - 1 || r - b < 0) continue;
+    int ru = rid + a, rd = rid - b;
+    int uy0, uy1, dy0, dy1; int64_t uz0, uz1, dz0, dz1;
+    if (!o_cellrange(R, ru, yh - a * O_WY, yh + a * O_WY, zh - a * O_WZ, zh + a * O_WZ, &uy0, &uy1, &uz0, &uz1)) continue;
+    if (!o_cellrange(R, rd, yh - b * O_WY, yh + b * O_WY, zh - b * O_WZ, zh + b * O_WZ, &dy0, &dy1, &dz0, &dz1)) continue;
+    int64_t f = (int64_t)(a + b) * (a + b) + a * a + b * b;
+    for (int64_t izu = uz0; izu <= uz1; ++izu) {
+      int64_t ua = R->cell_start[R->r_cellbase[ru] + izu * R->r_ny[ru] + uy0];
+      int64_t ub = R->cell_start[R->r_cellbase[ru] + izu * R->r_ny[ru] + uy1 + 1];
+      for (int64_t u = ua; u < ub; ++u) {
+        int64_t yu = R->s_y[u], zu = R->s_z[u];
+        if (llabs(yu - yh) > a * O_WY || llabs(zu - zh) > a * O_WZ) continue;
+        for (int64_t izd = dz0; izd <= dz1; ++izd) {
+          int64_t da = R->cell_start[R->r_cellbase[rd] + izd * R->r_ny[rd] + dy0];
+          int64_t db = R->cell_start[R->r_cellbase[rd] + izd * R->r_ny[rd] + dy1 + 1];
+          for (int64_t d = da; d < db; ++d) {
+            int64_t yd = R->s_y[d], zd = R->s_z[d];
+            if (llabs(yd - yh) > b * O_WY || llabs(zd - zh) > b * O_WZ) continue;
+            int64_t ey = (a + b) * yh - b * yu - a * yd, ez = (a + b) * zh - b * zu - a * zd;
+            int64_t D = O_AY * ey * ey + O_AZ * ez * ez;
+            if (6 * D > O_DMAX * f) continue;
+            int better = bu < 0 || D * bf < bD * f || (D * bf == bD * f && (u < bu || (u == bu && d < bd)));
+            if (better) { bD = D; bf = f; bu = u; bd = d; }
+          }
+        }
+      }
+    }
+  }
+  *bu_out = bu; *bd_out = bd;
+}
+
 static void o_neighbours(oracle_result* R) {
   int64_t n = R->nsel;
   for (int64_t h = 0; h < n; ++h) { R->up_raw[h] = -1; R->dn_raw[h] = -1; }
@@ -417,10 +511,12 @@ static void o_neighbours(oracle_result* R) {
     if (r < 1 || r > O_NROW - 2) continue;
     int64_t yh = R->s_y[h], zh = R->s_z[h];
     int ru = rid + 1, rd = rid - 1;
-    int uy0, uy1, dy0, dy1; int64_t uz0, uz1, dz0, dz1;
-    if (!o_cellrange(R, ru, yh - O_WY, yh + O_WY, zh - O_WZ, zh + O_WZ, &uy0, &uy1, &uz0, &uz1)) continue;
-    if (!o_cellrange(R, rd, yh - O_WY, yh + O_WY, zh - O_WZ, zh + O_WZ, &dy0, &dy1, &dz0, &dz1)) continue;
+    int uy0 = 0, uy1 = -1, dy0 = 0, dy1 = -1; int64_t uz0 = 0, uz1 = -1, dz0 = 0, dz1 = -1;
     int64_t bestD = INT64_MAX, bu = -1, bd = -1;
+    /* an empty cell range on either side leaves no (r+1, r-1) pair */
+    if (!o_cellrange(R, ru, yh - O_WY, yh + O_WY, zh - O_WZ, zh + O_WZ, &uy0, &uy1, &uz0, &uz1) ||
+        !o_cellrange(R, rd, yh - O_WY, yh + O_WY, zh - O_WZ, zh + O_WZ, &dy0, &dy1, &dz0, &dz1))
+      uz1 = uz0 - 1;
     for (int64_t izu = uz0; izu <= uz1; ++izu) {
       int64_t ua = R->cell_start[R->r_cellbase[ru] + izu * R->r_ny[ru] + uy0];
       int64_t ub = R->cell_start[R->r_cellbase[ru] + izu * R->r_ny[ru] + uy1 + 1];
@@ -441,6 +537,7 @@ static void o_neighbours(oracle_result* R) {
         }
       }
     }
+    if (bu < 0 && R->rowstep2) o_neighbours_gap(R, h, &bu, &bd);
     R->up_raw[h] = (int32_t)bu; R->dn_raw[h] = (int32_t)bd;
   }
 }
@@ -466,7 +563,9 @@ static double o_hz(const oracle_result* R, int32_t h, int32_t zref) { return (do
 /* Best hit of row rid inside the +-3 sigma window of the prediction (ties:
  * smaller sorted index); -1 if none passes chi2 <= O_CHI2_FOLLOW. */
 static int32_t o_search(const oracle_result* R, int rid, const ost* t, int32_t zref) {
-  double sy2 = t->C[0] + O_SY * O_SY, sz2 = t->C[2] + O_SZ * O_SZ;
+  double vy, vz;
+  o_meas_var(R->angerr, t, &vy, &vz);
+  double sy2 = t->C[0] + vy, sz2 = t->C[2] + vz;
   double wy = 3.0 * sqrt(sy2), wz = 3.0 * sqrt(sz2);
   int64_t ylo = (int64_t)floor((t->p[0] - wy) * 160.0) - 1, yhi = (int64_t)ceil((t->p[0] + wy) * 160.0) + 1;
   int64_t zlo = zref + (int64_t)floor((t->p[1] - wz) / R->zunit) - 1;
@@ -510,11 +609,11 @@ static int o_construct(oracle_result* R, int32_t h0, int32_t* out, double* state
   double s0 = tphi / sqrt(1.0 + tphi * tphi);
   double t0 = (o_hz(R, chain[2], zref) - o_hz(R, chain[0], zref)) / sqrt(dx * dx + dy * dy);
   ost t;
-  o_init_state(&t, x0, o_hy(R, chain[0]), o_hz(R, chain[0], zref), s0, t0, 0.0);
+  o_init(R, &t, x0, o_hy(R, chain[0]), o_hz(R, chain[0], zref), s0, t0, 0.0);
   for (int i = 1; i < nc; ++i) {
     int32_t h = chain[i];
     if (o_prop(&t, o_rowx(R->s_rid[h] % O_NROW), R->bzc) != 0) return 0;
-    o_update(&t, o_hy(R, h), o_hz(R, h, zref), NULL);
+    o_upd(R, &t, o_hy(R, h), o_hz(R, h, zref), NULL);
   }
   /* upward following */
   int32_t upl[O_NROW]; int nup = 0;
@@ -526,7 +625,7 @@ static int o_construct(oracle_result* R, int32_t h0, int32_t* out, double* state
     if (fabs(t.p[2]) > O_SIN_FOLLOW) break;
     int32_t h = o_search(R, sbase + r, &t, zref);
     if (h >= 0) {
-      o_update(&t, o_hy(R, h), o_hz(R, h, zref), NULL);
+      o_upd(R, &t, o_hy(R, h), o_hz(R, h, zref), NULL);
       upl[nup++] = h; top = h; last = t; misses = 0;
     } else if (++misses >= O_G) break;
   }
@@ -536,11 +635,11 @@ static int o_construct(oracle_result* R, int32_t h0, int32_t* out, double* state
   for (int i = 0; i < nup; ++i) att[na++] = upl[i];
   t = last;
   t.p[0] = o_hy(R, top); t.p[1] = o_hz(R, top, zref);
-  memcpy(t.C, O_CINIT, sizeof(O_CINIT));
+  o_reset_cov(R, &t);
   for (int i = na - 2; i >= 0; --i) {
     int32_t h = att[i];
     if (o_prop(&t, o_rowx(R->s_rid[h] % O_NROW), R->bzc) != 0) continue;
-    o_update(&t, o_hy(R, h), o_hz(R, h, zref), NULL);
+    o_upd(R, &t, o_hy(R, h), o_hz(R, h, zref), NULL);
   }
   last = t;
   int32_t dnl[O_NROW]; int ndn = 0;
@@ -550,7 +649,7 @@ static int o_construct(oracle_result* R, int32_t h0, int32_t* out, double* state
     if (fabs(t.p[2]) > O_SIN_FOLLOW) break;
     int32_t h = o_search(R, sbase + r, &t, zref);
     if (h >= 0) {
-      o_update(&t, o_hy(R, h), o_hz(R, h, zref), NULL);
+      o_upd(R, &t, o_hy(R, h), o_hz(R, h, zref), NULL);
       dnl[ndn++] = h; last = t; misses = 0;
     } else if (++misses >= O_G) break;
   }
@@ -593,18 +692,18 @@ static void o_sector_fit(oracle_result* R, const int32_t* hits, int m, const dou
   ost tmp = sd;
   if (o_prop(&tmp, xa, R->bzc) == 0) sd = tmp;
   ost t;
-  o_init_state(&t, xa, o_hy(R, hits[0]), o_hz(R, hits[0], zref), sd.p[2], sd.p[3], sd.p[4]);
+  o_init(R, &t, xa, o_hy(R, hits[0]), o_hz(R, hits[0], zref), sd.p[2], sd.p[3], sd.p[4]);
   for (int i = 1; i < m; ++i) {
     if (o_prop(&t, o_rowx(R->s_rid[hits[i]] % O_NROW), R->bzc) != 0) continue;
-    o_update(&t, o_hy(R, hits[i]), o_hz(R, hits[i], zref), NULL);
+    o_upd(R, &t, o_hy(R, hits[i]), o_hz(R, hits[i], zref), NULL);
   }
   o_store_state(st_out, &t);
   ost u;
-  o_init_state(&u, o_rowx(R->s_rid[hits[m - 1]] % O_NROW), o_hy(R, hits[m - 1]), o_hz(R, hits[m - 1], zref),
+  o_init(R, &u, o_rowx(R->s_rid[hits[m - 1]] % O_NROW), o_hy(R, hits[m - 1]), o_hz(R, hits[m - 1], zref),
                t.p[2], t.p[3], t.p[4]);
   for (int i = m - 2; i >= 0; --i) {
     if (o_prop(&u, o_rowx(R->s_rid[hits[i]] % O_NROW), R->bzc) != 0) continue;
-    o_update(&u, o_hy(R, hits[i]), o_hz(R, hits[i], zref), NULL);
+    o_upd(R, &u, o_hy(R, hits[i]), o_hz(R, hits[i], zref), NULL);
   }
   o_store_state(st_in, &u);
 }
@@ -796,7 +895,7 @@ static void o_final(oracle_result* R) {
     const double* so = R->st_out + 21 * tail;
     int frame = hsec[m - 1];
     ost t;
-    o_init_state(&t, o_rowx(R->s_rid[hs[m - 1]] % O_NROW), o_hy(R, hs[m - 1]), o_hz(R, hs[m - 1], zref), so[3], so[4], so[5]);
+    o_init(R, &t, o_rowx(R->s_rid[hs[m - 1]] % O_NROW), o_hy(R, hs[m - 1]), o_hz(R, hs[m - 1], zref), so[3], so[4], so[5]);
     double chi2 = 0; int used = 1; int flags = nseg > 1 ? 2 : 0;
     for (int64_t i = m - 2; i >= 0; --i) {
       int32_t h = hs[i];
@@ -806,7 +905,7 @@ static void o_final(oracle_result* R) {
       }
       if (o_prop(&t, o_rowx(R->s_rid[h] % O_NROW), R->bzc) != 0) continue;
       double c2;
-      if (o_update(&t, o_hy(R, h), o_hz(R, h, zref), &c2) != 0) continue;
+      if (o_upd(R, &t, o_hy(R, h), o_hz(R, h, zref), &c2) != 0) continue;
       chi2 += c2; ++used;
     }
     R->trk_off[it] = o;
@@ -1045,6 +1144,8 @@ oracle_result* oracle_run(const oracle_input* in, int32_t* status) {
   R->n = in->n;
   R->zunit = 0.003125 * in->vdrift;
   R->bzc = o_bzc(in->bz);
+  R->angerr = in->angular_errors != 0;
+  R->rowstep2 = in->row_step2 != 0;
   int64_t n1 = in->n + 1;
   R->yu = (int32_t*)malloc((size_t)n1 * 4); R->zu = (int32_t*)malloc((size_t)n1 * 4); R->rid = (int32_t*)malloc((size_t)n1 * 4);
   if (o_ingest(R, in) != 0) { *status = -1; oracle_free(R); return NULL; }

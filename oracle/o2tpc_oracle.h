@@ -29,6 +29,8 @@ typedef struct {
   const double* coll_time; /* interaction times of the TF, us, ascending (may be NULL) */
   int64_t n_coll;
   int32_t compress;        /* 1: also build the compressed TF ("ctf", o2tpc_ctf.c) */
+  int32_t row_step2;       /* 1: NeighboursFinder also links across one missing pad row */
+  int32_t angular_errors;  /* 1: cluster errors grow with the track's angles */
 } oracle_input;
 
 typedef struct oracle_result oracle_result;

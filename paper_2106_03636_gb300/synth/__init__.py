@@ -21,7 +21,10 @@ Physics of every primary: pT ~ 0.05 GeV + Exp(0.6 GeV), |eta| < 0.9,
 charge +-1, helix in Bz = 0.5 T, one cluster per crossed pad row, Gaussian
 smearing sigma_y = 0.1 cm, sigma_z = 0.15 cm, plus 10 % uniform noise
 clusters.  All random draws are seeded; the per-track draws are
-counter-based inside ``o2gen.c``.
+counter-based inside ``o2gen.c``.  Options: ``angular_errors`` adds the
+pad-length term (L tan phi)^2 / 12 and (L tan lambda)^2 / 12 (L = 160/151
+cm) to the smearing variances; ``row_drop`` loses each track cluster with
+that probability (missing pad rows).
 """
 from __future__ import annotations
 
@@ -66,6 +69,8 @@ class _GenParams(ctypes.Structure):
         ("vdrift", ctypes.c_double),
         ("t_window", ctypes.c_double),
         ("nthreads", ctypes.c_int32),
+        ("angular_errors", ctypes.c_int32),
+        ("row_drop", ctypes.c_double),
     ]
 
 
@@ -132,7 +137,7 @@ def generate(*, seed: int, t0, ntracks, fmt: int = FMT_FLOAT, sector_only: int =
              noise_frac: float = 0.1, bz: float = BZ, vdrift: float = VDRIFT,
              t_window: float | None = None, pt_mean: float = 0.6, pt_min: float = 0.05,
              eta_min: float = -0.9, eta_max: float = 0.9, with_truth: bool = True, nthreads: int | None = None,
-             name: str = "") -> TimeFrame:
+             name: str = "", angular_errors: bool = False, row_drop: float = 0.0) -> TimeFrame:
     lib = _load()
     t0 = np.ascontiguousarray(np.asarray(t0, dtype=np.float64))
     ntracks = np.ascontiguousarray(np.asarray(ntracks, dtype=np.int32))
@@ -149,6 +154,8 @@ def generate(*, seed: int, t0, ntracks, fmt: int = FMT_FLOAT, sector_only: int =
     P.zvtx_sigma, P.sigma_y, P.sigma_z = zvtx_sigma, sigma_y, sigma_z
     P.noise_frac, P.bz, P.vdrift, P.t_window = noise_frac, bz, vdrift, t_window
     P.nthreads = nthreads or max(1, min(32, os.cpu_count() or 1))
+    P.angular_errors = int(angular_errors)
+    P.row_drop = row_drop
     n = ctypes.c_int64()
     nt = ctypes.c_int64()
     h = lib.o2gen_run(ctypes.byref(P), ctypes.byref(n), ctypes.byref(nt))

@@ -78,6 +78,8 @@ typedef struct {
   double vdrift;           /* cm/us */
   double t_window;         /* us: clusters with time outside [0, t_window) are dropped */
   int32_t nthreads;
+  int32_t angular_errors;  /* 1: smearing grows with the crossing angles (pad-length term) */
+  double row_drop;         /* probability that a track's cluster on a row is lost */
 } gen_params;
 
 typedef struct {
@@ -156,36 +158,48 @@ static void g_track(g_state* S, int32_t coll, int32_t it, int64_t gid, g_buf* ou
     double phil0 = phi0 - a;
     for (int r = 0; r < G_NROW; ++r) {
       double xr = S->rowx[r];
-      double s_arc, yl;
+      double s_arc, yl, snp;
       if (straight) {
         double c = cos(phil0);
         if (c <= 0) continue;
         s_arc = xr / c;
         yl = s_arc * sin(phil0);
+        snp = sin(phil0);
       } else {
         double xc = cx * ca + cy * sa, yc = -cx * sa + cy * ca;
         double v = (xr - xc) / (h * Rc);
         if (v < -1.0 || v > 1.0) continue;
         double cand[2] = {asin(v), G_PI - asin(v)};
-        double best = -1.0, besty = 0.0;
+        double best = -1.0, besty = 0.0, bests = 0.0;
         for (int k = 0; k < 2; ++k) {
           double sa_ = h * Rc * (cand[k] - phil0);
           double per = 2.0 * G_PI * Rc;
           sa_ = fmod(sa_, per);
           if (sa_ < 0) sa_ += per;
           if (sa_ <= 0.0 || sa_ > G_PI * Rc) continue;
-          if (best < 0 || sa_ < best) { best = sa_; besty = yc - h * Rc * cos(cand[k]); }
+          if (best < 0 || sa_ < best) { best = sa_; besty = yc - h * Rc * cos(cand[k]); bests = sin(cand[k]); }
         }
         if (best < 0) continue;
-        s_arc = best; yl = besty;
+        s_arc = best; yl = besty; snp = bests;
       }
       double z = zv + s_arc * tanl;
       if (fabs(z) >= G_DRIFT_LEN) continue;
       int side_c = (z < 0);
       int sec = j + (side_c ? 18 : 0);
       if (P->sector_only >= 0 && sec != P->sector_only) continue;
-      double ys = yl + P->sigma_y * g_gauss(&R);
-      double zs = z + P->sigma_z * g_gauss(&R);
+      double sy = P->sigma_y, sz = P->sigma_z;
+      if (P->angular_errors) {
+        /* the pad-length term of the cluster errors: (L tan)^2 / 12 with L
+         * the row pitch, tan(phi) of the crossing in the sector frame and
+         * tan(lambda) of the track */
+        const double l2 = (160.0 / 151.0) * (160.0 / 151.0) / 12.0;
+        double s2 = snp * snp;
+        sy = sqrt(sy * sy + l2 * (s2 < 1.0 ? s2 / (1.0 - s2) : 1e6));
+        sz = sqrt(sz * sz + l2 * tanl * tanl);
+      }
+      double ys = yl + sy * g_gauss(&R);
+      double zs = z + sz * g_gauss(&R);
+      if (P->row_drop > 0.0 && g_uni(&R) < P->row_drop) continue;
       int np = S->npads[r];
       double pad = rint((ys + 0.2 * np) * 160.0);
       if (pad < 0 || pad > 64.0 * np - 1) continue;
