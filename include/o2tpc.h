@@ -91,6 +91,24 @@ enum {
                                        tracklets, sector tracks, pairs): batches
                                        overflow and rerun on the regular path
                                        (testing aid)                           */
+  O2TPC_FLAG_COOP_SEARCH = 1u << 6, /* following passes of the tracklet
+                                       constructor: the candidate hits of all
+                                       lanes' row windows scanned together by
+                                       the warp, instead of each lane scanning
+                                       its own (identical results)             */
+  O2TPC_FLAG_ROW_STEP2 = 1u << 7,  /* NeighboursFinder: a hit without an accepted
+                                       pair on the adjacent rows may link across
+                                       one missing pad row (rows r + a, r - b,
+                                       (a, b) in {(2,1), (1,2), (2,2)}, residual
+                                       (a + b) h - b u - a d, its chi2 scaled by
+                                       6 / ((a + b)^2 + a^2 + b^2)).  A reading:
+                                       the paper only asks for robustness at
+                                       five-fold occupancy (Sec. 2.3)          */
+  O2TPC_FLAG_ANGULAR_ERRORS = 1u << 8, /* cluster errors grow with the track
+                                       angles: variances + (L tan phi)^2 / 12 in
+                                       y and (L tan lambda)^2 / 12 in zeta, L the
+                                       pad length 160/151 cm, at the predicted
+                                       state (a reading, as above)             */
   O2TPC_FLAG_COMPRESS = 1u << 5     /* also build each TF's compressed form
                                        (o2tpc_result.ctf; Sec. 2.2: clusters of
                                        tracks with pT < 0.1 GeV removed, a
@@ -150,6 +168,14 @@ typedef struct {
                                     choice per GPU model: read at o2tpc_create
                                     (a matching entry counts as tuned), written
                                     after tuning                                  */
+  uint32_t debug_inject;         /* fault injection for tests (0: none).  Bit 0:
+                                    the staged NeighboursFinder arms its slab
+                                    barrier but issues no copy, and its bounded
+                                    waits give up after 64 polls: every wait runs
+                                    out with nothing in flight, the blocks read
+                                    global memory instead (same links) and the
+                                    batch reports o2tpc_stats.events bit 0.  Takes
+                                    effect with nf_staged = 1, on the regular path */
 } o2tpc_config;
 
 /* Launch shapes in use and, once the autotuner has run, its timings (device
@@ -418,8 +444,16 @@ int o2tpc_get_tuning(o2tpc_ctx* ctx, o2tpc_tuning* out);
  * arguments or invalid cluster content), O2TPC_ETOOBIG, O2TPC_ECUDA.
  * The static arrays' device addresses are looked up during the first call on
  * each device (with that device current), so make that first call before any
- * stream capture.  Every call shares the arrays and leaves its contents in
- * them: calls that overlap on the GPU race and must be serialised. */
+ * stream capture.  With CUDA's lazy module loading (the default) that first
+ * call may also load the library's device code and reserve the ~6 MB of
+ * static storage at that moment: a caller with a fixed memory plan makes one
+ * call with n = 0 at start-up (or runs with CUDA_MODULE_LOADING=EAGER).  The
+ * looked-up addresses are kept for the life of the process and are not valid
+ * after a cudaDeviceReset.  Every call copies its small descriptors (the TF,
+ * its tiles, the geometry) from host memory and waits for its stream to
+ * finish before it returns.  Every call shares the arrays and leaves its
+ * contents in them: calls that overlap on the GPU race and must be
+ * serialised. */
 #define O2TPC_STATIC_MAX_CLUSTERS 262144
 int o2tpc_sort_tf_static(const o2tpc_tf* tf, double vdrift_cm_us, int32_t* sorted_orig, int32_t* sorted_yz,
                          int32_t* row_grid, int32_t* cell_start, uint64_t cell_capacity, void* stream);

@@ -60,9 +60,14 @@ constexpr int kSlabWaitLimit = 1 << 22;  // mbarrier polls before giving up on a
 
 __device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// Injected fault (o2tpc_config.debug_inject bit 0): the barrier is armed for
+// the slab bytes but no copy is issued, and the waits give up after this many
+// polls - a wait that runs out with nothing in flight.
+constexpr int kSlabWaitInjected = 64;
+
 // Waits (bounded) for phase 0 of the mbarrier; false if it did not complete.
-__device__ inline bool slab_wait(unsigned bar) {
-  for (int i = 0; i < kSlabWaitLimit; ++i) {
+__device__ inline bool slab_wait(unsigned bar, int limit) {
+  for (int i = 0; i < limit; ++i) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -94,7 +99,8 @@ __global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ g
                                                    const int* __restrict__ nfBlockStart, int nRows,
                                                    const int* __restrict__ cellStart, const int2* __restrict__ syz,
                                                    const GeomConst* __restrict__ G, int* __restrict__ upRaw,
-                                                   int* __restrict__ dnRaw, unsigned* __restrict__ err) {
+                                                   int* __restrict__ dnRaw, unsigned* __restrict__ err,
+                                                   unsigned inject) {
   if ((int)blockIdx.x >= nfBlockStart[nRows]) return;  // launched with an upper bound of blocks
   __shared__ __align__(16) int2 s_slab[kStage ? 2 : 1][kStage ? kSlab : 1];
   __shared__ __align__(8) unsigned long long s_bar;
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ g
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
         for (int side = 0; side < 2; ++side)
-          if (s_use[side])
+          if (s_use[side] && !(inject & 1u))
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                     smem_addr(&s_slab[side][0])),
@@ -158,6 +164,7 @@ __global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ g
     return;
   }
   const bool staged = kStage && (s_use[0] || s_use[1]);
+  const int waitLimit = (inject & 1u) ? kSlabWaitInjected : kSlabWaitLimit;
   bool slabOk = true;
   int bu = -1, bd = -1;
   if (valid) {
@@ -169,7 +176,7 @@ __global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ g
     const bool inWin = cell_range(gu, npu, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, uy0, uy1, uz0, uz1) &&
                        cell_range(gd, npd, yh - kWinY, yh + kWinY, zh - kWinZ, zh + kWinZ, dy0, dy1, dz0, dz1);
     if (staged) {
-      slabOk = slab_wait(bar);
+      slabOk = slab_wait(bar, waitLimit);
       if (!slabOk) atomicOr(err, kErrTimeout);
     }
     const int2* su = (staged && slabOk && s_use[0]) ? s_slab[0] : syz;
@@ -232,8 +239,86 @@ __global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ g
     dnRaw[h] = bd;
   }
   // a copy that did not complete in time must land before the block's shared
-  // memory is released
-  if (staged && threadIdx.x == 0) slab_wait(bar);
+  // memory is released: thread 0 waits once more (the copies are at most 16 KB
+  // of device memory, microseconds against a limit of seconds; with the
+  // injected fault nothing was issued, so nothing can land later)
+  if (staged && threadIdx.x == 0) slab_wait(bar, waitLimit);
+}
+
+// K4b (row step 2, optional): a hit with no accepted pair on the adjacent
+// rows may link across one missing row - up on row r + a, down on row r - b,
+// (a, b) in {(2,1), (1,2), (2,2)} - with the residual (a + b) h - b u - a d,
+// whose variance is f = (a + b)^2 + a^2 + b^2 times a cluster's, so the
+// metric D = 2077 e_y^2 + 1536 e_zeta^2 scaled by 6 / f is the same 2-dof
+// chi2 (accepted if 6 D <= kMaxMetric f); windows scale with the row
+// distance.  The best pair minimises D / f (compared exactly as
+// D1 f2 < D2 f1 in 64 bits), ties to the smaller u, then d.  One thread per
+// hit; hits that found an adjacent-row pair return at once.
+__global__ void k_neighbours_gap(const int* __restrict__ nDev, const RowGrid* __restrict__ grid, int nRows,
+                                 const int* __restrict__ cellStart, const int2* __restrict__ syz,
+                                 const GeomConst* __restrict__ G, int* __restrict__ upRaw,
+                                 int* __restrict__ dnRaw) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= *nDev || upRaw[h] >= 0) return;
+  int lo = 0, hi = nRows;  // row of h: the last row starting at or before it
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (grid[m].start <= h) lo = m + 1;
+    else hi = m;
+  }
+  const int R = lo - 1;
+  const int r = (R % kRowsPerTF) % kNRow;
+  if (r < 1 || r > kNRow - 2) return;
+  const int2 hh = syz[h];
+  const int yh = hh.x, zh = hh.y;
+  long long bD = -1, bf = 1;
+  int bu = -1, bd = -1;
+  constexpr int kSteps[3][2] = {{2, 1}, {1, 2}, {2, 2}};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int a = kSteps[q][0], b = kSteps[q][1];
+    if (r + a > kNRow - 1 || r - b < 0) continue;
+    const RowGrid gu = grid[R + a], gd = grid[R - b];
+    int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
+    if (!cell_range(gu, G->npads[r + a], yh - a * kWinY, yh + a * kWinY, zh - a * kWinZ, zh + a * kWinZ, uy0, uy1,
+                    uz0, uz1))
+      continue;
+    if (!cell_range(gd, G->npads[r - b], yh - b * kWinY, yh + b * kWinY, zh - b * kWinZ, zh + b * kWinZ, dy0, dy1,
+                    dz0, dz1))
+      continue;
+    const long long f = (long long)((a + b) * (a + b) + a * a + b * b);
+    for (int izu = uz0; izu <= uz1; ++izu) {
+      const int ua = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy0);
+      const int ub = __ldg(cellStart + gu.cellBase + izu * gu.ny + uy1 + 1);
+      for (int u = ua; u < ub; ++u) {
+        const int2 pu = __ldg(syz + u);
+        if (abs(pu.x - yh) > a * kWinY || abs(pu.y - zh) > a * kWinZ) continue;
+        for (int izd = dz0; izd <= dz1; ++izd) {
+          const int da = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy0);
+          const int db = __ldg(cellStart + gd.cellBase + izd * gd.ny + dy1 + 1);
+          for (int d = da; d < db; ++d) {
+            const int2 pd = __ldg(syz + d);
+            if (abs(pd.x - yh) > b * kWinY || abs(pd.y - zh) > b * kWinZ) continue;
+            const long long ey = (long long)(a + b) * yh - (long long)b * pu.x - (long long)a * pd.x;
+            const long long ez = (long long)(a + b) * zh - (long long)b * pu.y - (long long)a * pd.y;
+            const long long D = (long long)kWeightY * ey * ey + (long long)kWeightZ * ez * ez;
+            if (6 * D > (long long)kMaxMetric * f) continue;
+            const bool better = bu < 0 || D * bf < bD * f || (D * bf == bD * f && (u < bu || (u == bu && d < bd)));
+            if (better) {
+              bD = D;
+              bf = f;
+              bu = u;
+              bd = d;
+            }
+          }
+        }
+      }
+    }
+  }
+  if (bu >= 0) {
+    upRaw[h] = bu;
+    dnRaw[h] = bd;
+  }
 }
 
 // K5 + K6a: reciprocity filter on the raw (snapshot) links and the chain-head
@@ -428,10 +513,10 @@ void launch_lower_bounds(const int* list, const int* nListDev, const int* keys, 
 
 void launch_neighbours(int nfBlocks, int hitsPerBlock, bool stage, const RowGrid* grid, const int* nfBlockStart,
                        int nRows, const int* cellStart, const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw,
-                       unsigned* err, cudaStream_t st) {
+                       unsigned* err, cudaStream_t st, unsigned inject) {
   if (nfBlocks > 0) {
 #define O2TPC_NF(B, S) \
-  k_neighbours<B, S><<<nfBlocks, B, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw, err)
+  k_neighbours<B, S><<<nfBlocks, B, 0, st>>>(grid, nfBlockStart, nRows, cellStart, syz, G, upRaw, dnRaw, err, inject)
     if (hitsPerBlock == 64) {
       if (stage) O2TPC_NF(64, true);
       else O2TPC_NF(64, false);
@@ -443,6 +528,14 @@ void launch_neighbours(int nfBlocks, int hitsPerBlock, bool stage, const RowGrid
       else O2TPC_NF(128, false);
     }
 #undef O2TPC_NF
+    ++g_launch_count;
+  }
+}
+
+void launch_neighbours_gap(int n, const int* nDev, const RowGrid* grid, int nRows, const int* cellStart,
+                           const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw, cudaStream_t st) {
+  if (n > 0) {
+    k_neighbours_gap<<<(n + 127) / 128, 128, 0, st>>>(nDev, grid, nRows, cellStart, syz, G, upRaw, dnRaw);
     ++g_launch_count;
   }
 }

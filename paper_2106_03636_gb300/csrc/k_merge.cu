@@ -328,9 +328,13 @@ __global__ void k_chain_counts(const int* __restrict__ nHeadsDev, const int* __r
 // Inward refit over a chain of sector tracks from its tail (the last of at
 // most kMaxChain segments) back to its head through the prev links, hits of
 // each segment descending in rows, in precision T.  y is kept relative to
-// the origin yref (integer units, the first hit fitted in the current sector
-// frame); at a sector boundary the state is made absolute, rotated, and
-// re-referenced to the next hit.  Returns flags bits 2 (stopped at a
+// the origin yref (integer units), moved in whole centimetres to each hit
+// before its update, and zeta relative to the hit itself (recentre_z; zeta
+// is put back relative to zref at the end); at a sector boundary the state is
+// made absolute,
+// rotated, and re-referenced to the next hit.  Steps between pad rows come
+// from the row pitch; the first step after a rotation (x off the rows) from
+// the positions.  Returns flags bits 2 (stopped at a
 // boundary) and 8 (FP32 covariance lost positive definiteness); yref of the
 // final state in *yrefOut.
 template <typename T>
@@ -348,7 +352,10 @@ __device__ int refit_chain(int head, int tail, const SectorTrackBufs& sb, const 
   const int2 pl = sb.yz[hl];
   int yref = pl.x;
   const T xl = sizeof(T) == 8 ? (T)G->rowx_d[sb.rows[hl]] : (T)G->rowx[sb.rows[hl]];
-  kf_reset<T>(t, xl, T(0), (T)(pl.y - zref) * zunit, (T)so[3], (T)so[4], (T)so[5]);
+  kf_reset<T>(t, xl, T(0), T(0), (T)so[3], (T)so[4], (T)so[5]);  // at the last hit: the origins
+  kf_meas_cov<T>(t, G->angErr);
+  int srow = sb.rows[hl];  // row of the state, -1 after a rotation
+  int zcur = pl.y;         // drift origin of the fit, moved to each hit
   chi2 = T(0);
   used = 1;
   int flags = 0;
@@ -364,23 +371,36 @@ __device__ int refit_chain(int head, int tail, const SectorTrackBufs& sb, const 
         t.p[0] += (T)yref * yunit;
         if (kf_rotate<T>(t, rc, sgn * rs, bzc) != 0) {
           t.p[0] -= (T)yref * yunit;
+          t.p[1] += (T)(zcur - zref) * zunit;
           *yrefOut = yref;
           return flags | 4;
         }
         yref = p.x;
         t.p[0] -= (T)yref * yunit;
         frame = sec;
+        srow = -1;
       }
-      const T xr = sizeof(T) == 8 ? (T)G->rowx_d[sb.rows[i]] : (T)G->rowx[sb.rows[i]];
-      if (kf_prop<T>(t, xr, bzc) != 0) continue;
+      const int ri = sb.rows[i];
+      if constexpr (sizeof(T) == 8) {  // FP64 fallback: single-precision geometry, double covariance
+        const float dx = srow >= 0 ? (float)(ri - srow) * G->pitch : (float)(G->rowx_d[ri] - (double)t.x);
+        if (kf_prop_dx_cov64(t, G->rowx_d[ri], dx, G->bzc) != 0) continue;
+      } else if (srow >= 0) {
+        if (kf_prop_row<T>(t, srow, ri, G, bzc) != 0) continue;
+      } else {
+        if (kf_prop<T>(t, (T)G->rowx[ri], bzc) != 0) continue;
+      }
+      srow = ri;
+      recentre_y<T>(t.p[0], yref, p.x);
+      recentre_z<T>(t.p[1], zcur, p.y, zunit);
       T c2;
-      if (kf_update<T>(t, (T)(p.x - yref) * yunit, (T)(p.y - zref) * zunit, &c2) != 0) continue;
+      if (kf_update<T>(t, (T)(p.x - yref) * yunit, T(0), &c2, G->angErr) != 0) continue;
       chi2 += c2;
       ++used;
       if (!kf_cov_ok<T>(t.C)) flags |= 8;
     }
     if (sg == head) break;
   }
+  t.p[1] += (T)(zcur - zref) * zunit;  // zeta back to the track's origin
   *yrefOut = yref;
   return flags;
 }
@@ -463,7 +483,9 @@ __global__ void __launch_bounds__(128) k_final_refit(const int* __restrict__ nHe
   write_track<float>(t, sf, yref, c2f, used, frame, (nseg > 1 ? 2 : 0) | (fl & 4), zref, G, ob);
 }
 
-// K11b: the queued tracks again with an FP64 covariance (flag bit 1).
+// K11b: the queued tracks again with an FP64 covariance (flag bit 1): the
+// state and its covariance in double, each transport step's geometry in
+// single precision (kf_prop_dx_cov64).
 __global__ void __launch_bounds__(128) k_final_refit64(const int* __restrict__ heads, SectorTrackBufs sb, MergeBufs mb,
                                                        const int2* __restrict__ syz, const GeomConst* __restrict__ G,
                                                        OutBufs ob) {

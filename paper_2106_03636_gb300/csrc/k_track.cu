@@ -32,55 +32,19 @@ __device__ inline int find_row(const RowGrid* __restrict__ grid, int nRows, int 
   return lo - 1;
 }
 
-__device__ inline int clamp_i(float v) { return (int)fminf(fmaxf(v, -1.0e9f), 1.0e9f); }
-
-// Best hit of a row inside the +-3 sigma window of the prediction (ties: the
-// smaller sorted index); -1 if none has chi2 <= kChi2Follow.  The best hit's
-// coordinates come back in *pbest.
-__device__ int search_row(const RowGrid& g, int npads, const int* __restrict__ cellStart,
-                          const int2* __restrict__ syz, const KState<float>& s, int yref, int zref,
-                          float zunit, float izunit, int2* pbest) {
-  if (g.count == 0) return -1;
-  const float sy2 = s.C[0] + kSigY * kSigY, sz2 = s.C[2] + kSigZ * kSigZ;
-  const float wy = 3.f * sqrtf(sy2), wz = 3.f * sqrtf(sz2);
-  if (!(wy < 1e4f) || !(wz < 1e4f) || !isfinite(s.p[0]) || !isfinite(s.p[1])) return -1;
-  // the cell rectangle only has to cover the window: one unit of slack on
-  // each side absorbs the rounding of the float products
-  const int ylo = yref + clamp_i(floorf((s.p[0] - wy) * 160.f)) - 1;
-  const int yhi = yref + clamp_i(ceilf((s.p[0] + wy) * 160.f)) + 1;
-  const int zlo = zref + clamp_i(floorf((s.p[1] - wz) * izunit)) - 1;
-  const int zhi = zref + clamp_i(ceilf((s.p[1] + wz) * izunit)) + 1;
-  int iy0, iy1, iz0, iz1;
-  if (!cell_range(g, npads, ylo, yhi, zlo, zhi, iy0, iy1, iz0, iz1)) return -1;
-  const float isy2 = 1.f / sy2, isz2 = 1.f / sz2;
-  int best = -1;
-  float bchi = 0.f;
-  int2 bp = make_int2(0, 0);
-  for (int iz = iz0; iz <= iz1; ++iz) {
-    const int a = __ldg(cellStart + g.cellBase + iz * g.ny + iy0);
-    const int b = __ldg(cellStart + g.cellBase + iz * g.ny + iy1 + 1);
-    for (int h = a; h < b; ++h) {
-      const int2 p = __ldg(syz + h);
-      const float dy = hit_y(p.x, yref) - s.p[0], dz = hit_z(p.y, zref, zunit) - s.p[1];
-      if (fabsf(dy) > wy || fabsf(dz) > wz) continue;
-      const float chi = dy * dy * isy2 + dz * dz * isz2;
-      if (chi > kChi2Follow) continue;
-      if (best < 0 || chi < bchi || (chi == bchi && h < best)) {
-        best = h;
-        bchi = chi;
-        bp = p;
-      }
-    }
-  }
-  *pbest = bp;
-  return best;
+// Row of hit h linked up from a hit on row R: R + 1, or R + 2 when the link
+// crosses a missing row (row step 2).
+__device__ inline int link_row(const RowGrid* __restrict__ grid, int R, int h) {
+  const RowGrid g = grid[R + 1];
+  return h < g.start + g.count ? R + 1 : R + 2;
 }
 
-__device__ inline void reset_cov(KState<float>& s) {
+__device__ inline int clamp_i(float v) { return (int)fminf(fmaxf(v, -1.0e9f), 1.0e9f); }
+
+__device__ inline void reset_cov(KState<float>& s, int angErr) {
 #pragma unroll
   for (int i = 0; i < 15; ++i) s.C[i] = 0.f;
-  s.C[0] = kSigY * kSigY;
-  s.C[2] = kSigZ * kSigZ;
+  kf_meas_cov<float>(s, angErr);
   s.C[5] = 0.04f;
   s.C[9] = 0.25f;
   s.C[14] = 400.f;
@@ -122,70 +86,331 @@ __device__ inline void load_state(KState<float>& s, const float* src) {
 // tb.nasc and its row base in tb.rbase; tb.nhits is written by the last pass
 // (0: dropped).  Results do not depend on which thread builds which tracklet.
 
+// Lanes with want = true take consecutive work items from *counter, one
+// atomic per warp; returns this lane's item (meaningful where want).  All 32
+// lanes must call it.
+__device__ inline int warp_take(int* counter, bool want) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(full, want);
+  int base = 0;
+  if (m) {
+    const int leader = __ffs(m) - 1;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(full, base, leader);
+  }
+  return base + __popc(m & ((1u << lane) - 1u));
+}
+
 // (a) chain fit: seed from the first and third chain hits, then one update
-// per chain hit.  A transport failure drops the tracklet.
+// per chain hit.  A transport failure drops the tracklet.  Every iteration of
+// the loop is one chain hit of every busy lane; a lane whose chain ends takes
+// the next tracklet.
 __global__ void __launch_bounds__(128) k_tl_chain(const int* __restrict__ nTlDev, int* __restrict__ counter, const int* __restrict__ starts,
                                                   const int* __restrict__ up, const RowGrid* __restrict__ grid,
                                                   int nRows, const int2* __restrict__ syz,
                                                   const GeomConst* __restrict__ G, TrackletBufs tb) {
+  const unsigned full = 0xffffffffu;
   const float zunit = G->zunit, bzc = G->bzc;
   const int nTl = *nTlDev;
+  bool have = false, exhausted = false;
+  int k = 0, nc = 0, hit = -1, prev = 0, Rh = 0, R0 = 0, r0 = 0, yref = 0, zref = 0;
+  KState<float> st;
   for (;;) {
-    const int k = atomicAdd(counter, 1);
-    if (k >= nTl) return;
-    const int h0 = starts[k];
-    const int R0 = find_row(grid, nRows, h0);
-    const int r0 = (R0 % kRowsPerTF) % kNRow;
-    int* H = tb.hits + (size_t)k * kMaxTlHits;
-    uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
-    const int2 a0 = syz[h0];
-    const int zref = a0.y, yref = a0.x;
-    tb.zref[k] = zref;
-    tb.rbase[k] = R0 - r0;
-    const int h1 = up[h0];
-    const int2 a2 = syz[up[h1]];
-    const float x0 = G->rowx[r0], x2 = G->rowx[r0 + 2];
-    const float dx = x2 - x0, dy = hit_y(a2.x, yref) - hit_y(a0.x, yref);
-    const float tphi = dy / dx;
-    const float s0 = tphi / sqrtf(1.f + tphi * tphi);
-    const float t0 = (hit_z(a2.y, zref, zunit) - hit_z(a0.y, zref, zunit)) / sqrtf(dx * dx + dy * dy);
-    KState<float> st;
-    kf_reset<float>(st, x0, hit_y(a0.x, yref), hit_z(a0.y, zref, zunit), s0, t0, 0.f);
-    H[0] = h0;
-    Rw[0] = (uint8_t)r0;
-    int nc = 1, hit = h1;
-    bool dropped = false;
-    while (hit >= 0 && nc < kNRow - r0) {
-      const int row = r0 + nc;
-      const int2 hp = syz[hit];  // both loads in flight during the transport
-      const int next = up[hit];
-      if (kf_prop<float>(st, G->rowx[row], bzc) != 0) {
-        dropped = true;
-        break;
+    const bool want = !have && !exhausted;
+    const int kk = warp_take(counter, want);
+    if (want) {
+      if (kk >= nTl) {
+        exhausted = true;
+      } else {
+        k = kk;
+        const int h0 = starts[k];
+        R0 = find_row(grid, nRows, h0);
+        r0 = (R0 % kRowsPerTF) % kNRow;
+        const int2 a0 = syz[h0];
+        zref = a0.y;
+        yref = a0.x;
+        tb.zref[k] = zref;
+        tb.rbase[k] = R0 - r0;
+        const int h1 = up[h0];
+        const int R1 = link_row(grid, R0, h1);
+        const int h2 = up[h1];
+        const int R2 = link_row(grid, R1, h2);
+        const int2 a2 = syz[h2];
+        const float x0 = G->rowx[r0];
+        const float dx = (float)(R2 - R0) * G->pitch, dy = hit_y(a2.x, yref) - hit_y(a0.x, yref);
+        const float tphi = dy / dx;
+        const float s0 = tphi / sqrtf(1.f + tphi * tphi);
+        const float t0 = (hit_z(a2.y, zref, zunit) - hit_z(a0.y, zref, zunit)) / sqrtf(dx * dx + dy * dy);
+        kf_reset<float>(st, x0, hit_y(a0.x, yref), hit_z(a0.y, zref, zunit), s0, t0, 0.f);
+        kf_meas_cov<float>(st, G->angErr);
+        tb.hits[(size_t)k * kMaxTlHits] = h0;
+        tb.rows[(size_t)k * kMaxTlHits] = (uint8_t)r0;
+        nc = 1;
+        hit = h1;
+        prev = r0;
+        Rh = R1;
+        have = true;
       }
-      kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr);
-      H[nc] = hit;
-      Rw[nc] = (uint8_t)row;
-      ++nc;
-      hit = next;
     }
-    tb.nasc[k] = dropped ? 0 : nc;
-    if (dropped) tb.nhits[k] = 0;
-    else store_raw(tb.state + (size_t)k * 21, st);
+    if (__ballot_sync(full, have) == 0) {
+      if (__all_sync(full, exhausted)) break;
+      continue;
+    }
+    if (!have) continue;
+    if (hit < 0 || nc >= kMaxTlHits) {  // the chain is fitted
+      tb.nasc[k] = nc;
+      tb.yref[k] = yref;
+      store_raw(tb.state + (size_t)k * 21, st);
+      have = false;
+      continue;
+    }
+    const int row = r0 + (Rh - R0);
+    const int2 hp = syz[hit];  // both loads in flight during the transport
+    const int next = up[hit];
+    if (kf_prop_row<float>(st, prev, row, G, bzc) != 0) {
+      tb.nasc[k] = 0;
+      tb.yref[k] = yref;
+      tb.nhits[k] = 0;
+      have = false;
+      continue;
+    }
+    recentre_y(st.p[0], yref, hp.x);
+    kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr, G->angErr);
+    tb.hits[(size_t)k * kMaxTlHits + nc] = hit;
+    tb.rows[(size_t)k * kMaxTlHits + nc] = (uint8_t)row;
+    ++nc;
+    prev = row;
+    hit = next;
+    if (hit >= 0) Rh = link_row(grid, Rh, hit);
   }
 }
 
-// Following (passes b and d): from row r in steps of dir, transport, search
-// the +-3 sigma window, update with the best hit; stop after kMaxMiss rows
-// without a hit, at the row range end, on a transport failure or when
-// |sin phi| > kSinFollow.  The state after the last accepted hit is kept in
-// shared memory (one column per thread) and returned in st.  Appends the
-// hits at H[n..]; returns the new count.
+// (c) inward refit from the top hit through every attached hit; a hit whose
+// transport fails is skipped.  One attached hit of every busy lane per
+// iteration, as in (a).
+__global__ void __launch_bounds__(128) k_tl_refit(const int* __restrict__ nTlDev, int* __restrict__ counter, const int2* __restrict__ syz,
+                                                  const GeomConst* __restrict__ G, TrackletBufs tb) {
+  const unsigned full = 0xffffffffu;
+  const float zunit = G->zunit, bzc = G->bzc;
+  const int nTl = *nTlDev;
+  bool have = false, exhausted = false;
+  int k = 0, i = 0, srow = 0, yref = 0, zref = 0;
+  KState<float> st;
+  for (;;) {
+    const bool want = !have && !exhausted;
+    const int kk = warp_take(counter, want);
+    if (want) {
+      if (kk >= nTl) {
+        exhausted = true;
+      } else {
+        const int na = tb.nasc[kk];
+        if (na > 0) {
+          k = kk;
+          zref = tb.zref[k];
+          yref = tb.yref[k];
+          load_state(st, tb.state + (size_t)k * 21);
+          srow = tb.rows[(size_t)k * kMaxTlHits + na - 1];
+          i = na - 2;
+          have = true;
+        }
+      }
+    }
+    if (__ballot_sync(full, have) == 0) {
+      if (__all_sync(full, exhausted)) break;
+      continue;
+    }
+    if (!have) continue;
+    if (i < 0) {
+      tb.yref[k] = yref;
+      store_raw(tb.state + (size_t)k * 21, st);
+      have = false;
+      continue;
+    }
+    const int2 hp = syz[tb.hits[(size_t)k * kMaxTlHits + i]];
+    const int row = tb.rows[(size_t)k * kMaxTlHits + i];
+    --i;
+    if (kf_prop_row<float>(st, srow, row, G, bzc) != 0) continue;
+    srow = row;
+    recentre_y(st.p[0], yref, hp.x);
+    kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr, G->angErr);
+  }
+}
+
+// --------------------------------------------- following (passes b, d)
+// From the row after the chain's top (b, outward) or below its start (d,
+// inward), one pad row per step: transport, search the +-3 sigma window of
+// the prediction, update with the best hit; stop after kMaxMiss rows without
+// a hit, at the row range end, on a transport failure or when |sin phi| >
+// kSinFollow.  The state after the last accepted hit is kept (shared memory)
+// and is the pass's result.
+//
+// One persistent kernel per direction, written as one loop in which every
+// iteration is one row step of every busy lane: a lane whose tracklet ends
+// takes the next one (one atomic per warp for all such lanes), so the
+// transport and the update run converged whatever the tracklets' lengths.
+// The row search comes in two forms that pick the same hit:
+// * per lane: each lane scans the candidate cells of its own window;
+// * warp-cooperative: the candidates of all lanes' windows on this step are
+//   laid out one after another and scanned 32 at a time by the whole warp
+//   (a lane finds the owner of candidate q by a binary search over the
+//   warp's exclusive candidate offsets; per owner the smallest key wins).
+// Both score a candidate by the same explicitly rounded expression and keep
+// the smallest (chi2 bits << 32 | hit) - chi2 >= 0, so its bit pattern orders
+// like its value - which is the rule "smallest chi2, then the smaller
+// sorted index".
+
+struct SearchPar {
+  float y, z, wy, wz, isy2, isz2;
+  int yref, zref;
+};
+
+// Window of a row search; false: no candidate can pass (empty row, unusable
+// window).  The cell rectangle only has to cover the window: one unit of
+// slack on each side absorbs the rounding of the float products.
+__device__ inline bool search_window(const RowGrid& g, int npads, const KState<float>& s, int yref, int zref,
+                                     float izunit, int angErr, SearchPar& P, int& iy0, int& iy1, int& iz0,
+                                     int& iz1) {
+  if (g.count == 0) return false;
+  float vy, vz;
+  meas_var<float>(angErr, s, vy, vz);
+  const float sy2 = s.C[0] + vy, sz2 = s.C[2] + vz;
+  const float wy = 3.f * sqrtf(sy2), wz = 3.f * sqrtf(sz2);
+  if (!(wy < 1e4f) || !(wz < 1e4f) || !isfinite(s.p[0]) || !isfinite(s.p[1])) return false;
+  const int ylo = yref + clamp_i(floorf((s.p[0] - wy) * 160.f)) - 1;
+  const int yhi = yref + clamp_i(ceilf((s.p[0] + wy) * 160.f)) + 1;
+  const int zlo = zref + clamp_i(floorf((s.p[1] - wz) * izunit)) - 1;
+  const int zhi = zref + clamp_i(ceilf((s.p[1] + wz) * izunit)) + 1;
+  if (!cell_range(g, npads, ylo, yhi, zlo, zhi, iy0, iy1, iz0, iz1)) return false;
+  P.y = s.p[0];
+  P.z = s.p[1];
+  P.wy = wy;
+  P.wz = wz;
+  P.isy2 = 1.f / sy2;
+  P.isz2 = 1.f / sz2;
+  P.yref = yref;
+  P.zref = zref;
+  return true;
+}
+
+constexpr unsigned long long kNoHit = ~0ull;
+
+// Key of candidate hit h at p against window P, or kNoHit if it fails the
+// window or the chi2 cut.  Every operation is rounded explicitly, so the key
+// is the same number wherever this is inlined.
+__device__ inline unsigned long long cand_key(int h, int2 p, const SearchPar& P, float zunit) {
+  const float dy = __fsub_rn(__fmul_rn((float)(p.x - P.yref), 0.00625f), P.y);
+  const float dz = __fsub_rn(__fmul_rn((float)(p.y - P.zref), zunit), P.z);
+  if (fabsf(dy) > P.wy || fabsf(dz) > P.wz) return kNoHit;
+  const float chi = __fadd_rn(__fmul_rn(__fmul_rn(dy, dy), P.isy2), __fmul_rn(__fmul_rn(dz, dz), P.isz2));
+  if (chi > kChi2Follow) return kNoHit;
+  return ((unsigned long long)__float_as_uint(chi) << 32) | (unsigned)h;
+}
+
+// Per-lane search: cell rows [iz0, iz0 + nseg) x columns [iy0, iy1].
+__device__ inline unsigned long long lane_search(int nseg, int cellBase, int ny, int iy0, int iy1, int iz0,
+                                                 const int* __restrict__ cellStart, const int2* __restrict__ syz,
+                                                 const SearchPar& P, float zunit) {
+  unsigned long long best = kNoHit;
+  for (int j = 0; j < nseg; ++j) {
+    const int cb = cellBase + (iz0 + j) * ny;
+    const int a = __ldg(cellStart + cb + iy0);
+    const int b = __ldg(cellStart + cb + iy1 + 1);
+    for (int h = a; h < b; ++h) {
+      const unsigned long long key = cand_key(h, __ldg(syz + h), P, zunit);
+      if (key < best) best = key;
+    }
+  }
+  return best;
+}
+
+// Warp-cooperative search.  Lane l searches cell rows [iz0, iz0 + nseg) x
+// columns [iy0, iy1] of its window sp[l] when nseg > 0; returns its best key.
+// All 32 lanes must call it.  sp / sbest: this warp's 32 slots.
+__device__ inline unsigned long long coop_search(int nseg, int cellBase, int ny, int iy0, int iy1, int iz0,
+                                                 const int* __restrict__ cellStart, const int2* __restrict__ syz,
+                                                 const SearchPar* sp, unsigned long long* sbest, float zunit) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  sbest[lane] = kNoHit;
+  const int maxseg = (int)__reduce_max_sync(full, (unsigned)nseg);
+  __syncwarp();
+  for (int j = 0; j < maxseg; ++j) {
+    int a = 0, c = 0;
+    if (j < nseg) {
+      const int cb = cellBase + (iz0 + j) * ny;
+      a = __ldg(cellStart + cb + iy0);
+      c = __ldg(cellStart + cb + iy1 + 1) - a;
+    }
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(full, inc, o);
+      if (lane >= o) inc += v;
+    }
+    const int total = __shfl_sync(full, inc, 31);
+    const int exc = inc - c;
+    for (int base = 0; base < total; base += 32) {
+      const int q = base + lane;
+      // owner: the last lane whose candidates start at or before q
+      int own = 0, eown = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int e = __shfl_sync(full, exc, own + step);
+        if (e <= q) {
+          own += step;
+          eown = e;
+        }
+      }
+      const int aown = __shfl_sync(full, a, own);
+      unsigned long long key = kNoHit;
+      if (q < total) {
+        const int h = aown + (q - eown);
+        key = cand_key(h, __ldg(syz + h), sp[own], zunit);
+      } else {
+        own = 32;  // past the end: a run of its own
+      }
+      // minimum over each run of equal owners (the runs are contiguous)
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_down_sync(full, key, o);
+        const int ow = __shfl_down_sync(full, own, o);
+        if (lane + o < 32 && ow == own && v < key) key = v;
+      }
+      const int prevOwn = __shfl_up_sync(full, own, 1);
+      if (own < 32 && (lane == 0 || prevOwn != own) && key < sbest[own]) sbest[own] = key;
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  return sbest[lane];
+}
+
+// (b) kDir = +1: outward following above the chain; its result is the
+// inward refit's starting state: the last accepted state with the position
+// of the top hit and a fresh covariance.  (d) kDir = -1: inward following
+// below the chain start; the state kept is the one at the innermost accepted
+// hit.  coop: 1 warp-cooperative search, 0 per-lane search.
+// Blocks of 128 per SM the following kernels are compiled for: 7 (72
+// registers, no spills) measured 2 % faster over both passes on the full
+// Time Frame than 8 (64 registers, ~40 bytes of spills).
+#ifndef O2TPC_FOLLOW_MIN_BLOCKS
+#define O2TPC_FOLLOW_MIN_BLOCKS 7
+#endif
+
 template <int kDir>
-__device__ inline int follow(KState<float>& st, float (*s_last)[128], int r, int n, int* H, uint8_t* Rw, int* top,
-                             int Rs, int yref, int zref, const RowGrid* __restrict__ grid,
-                             const int* __restrict__ cellStart, const int2* __restrict__ syz,
-                             const GeomConst* __restrict__ G, float zunit, float izunit, float bzc) {
+__global__ void __launch_bounds__(128, O2TPC_FOLLOW_MIN_BLOCKS) k_tl_follow(const int* __restrict__ nTlDev, int* __restrict__ counter,
+                                                     const RowGrid* __restrict__ grid,
+                                                     const int* __restrict__ cellStart,
+                                                     const int2* __restrict__ syz,
+                                                     const GeomConst* __restrict__ G, TrackletBufs tb, int coop) {
+  __shared__ float s_last[21][128];
+  __shared__ SearchPar s_par[128];
+  __shared__ unsigned long long s_best[128];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wb = threadIdx.x & ~31;
+  const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
+  const int nTl = *nTlDev;
   auto save_last = [&](const KState<float>& q) {
     s_last[0][threadIdx.x] = q.x;
 #pragma unroll
@@ -193,124 +418,115 @@ __device__ inline int follow(KState<float>& st, float (*s_last)[128], int r, int
 #pragma unroll
     for (int j = 0; j < 15; ++j) s_last[6 + j][threadIdx.x] = q.C[j];
   };
-  save_last(st);
-  int misses = 0;
-  for (; kDir > 0 ? r < kNRow : r >= 0; r += kDir) {
-    if (kf_prop<float>(st, G->rowx[r], bzc) != 0 || fabsf(st.p[2]) > kSinFollow) break;
-    int2 hp;
-    const int hit = search_row(grid[Rs + r], G->npads[r], cellStart, syz, st, yref, zref, zunit, izunit, &hp);
-    if (hit >= 0) {
-      kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr);
-      H[n] = hit;
-      Rw[n] = (uint8_t)r;
-      ++n;
-      *top = hit;
-      save_last(st);
-      misses = 0;
-    } else if (++misses >= kMaxMiss) {
-      break;
+  bool have = false, exhausted = false;
+  int k = 0, r = 0, n = 0, misses = 0, srow = 0, yref = 0, yrefLast = 0, zref = 0, Rs = 0;
+  KState<float> st;
+  // ends the lane's tracklet with the state after its last accepted hit
+  auto finish = [&]() {
+    st.x = s_last[0][threadIdx.x];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) st.p[j] = s_last[1 + j][threadIdx.x];
+#pragma unroll
+    for (int j = 0; j < 15; ++j) st.C[j] = s_last[6 + j][threadIdx.x];
+    yref = yrefLast;
+    float* S = tb.state + (size_t)k * 21;
+    if (kDir > 0) {
+      const int2 p = syz[tb.hits[(size_t)k * kMaxTlHits + n - 1]];  // the top hit
+      recentre_y(st.p[0], yref, p.x);
+      st.p[0] = hit_y(p.x, yref);
+      st.p[1] = hit_z(p.y, zref, zunit);
+      reset_cov(st, G->angErr);
+      tb.nasc[k] = n;
+      tb.yref[k] = yref;
+      store_raw(S, st);
+    } else {
+      tb.nhits[k] = n;
+      store_state(S, st, yref);
+    }
+    have = false;
+  };
+  for (;;) {
+    // lanes without a tracklet take the next ones
+    const unsigned need = __ballot_sync(full, !have && !exhausted);
+    if (need) {
+      const int leader = __ffs(need) - 1;
+      int base = 0;
+      if (lane == leader) base = atomicAdd(counter, __popc(need));
+      base = __shfl_sync(full, base, leader);
+      if (!have && !exhausted) {
+        k = base + __popc(need & ((1u << lane) - 1));
+        if (k >= nTl) {
+          exhausted = true;
+        } else {
+          const int na = tb.nasc[k];
+          if (na > 0) {
+            const uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
+            Rs = tb.rbase[k];
+            zref = tb.zref[k];
+            yref = tb.yref[k];
+            load_state(st, tb.state + (size_t)k * 21);
+            n = na;
+            r = (kDir > 0) ? Rw[na - 1] + 1 : Rw[0] - 1;
+            misses = 0;
+            srow = row_of_x(st.x);
+            save_last(st);
+            yrefLast = yref;
+            have = true;
+          }
+        }
+      }
+    }
+    if (__ballot_sync(full, have) == 0) {
+      if (__all_sync(full, exhausted)) break;
+      continue;
+    }
+    // one row step of every busy lane: transport, then the window
+    int nseg = 0, cellBase = 0, ny = 0, iy0 = 0, iy1 = 0, iz0 = 0, iz1 = 0;
+    SearchPar P;
+    if (have) {
+      if ((kDir > 0) ? (r >= kNRow) : (r < 0)) {
+        finish();
+      } else if (kf_prop_row<float>(st, srow, r, G, bzc) != 0 || fabsf(st.p[2]) > kSinFollow) {
+        finish();
+      } else {
+        srow = r;
+        const RowGrid g = grid[Rs + r];
+        if (search_window(g, G->npads[r], st, yref, zref, izunit, G->angErr, P, iy0, iy1, iz0, iz1)) {
+          nseg = iz1 - iz0 + 1;
+          cellBase = g.cellBase;
+          ny = g.ny;
+        }
+      }
+    }
+    unsigned long long best;
+    if (coop) {
+      if (nseg > 0) s_par[threadIdx.x] = P;
+      __syncwarp();
+      best = coop_search(nseg, cellBase, ny, iy0, iy1, iz0, cellStart, syz, s_par + wb, s_best + wb, zunit);
+    } else {
+      best = lane_search(nseg, cellBase, ny, iy0, iy1, iz0, cellStart, syz, P, zunit);
+    }
+    if (have) {
+      if (best != kNoHit) {
+        const int hit = (int)(unsigned)(best & 0xffffffffull);
+        const int2 hp = syz[hit];
+        recentre_y(st.p[0], yref, hp.x);
+        kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr, G->angErr);
+        tb.hits[(size_t)k * kMaxTlHits + n] = hit;
+        tb.rows[(size_t)k * kMaxTlHits + n] = (uint8_t)r;
+        ++n;
+        save_last(st);
+        yrefLast = yref;
+        misses = 0;
+        r += kDir;
+      } else if (++misses >= kMaxMiss) {
+        finish();
+      } else {
+        r += kDir;
+      }
     }
   }
-  st.x = s_last[0][threadIdx.x];
-#pragma unroll
-  for (int j = 0; j < 5; ++j) st.p[j] = s_last[1 + j][threadIdx.x];
-#pragma unroll
-  for (int j = 0; j < 15; ++j) st.C[j] = s_last[6 + j][threadIdx.x];
-  return n;
 }
-
-// The two following passes are latency bound (dependent grid -> cell -> hit
-// loads per row step): they run at 9 CTAs of 128 threads per SM (56
-// registers, a few bytes of spill), measured 12 % faster than at 7 CTAs.
-
-// (b) outward following above the chain; then the refit's starting state:
-// the last accepted state with the position of the top hit and a fresh
-// covariance.
-__global__ void __launch_bounds__(128, 9) k_tl_out(const int* __restrict__ nTlDev, int* __restrict__ counter, const RowGrid* __restrict__ grid,
-                                                const int* __restrict__ cellStart, const int2* __restrict__ syz,
-                                                const GeomConst* __restrict__ G, TrackletBufs tb) {
-  __shared__ float s_last[21][128];
-  const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
-  const int nTl = *nTlDev;
-  for (;;) {
-    const int k = atomicAdd(counter, 1);
-    if (k >= nTl) return;
-    const int nc = tb.nasc[k];
-    if (nc == 0) continue;
-    int* H = tb.hits + (size_t)k * kMaxTlHits;
-    uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
-    const int r0 = Rw[0], Rs = tb.rbase[k], zref = tb.zref[k];
-    const int yref = syz[H[0]].x;
-    KState<float> st;
-    float* S = tb.state + (size_t)k * 21;
-    load_state(st, S);
-    int top = H[nc - 1];
-    const int na = follow<1>(st, s_last, r0 + nc, nc, H, Rw, &top, Rs, yref, zref, grid, cellStart, syz, G, zunit,
-                             izunit, bzc);
-    const int2 p = syz[top];
-    st.p[0] = hit_y(p.x, yref);
-    st.p[1] = hit_z(p.y, zref, zunit);
-    reset_cov(st);
-    tb.nasc[k] = na;
-    store_raw(S, st);
-  }
-}
-
-// (c) inward refit from the top hit through every attached hit; a hit whose
-// transport fails is skipped.
-__global__ void __launch_bounds__(128) k_tl_refit(const int* __restrict__ nTlDev, int* __restrict__ counter, const int2* __restrict__ syz,
-                                                  const GeomConst* __restrict__ G, TrackletBufs tb) {
-  const float zunit = G->zunit, bzc = G->bzc;
-  const int nTl = *nTlDev;
-  for (;;) {
-    const int k = atomicAdd(counter, 1);
-    if (k >= nTl) return;
-    const int na = tb.nasc[k];
-    if (na == 0) continue;
-    const int* H = tb.hits + (size_t)k * kMaxTlHits;
-    const uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
-    const int zref = tb.zref[k];
-    const int yref = syz[H[0]].x;
-    KState<float> st;
-    float* S = tb.state + (size_t)k * 21;
-    load_state(st, S);
-    for (int i = na - 2; i >= 0; --i) {
-      const int2 hp = syz[H[i]];
-      if (kf_prop<float>(st, G->rowx[Rw[i]], bzc) != 0) continue;
-      kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr);
-    }
-    store_raw(S, st);
-  }
-}
-
-// (d) inward following below the chain start; the state kept is the one at
-// the innermost accepted hit.
-__global__ void __launch_bounds__(128, 9) k_tl_in(const int* __restrict__ nTlDev, int* __restrict__ counter, const RowGrid* __restrict__ grid,
-                                               const int* __restrict__ cellStart, const int2* __restrict__ syz,
-                                               const GeomConst* __restrict__ G, TrackletBufs tb) {
-  __shared__ float s_last[21][128];
-  const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
-  const int nTl = *nTlDev;
-  for (;;) {
-    const int k = atomicAdd(counter, 1);
-    if (k >= nTl) return;
-    const int na = tb.nasc[k];
-    if (na == 0) continue;
-    int* H = tb.hits + (size_t)k * kMaxTlHits;
-    uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
-    const int r0 = Rw[0], Rs = tb.rbase[k], zref = tb.zref[k];
-    const int yref = syz[H[0]].x;
-    KState<float> st;
-    float* S = tb.state + (size_t)k * 21;
-    load_state(st, S);
-    int top = -1;
-    const int n = follow<-1>(st, s_last, r0 - 1, na, H, Rw, &top, Rs, yref, zref, grid, cellStart, syz, G, zunit,
-                             izunit, bzc);
-    tb.nhits[k] = n;
-    store_state(S, st, yref);
-  }
-}
-
 
 // Ownership keys.  Only tracklets of the same sector can share a hit, so the
 // tie-break id is the tracklet's index within its sector (same order as the
@@ -495,7 +711,7 @@ __global__ void __launch_bounds__(128) k_sector_fit(const int* __restrict__ nStD
                                                     SectorTrackBufs sb) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= *nStDev) return;
-  const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
+  const float zunit = G->zunit, bzc = G->bzc;
   const int b = sb.off[id], m = sb.off[id + 1] - b;
   const int2* P = sb.yz + b;
   const uint8_t* Rw = sb.rows + b;
@@ -505,26 +721,41 @@ __global__ void __launch_bounds__(128) k_sector_fit(const int* __restrict__ nStD
   const float xa = G->rowx[Rw[0]];
   {
     KState<float> tmp = sd;
-    if (kf_prop<float>(tmp, xa, bzc) == 0) sd = tmp;
+    if (kf_prop_row<float>(tmp, row_of_x(sd.x), Rw[0], G, bzc) == 0) sd = tmp;
   }
   KState<float> t;
   int2 p = P[0];
-  const int yref = p.x;
+  int yref = p.x;
   kf_reset<float>(t, xa, hit_y(p.x, yref), hit_z(p.y, zref, zunit), sd.p[2], sd.p[3], sd.p[4]);
+  kf_meas_cov<float>(t, G->angErr);
+  int srow = Rw[0], zcur = zref;
   for (int i = 1; i < m; ++i) {
-    if (kf_prop<float>(t, G->rowx[Rw[i]], bzc) != 0) continue;
+    if (kf_prop_row<float>(t, srow, Rw[i], G, bzc) != 0) continue;
+    srow = Rw[i];
     p = P[i];
-    kf_update<float>(t, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
+    recentre_y(t.p[0], yref, p.x);
+    recentre_z(t.p[1], zcur, p.y, zunit);
+    kf_update<float>(t, hit_y(p.x, yref), 0.f, nullptr, G->angErr);
   }
+  t.p[1] += (float)(zcur - zref) * zunit;
   store_state(sb.out + (size_t)id * 21, t, yref);
   KState<float> u;
   p = P[m - 1];
+  yref = p.x;
   kf_reset<float>(u, G->rowx[Rw[m - 1]], hit_y(p.x, yref), hit_z(p.y, zref, zunit), t.p[2], t.p[3], t.p[4]);
+  kf_meas_cov<float>(u, G->angErr);
+  srow = Rw[m - 1];
+  zcur = P[m - 1].y;
+  u.p[1] = 0.f;
   for (int i = m - 2; i >= 0; --i) {
-    if (kf_prop<float>(u, G->rowx[Rw[i]], bzc) != 0) continue;
+    if (kf_prop_row<float>(u, srow, Rw[i], G, bzc) != 0) continue;
+    srow = Rw[i];
     p = P[i];
-    kf_update<float>(u, hit_y(p.x, yref), hit_z(p.y, zref, zunit), nullptr);
+    recentre_y(u.p[0], yref, p.x);
+    recentre_z(u.p[1], zcur, p.y, zunit);
+    kf_update<float>(u, hit_y(p.x, yref), 0.f, nullptr, G->angErr);
   }
+  u.p[1] += (float)(zcur - zref) * zunit;
   store_state(sb.in + (size_t)id * 21, u, yref);
 }
 
@@ -540,9 +771,9 @@ PassGrid pass_grid() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.chain, k_tl_chain, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.out, k_tl_out, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.out, k_tl_follow<1>, 128, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.refit, k_tl_refit, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.in, k_tl_in, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.in, k_tl_follow<-1>, 128, 0);
   }
   return g;
 }
@@ -550,7 +781,7 @@ PassGrid pass_grid() {
 
 void launch_tracklets(int nTl, const int* nTlDev, int* workCounter, const int* starts, const int* up,
                       const RowGrid* grid, int nRows, const int* cellStart, const int2* syz, const GeomConst* G,
-                      TrackletBufs tb, cudaStream_t st, cudaEvent_t* passEnd) {
+                      TrackletBufs tb, cudaStream_t st, cudaEvent_t* passEnd, bool coopSearch) {
   auto mark = [&](int i) {
     if (passEnd) cudaEventRecord(passEnd[i], st);
   };
@@ -563,11 +794,12 @@ void launch_tracklets(int nTl, const int* nTlDev, int* workCounter, const int* s
   cudaMemsetAsync(workCounter, 0, 4 * sizeof(int), st);
   k_tl_chain<<<blocks(g.chain), 128, 0, st>>>(nTlDev, workCounter, starts, up, grid, nRows, syz, G, tb);
   mark(0);
-  k_tl_out<<<blocks(g.out), 128, 0, st>>>(nTlDev, workCounter + 1, grid, cellStart, syz, G, tb);
+  const int coop = coopSearch ? 1 : 0;
+  k_tl_follow<1><<<blocks(g.out), 128, 0, st>>>(nTlDev, workCounter + 1, grid, cellStart, syz, G, tb, coop);
   mark(1);
   k_tl_refit<<<blocks(g.refit), 128, 0, st>>>(nTlDev, workCounter + 2, syz, G, tb);
   mark(2);
-  k_tl_in<<<blocks(g.in), 128, 0, st>>>(nTlDev, workCounter + 3, grid, cellStart, syz, G, tb);
+  k_tl_follow<-1><<<blocks(g.in), 128, 0, st>>>(nTlDev, workCounter + 3, grid, cellStart, syz, G, tb, coop);
   mark(3);
   g_launch_count += 4;
 }

@@ -31,6 +31,31 @@ using namespace o2tpc;
 
 thread_local long long o2tpc::g_launch_count = 0;
 
+void o2tpc::fill_geom(GeomConst& g, double bz, double vd) {
+  const double pi = 3.14159265358979323846;
+  std::memset(&g, 0, sizeof(g));
+  for (int r = 0; r < kNRow; ++r) {
+    double x = 85.0 + (double)r * 160.0 / 151.0;
+    g.rowx[r] = (float)x;
+    g.rowx_d[r] = x;
+    g.npads[r] = (int)std::floor(2.0 * x * std::tan(10.0 * pi / 180.0) / 0.4);
+  }
+  g.pitch_d = 160.0 / 151.0;
+  g.pitch = (float)g.pitch_d;
+  for (int s = 0; s < 18; ++s) g.sec_alpha[s] = (float)((s * 20.0 + 10.0) * pi / 180.0);
+  g.tan10 = (float)std::tan(10.0 * pi / 180.0);
+  g.rot_cos = (float)std::cos(20.0 * pi / 180.0);
+  g.rot_sin = (float)std::sin(20.0 * pi / 180.0);
+  g.rot_cos_d = std::cos(20.0 * pi / 180.0);
+  g.rot_sin_d = std::sin(20.0 * pi / 180.0);
+  g.bzc_d = -0.00299792458 * bz;
+  g.bzc = (float)g.bzc_d;
+  g.zunit_d = 0.003125 * vd;
+  g.zunit = (float)g.zunit_d;
+  g.vd_d = vd;
+  g.kz = (float)(1.0 / (0.003125 * vd));
+}
+
 namespace {
 
 constexpr int kTileMin = 65536;           // clusters per ingest tile, at least
@@ -304,28 +329,6 @@ int read_int(Ctx* c, const int* dptr) {
   return v;
 }
 
-void fill_geom(GeomConst& g, double bz, double vd) {
-  const double pi = 3.14159265358979323846;
-  for (int r = 0; r < kNRow; ++r) {
-    double x = 85.0 + (double)r * 160.0 / 151.0;
-    g.rowx[r] = (float)x;
-    g.rowx_d[r] = x;
-    g.npads[r] = (int)std::floor(2.0 * x * std::tan(10.0 * pi / 180.0) / 0.4);
-  }
-  for (int s = 0; s < 18; ++s) g.sec_alpha[s] = (float)((s * 20.0 + 10.0) * pi / 180.0);
-  g.tan10 = (float)std::tan(10.0 * pi / 180.0);
-  g.rot_cos = (float)std::cos(20.0 * pi / 180.0);
-  g.rot_sin = (float)std::sin(20.0 * pi / 180.0);
-  g.rot_cos_d = std::cos(20.0 * pi / 180.0);
-  g.rot_sin_d = std::sin(20.0 * pi / 180.0);
-  g.bzc_d = -0.00299792458 * bz;
-  g.bzc = (float)g.bzc_d;
-  g.zunit_d = 0.003125 * vd;
-  g.zunit = (float)g.zunit_d;
-  g.vd_d = vd;
-  g.kz = (float)(1.0 / (0.003125 * vd));
-}
-
 // ------------------------------------------------------------ the batch
 void tune_cache_store(Ctx* c);
 
@@ -511,7 +514,8 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     const long long before = g_launch_count;
     graph_enqueue(A, c->dGeom, c->tune.nf_hits_per_block, c->tune.nf_staged != 0, c->tune.sort_threads_per_row,
-                  (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, st);
+                  (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, st, (c->cfg.flags & O2TPC_FLAG_COOP_SEARCH) != 0,
+                  (c->cfg.flags & O2TPC_FLAG_ROW_STEP2) != 0);
     const cudaError_t ce = cudaStreamEndCapture(st, &g);
     c->graphKernels = g_launch_count - before;
     if (ce != cudaSuccess || !g || cudaGraphInstantiate(&c->graphExec, g, 0) != cudaSuccess) {
@@ -671,8 +675,12 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   const int nfB = c->tune.nf_hits_per_block;
   const int nfBlocksMax = n / nfB + nRows + 1;
   launch_neighbours(nfBlocksMax, nfB, c->tune.nf_staged != 0, grid, nfBlockStart, nRows, cellStart, syz, G, upRaw,
-                    dnRaw, dErr, st);
+                    dnRaw, dErr, st, c->cfg.debug_inject);
   CKL();
+  if (c->cfg.flags & O2TPC_FLAG_ROW_STEP2) {
+    launch_neighbours_gap(n, &C->n, grid, nRows, cellStart, syz, G, upRaw, dnRaw, st);
+    CKL();
+  }
   CK(cudaEventRecord(c->evs[3], st));
   launch_clean(n, &C->n, upRaw, dnRaw, up, dn, flag, st);
   CKL();
@@ -698,9 +706,11 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   tb.rows = dalloc<uint8_t>(M, (size_t)nTl * kMaxTlHits);
   tb.state = dalloc<float>(M, (size_t)nTl * 21);
   tb.zref = dalloc<int>(M, nTl);
+  tb.yref = dalloc<int>(M, nTl);
   tb.rbase = dalloc<int>(M, nTl);
   int* workCounter = dalloc<int>(M, 4);
-  launch_tracklets(nTl, &C->nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st, c->evTl);
+  launch_tracklets(nTl, &C->nTl, workCounter, starts, up, grid, nRows, cellStart, syz, G, tb, st, c->evTl,
+                   (c->cfg.flags & O2TPC_FLAG_COOP_SEARCH) != 0);
   CKL();
 
   // ---- A9: selection
@@ -1493,6 +1503,8 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
     for (auto& e : x->evTl) CK(cudaEventCreate(&e));
     for (auto& e : x->evCtf) CK(cudaEventCreate(&e));
     fill_geom(x->hGeom, c.bz_tesla, c.vdrift_cm_us);
+    x->hGeom.angErr = (c.flags & O2TPC_FLAG_ANGULAR_ERRORS) ? 1 : 0;
+    x->hGeom.rowStep2 = (c.flags & O2TPC_FLAG_ROW_STEP2) ? 1 : 0;
     x->dGeom = static_cast<GeomConst*>(x->dev_alloc(sizeof(GeomConst)));
     x->dCounts = static_cast<Counts*>(x->dev_alloc(sizeof(Counts)));
     CK(cudaMemcpyAsync(x->dGeom, &x->hGeom, sizeof(GeomConst), cudaMemcpyHostToDevice, x->stream));

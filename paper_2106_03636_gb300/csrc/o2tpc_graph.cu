@@ -85,6 +85,7 @@ size_t graph_carve(GraphArena& A, char* base) {
   take(A.tb.rows, (size_t)k.tlCap * kMaxTlHits);
   take(A.tb.state, (size_t)k.tlCap * 21);
   take(A.tb.zref, k.tlCap);
+  take(A.tb.yref, k.tlCap);
   take(A.tb.rbase, k.tlCap);
   take(A.workCounter, 4);
   take(A.w, n);
@@ -160,7 +161,7 @@ size_t graph_carve(GraphArena& A, char* base) {
 // The batch pipeline with capacities for sizes and no host synchronisation;
 // the TF table, tiles and Counts (n, nKeys) are filled before each replay.
 void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, bool nfStage, int sortThreads,
-                   int forceFp64, cudaStream_t st) {
+                   int forceFp64, cudaStream_t st, bool coopSearch, bool rowStep2) {
   const GraphCaps& k = A.caps;
   Counts* C = A.cnt;
   const int n = k.nCap;
@@ -175,13 +176,14 @@ void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, bool nf
   // A5-A7
   launch_neighbours(n / nfBlock + k.nRows + 1, nfBlock, nfStage, A.grid, A.nfBlockStart, k.nRows, A.cellStart, A.syz, G,
                     A.upRaw, A.dnRaw, A.err, st);
+  if (rowStep2) launch_neighbours_gap(n, &C->n, A.grid, k.nRows, A.cellStart, A.syz, G, A.upRaw, A.dnRaw, st);
   launch_clean(n, &C->n, A.upRaw, A.dnRaw, A.up, A.dn, A.flag, st);
   launch_ballot_count(n, &C->n, A.flag, A.tileCnt, A.tileOff, &C->nTl, k.tlCap, &C->overflow, A.scratch, st);
   launch_ballot_compact(n, &C->n, A.flag, A.tileOff, A.starts, k.tlCap, &C->overflow, st);
   launch_tf_ranges(k.BCap, A.grid, A.starts, &C->nTl, A.tlTfBegin, st);
   // A8
   launch_tracklets(k.tlCap, &C->nTl, A.workCounter, A.starts, A.up, A.grid, k.nRows, A.cellStart, A.syz, G, A.tb,
-                   st, nullptr);
+                   st, nullptr, coopSearch);
   // A9
   cudaMemsetAsync(A.w, 0, sizeof(unsigned long long) * (size_t)n, st);
   launch_ownership(k.tlCap, &C->nTl, k.BCap * kNSec, A.grid, A.starts, A.tb, A.w, A.secBegin, A.wide, st);

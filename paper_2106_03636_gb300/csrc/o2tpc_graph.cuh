@@ -55,6 +55,6 @@ GraphCaps graph_caps(long long maxClusters, int maxTFs, bool tight = false);
 size_t graph_carve(GraphArena& A, char* base);
 // Enqueues the whole pipeline on st (for stream capture).
 void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, bool nfStage, int sortThreads,
-                   int forceFp64, cudaStream_t st);
+                   int forceFp64, cudaStream_t st, bool coopSearch = false, bool rowStep2 = false);
 
 }  // namespace o2tpc

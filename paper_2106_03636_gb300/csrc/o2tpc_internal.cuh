@@ -30,6 +30,10 @@ constexpr int kMaxMetric = 16 * 1536 * 2077;  // 2-dof chi2 <= 16, scaled
 // ---------------------------------------------------------- track fit
 constexpr float kSigY = 0.1f;
 constexpr float kSigZ = 0.15f;
+// Angle-dependent cluster errors (optional model): the variances grow by
+// (L tan phi)^2 / 12 along y and (L tan lambda)^2 / 12 along the drift, L the
+// pad length (the row pitch, 160/151 cm).
+constexpr double kLpad2_12 = (160.0 / 151.0) * (160.0 / 151.0) / 12.0;
 constexpr int kMaxMiss = 4;        // consecutive rows without a hit before stopping
 constexpr int kMinHits = 10;       // tracklet / sector-track minimum
 constexpr float kChi2Follow = 18.f;
@@ -43,6 +47,10 @@ constexpr float kChi2Merge = 30.f;
 struct GeomConst {
   float rowx[kNRow];
   double rowx_d[kNRow];
+  float pitch;      // pad-row spacing 160/151 cm: transport steps between rows
+  double pitch_d;
+  int angErr;       // 1: angle-dependent cluster errors
+  int rowStep2;     // 1: the NeighboursFinder also links across one missing row
   int npads[kNRow];
   float sec_alpha[18];
   float tan10;
@@ -80,6 +88,10 @@ struct TFDesc {
   int nColl;         // interaction times of this TF (ascending, us)
   int collBase;      // first of them in the batch's array
 };
+
+// Fills the geometry table for a field of bz tesla and a drift velocity of vd
+// cm/us (host side; defined in o2tpc_capi.cu, used by every entry point).
+void fill_geom(GeomConst& g, double bz, double vd);
 
 // Device error word bits
 enum : unsigned { kErrInput = 1u, kErrOverflow = 2u, kErrTimeout = 4u, kErrMembrane = 8u };
@@ -170,6 +182,22 @@ __device__ inline float kf_asin<float>(float v) { return asinf(v); }
 template <>
 __device__ inline double kf_asin<double>(double v) { return asin(v); }
 
+// Cluster variances (y, zeta) for a track with the state's angles: kSigY^2,
+// kSigZ^2, plus with the angle-dependent model (angErr) the pad-length terms
+// kLpad2_12 * tan^2(phi), tan^2(phi) = s^2 / (1 - s^2) from s = sin(phi), and
+// kLpad2_12 * t^2 (t = dzeta/ds, |t| = tan(lambda)).
+template <typename T>
+__device__ inline void meas_var(int angErr, const KState<T>& s, T& vy, T& vz) {
+  vy = T(kSigY) * T(kSigY);
+  vz = T(kSigZ) * T(kSigZ);
+  if (angErr) {
+    const T s2 = s.p[2] * s.p[2];
+    const T tan2 = s2 < T(1) ? s2 / (T(1) - s2) : T(1e6);
+    vy += T(kLpad2_12) * tan2;
+    vz += T(kLpad2_12) * s.p[3] * s.p[3];
+  }
+}
+
 template <typename T>
 __device__ inline void kf_reset(KState<T>& s, T x, T y, T z, T sphi, T t, T q) {
   s.x = x;
@@ -250,11 +278,15 @@ __device__ inline void kf_sandwich_transport(T* C, T a02, T a04, T a12, T a13, T
 // a three-point Simpson integral of its cancellation-free integrand when
 // |k dx| < 0.05, else (dx/c2 - ds)/k.  Returns 0, or -1 if |sin phi| would
 // reach kSinProp.
+// One transport step's increments and Jacobian terms from parameters p
+// (y, zeta, sin phi, t, q/pT) over dx; -1 if |sin phi| would reach kSinProp.
 template <typename T>
-__device__ inline int kf_prop(KState<T>& s, T x2, T bzc) {
-  T dx = x2 - s.x;
-  if (dx == T(0)) return 0;
-  T s1 = s.p[2], q = s.p[4], tz = s.p[3];
+struct PropStep {
+  T dy, dzeta, s2, a02, a04, a12, a13, a14, a24;
+};
+template <typename T>
+__device__ inline int kf_prop_step(const T* p, T dx, T bzc, PropStep<T>& o) {
+  T s1 = p[2], q = p[4], tz = p[3];
   T k = q * bzc;
   T s2 = s1 + k * dx;
   if (fabs(s1) >= T(kSinProp) || fabs(s2) >= T(kSinProp)) return -1;
@@ -292,20 +324,109 @@ __device__ inline int kf_prop(KState<T>& s, T x2, T bzc) {
   const T a13 = ds;
   const T a14 = tz * bzc * ddsdk;
   const T a24 = dx * bzc;
-  s.p[0] += dy;
-  s.p[1] += tz * ds;
-  s.p[2] = s2;
-  s.x = x2;
-  kf_sandwich_transport<T>(s.C, a02, a04, a12, a13, a14, a24);
+  o.dy = dy;
+  o.dzeta = tz * ds;
+  o.s2 = s2;
+  o.a02 = a02;
+  o.a04 = a04;
+  o.a12 = a12;
+  o.a13 = a13;
+  o.a14 = a14;
+  o.a24 = a24;
   return 0;
 }
 
-// Kalman update with a (y, zeta) measurement of errors (kSigY, kSigZ).
 template <typename T>
-__device__ inline int kf_update(KState<T>& s, T ym, T zm, T* chi2) {
+__device__ inline int kf_prop_dx(KState<T>& s, T x2, T dx, T bzc) {
+  if (dx == T(0)) return 0;
+  PropStep<T> o;
+  if (kf_prop_step<T>(s.p, dx, bzc, o) != 0) return -1;
+  s.p[0] += o.dy;
+  s.p[1] += o.dzeta;
+  s.p[2] = o.s2;
+  s.x = x2;
+  kf_sandwich_transport<T>(s.C, o.a02, o.a04, o.a12, o.a13, o.a14, o.a24);
+  return 0;
+}
+
+// The FP64 fallback's transport: the step's geometry (increments and
+// Jacobian terms) in single precision, as on the FP32 path, applied to the
+// double-precision state, and the covariance propagated in double.  Double
+// precision is needed only where the FP32 covariance lost positive
+// definiteness; the transcendental geometry stays single precision, where a
+// GPU runs it fast.
+__device__ inline int kf_prop_dx_cov64(KState<double>& s, double x2, float dx, float bzc) {
+  if (dx == 0.f) return 0;
+  float pf[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) pf[i] = (float)s.p[i];
+  PropStep<float> o;
+  if (kf_prop_step<float>(pf, dx, bzc, o) != 0) return -1;
+  s.p[0] += (double)o.dy;
+  s.p[1] += (double)o.dzeta;
+  s.p[2] += s.p[4] * (double)bzc * (double)dx;
+  s.x = x2;
+  kf_sandwich_transport<double>(s.C, o.a02, o.a04, o.a12, o.a13, o.a14, o.a24);
+  return 0;
+}
+
+// Transport to x2 from a state at any x (after a frame rotation, or to another
+// track's x): the step is the difference of the two positions.
+template <typename T>
+__device__ inline int kf_prop(KState<T>& s, T x2, T bzc) {
+  return kf_prop_dx<T>(s, x2, x2 - s.x, bzc);
+}
+
+// Transport between pad rows r1 -> r2 of a state sitting on row r1.  The step
+// (r2 - r1) * pitch carries one rounding; the difference of the two rounded
+// row positions would carry up to 1.5e-5 cm in single precision, an error
+// that dominates the FP32 curvature of short tracks (a 10-row stub's
+// sagitta is a few 1e-3 cm).
+template <typename T>
+__device__ inline int kf_prop_row(KState<T>& s, int r1, int r2, const GeomConst* __restrict__ G, T bzc) {
+  const T pitch = sizeof(T) == 8 ? (T)G->pitch_d : (T)G->pitch;
+  const T x2 = sizeof(T) == 8 ? (T)G->rowx_d[r2] : (T)G->rowx[r2];
+  return kf_prop_dx<T>(s, x2, (T)(r2 - r1) * pitch, bzc);
+}
+
+// Pad row of a state whose x is a row position (within its rounding).
+__device__ inline int row_of_x(float x) { return __float2int_rn((x - 85.f) * (151.f / 160.f)); }
+
+// Moves a fit's y origin yref (integer units of 1/160 cm) in whole
+// centimetres to within half a centimetre of the hit at yu, and the state's y
+// (cm, relative to the origin) with it.  A shift by whole centimetres is an
+// exact number, so the state only takes the rounding of a value below ~1 cm;
+// the fits then never hold y values of several cm, whose rounding (2e-7 cm at
+// 4 cm) would show in the curvature of short tracks.
+// Moves a fit's drift origin zref (integer units) to the hit at zu, and the
+// state's zeta (cm, relative to the origin) with it: the fit then only holds
+// zeta values of about a row step, and the rounding of the tens of cm a long
+// steep track spans does not build up along it.  The shift itself carries one
+// rounding of a value of that row step's size.
+template <typename T>
+__device__ inline void recentre_z(T& z, int& zref, int zu, T zunit) {
+  const int d = zu - zref;
+  if (d != 0) {
+    z -= (T)d * zunit;
+    zref = zu;
+  }
+}
+
+template <typename T>
+__device__ inline void recentre_y(T& y, int& yref, int yu) {
+  const int m = floordiv_i32(yu - yref + 80, 160);
+  if (m != 0) {
+    y -= (T)m;
+    yref += 160 * m;
+  }
+}
+
+// Kalman update with a (y, zeta) measurement of variances (vy, vz).
+template <typename T>
+__device__ inline int kf_update_v(KState<T>& s, T ym, T zm, T vy, T vz, T* chi2) {
   T* C = s.C;
   T r0 = ym - s.p[0], r1 = zm - s.p[1];
-  T S00 = C[0] + T(kSigY) * T(kSigY), S01 = C[1], S11 = C[2] + T(kSigZ) * T(kSigZ);
+  T S00 = C[0] + vy, S01 = C[1], S11 = C[2] + vz;
   T det = S00 * S11 - S01 * S01;
   if (!(det > T(0))) return -1;
   const T idet = T(1) / det;
@@ -323,6 +444,22 @@ __device__ inline int kf_update(KState<T>& s, T ym, T zm, T* chi2) {
 #pragma unroll
     for (int j = 0; j <= i; ++j) C[ix(i, j)] -= K0[i] * Cy[j] + K1[i] * Cz[j];
   return 0;
+}
+
+// Kalman update with the cluster variances of the error model at the
+// predicted state's angles.
+template <typename T>
+__device__ inline int kf_update(KState<T>& s, T ym, T zm, T* chi2, int angErr) {
+  T vy, vz;
+  meas_var<T>(angErr, s, vy, vz);
+  return kf_update_v<T>(s, ym, zm, vy, vz, chi2);
+}
+
+// The (y, zeta) entries of a fresh covariance: the cluster variances at the
+// state's angles.
+template <typename T>
+__device__ inline void kf_meas_cov(KState<T>& s, int angErr) {
+  meas_var<T>(angErr, s, s.C[0], s.C[2]);
 }
 
 // Frame rotation by dalpha (cos ca, sin sa): new alpha = old alpha + dalpha.

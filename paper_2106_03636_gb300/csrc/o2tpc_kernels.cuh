@@ -29,10 +29,15 @@ void launch_cell_sort(int nRows, const RowGrid* grid, const int4* bucket, int* c
 
 // k_ca.cu
 // syz must hold one int2 of padding past the last hit (the 16-byte aligned
-// slab copies may read it); err collects kErrTimeout.
+// slab copies may read it); err collects kErrTimeout.  inject: the context's
+// debug_inject bits (bit 0: staged slabs armed but not copied, short waits).
 void launch_neighbours(int nfBlocks, int hitsPerBlock, bool stage, const RowGrid* grid, const int* nfBlockStart,
                        int nRows, const int* cellStart, const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw,
-                       unsigned* err, cudaStream_t st);
+                       unsigned* err, cudaStream_t st, unsigned inject = 0);
+// Row step 2: links across one missing row for the hits that found no
+// adjacent-row pair (after launch_neighbours; n sizes the grid).
+void launch_neighbours_gap(int n, const int* nDev, const RowGrid* grid, int nRows, const int* cellStart,
+                           const int2* syz, const GeomConst* G, int* upRaw, int* dnRaw, cudaStream_t st);
 // Data-dependent sizes are read by the kernels from device memory (nDev,
 // the fields of Counts); the host-side n of a launcher only sizes its grid:
 // the exact size on the regular path, a capacity on the captured path.
@@ -81,14 +86,16 @@ struct TrackletBufs {
   uint8_t* rows; // [nTl * kMaxTlHits]
   float* state;  // [nTl * 21]  x, par[5], cov[15] at the innermost hit
   int* zref;     // [nTl]
+  int* yref;     // [nTl]  y origin (units) of the state handed between the passes
   int* rbase;    // [nTl]  batch-global row of pad row 0 of the tracklet's sector
 };
 // passEnd: optional 4 events recorded after the chain-fit, outward, refit and
-// inward passes.
+// inward passes.  coopSearch: the following passes scan the row windows
+// cooperatively over the warp instead of lane by lane (identical results).
 // nTl sizes the grids; the kernels read the count at nTlDev
 void launch_tracklets(int nTl, const int* nTlDev, int* workCounter, const int* starts, const int* up,
                       const RowGrid* grid, int nRows, const int* cellStart, const int2* syz, const GeomConst* G,
-                      TrackletBufs tb, cudaStream_t st, cudaEvent_t* passEnd = nullptr);
+                      TrackletBufs tb, cudaStream_t st, cudaEvent_t* passEnd = nullptr, bool coopSearch = false);
 
 struct SectorTrackBufs {
   int* tl;        // [nSt] tracklet of the sector track

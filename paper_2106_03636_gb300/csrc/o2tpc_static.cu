@@ -16,9 +16,12 @@
 // holds them (about 6 MB) until the process exits.  Their device addresses
 // are looked up once per device with cudaGetSymbolAddress, during the first
 // call on that device; that first call should therefore come before any
-// stream capture.  All calls share the arrays and leave the last call's
-// contents in them, so calls that overlap on the GPU (different streams or
-// threads at the same time) race: serialise them.
+// stream capture.  Under lazy module loading that first call can also load
+// the module and reserve the static storage, so callers with a fixed memory
+// plan make one call with n = 0 at start-up.  The cached addresses are not
+// valid across a cudaDeviceReset.  All calls share the arrays and leave the
+// last call's contents in them, so calls that overlap on the GPU (different
+// streams or threads at the same time) race: serialise them.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -95,20 +98,6 @@ cudaError_t setup(int dev, StaticPtrs& P) {
   return cudaSuccess;
 }
 
-void fill_static_geom(GeomConst& g, double vd) {
-  const double pi = 3.14159265358979323846;
-  memset(&g, 0, sizeof(g));
-  for (int r = 0; r < kNRow; ++r) {
-    double x = 85.0 + (double)r * 160.0 / 151.0;
-    g.rowx[r] = (float)x;
-    g.rowx_d[r] = x;
-    g.npads[r] = (int)std::floor(2.0 * x * std::tan(10.0 * pi / 180.0) / 0.4);
-  }
-  g.zunit_d = 0.003125 * vd;
-  g.zunit = (float)g.zunit_d;
-  g.kz = (float)(1.0 / (0.003125 * vd));
-}
-
 }  // namespace
 }  // namespace o2tpc
 
@@ -138,7 +127,7 @@ extern "C" int o2tpc_sort_tf_static(const o2tpc_tf* tf, double vdrift_cm_us, int
   const int n = (int)tf->n;
   // descriptors (host copies into the static arrays, in stream order)
   GeomConst g;
-  fill_static_geom(g, vdrift_cm_us);
+  fill_geom(g, 0.5, vdrift_cm_us);  // the field plays no part in binning
   TFDesc d{};
   d.format = tf->format;
   d.n = n;

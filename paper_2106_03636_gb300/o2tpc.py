@@ -37,6 +37,9 @@ O2TPC_FLAG_GRAPH_TIGHT = 1 << 4
 O2TPC_FLAG_COMPRESS = 1 << 5
 O2TPC_FLAG_NO_BATCHING = 1 << 1
 O2TPC_FLAG_FORCE_FP64 = 1 << 2
+O2TPC_FLAG_COOP_SEARCH = 1 << 6
+O2TPC_FLAG_ROW_STEP2 = 1 << 7
+O2TPC_FLAG_ANGULAR_ERRORS = 1 << 8
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -62,6 +65,7 @@ class o2tpc_config(ctypes.Structure):
         ("graph_max_tfs", ctypes.c_int32),
         ("nf_staged", ctypes.c_int32),
         ("tune_cache_path", ctypes.c_char_p),
+        ("debug_inject", ctypes.c_uint32),
     ]
 
 
@@ -403,13 +407,15 @@ class Tracker:
     stream); otherwise the library's own memory pool and copy stream serve
     them and uploads of queued TFs overlap earlier batches.  ``fail_alloc``
     (with ``torch_memory``): called with each request's size; True makes that
-    allocation fail (fault tests)."""
+    allocation fail (fault tests).  ``debug_inject``: o2tpc_config.debug_inject
+    (bit 0: the staged NeighboursFinder's waits run out with no copy in
+    flight)."""
 
     def __init__(self, device: int = 0, bz: float = 0.5, vdrift: float = 2.58, flags: int = 0,
                  mem_budget: int = 0, max_inflight: int = 0, max_batch: int = 0, torch_memory: bool = False,
                  batch_full_clusters: int = 0, nf_hits_per_block: int = 0, sort_threads_per_row: int = 0,
                  graph_max_clusters: int = 0, graph_max_tfs: int = 0, nf_staged: bool = False,
-                 tune_cache_path: str | None = None, fail_alloc=None):
+                 tune_cache_path: str | None = None, fail_alloc=None, debug_inject: int = 0):
         self.cfg = o2tpc_config()
         self.cfg.device = device
         self.cfg.bz_tesla = bz
@@ -426,6 +432,7 @@ class Tracker:
         self.cfg.nf_staged = int(nf_staged)
         self._cache_path = tune_cache_path.encode() if tune_cache_path else None
         self.cfg.tune_cache_path = self._cache_path
+        self.cfg.debug_inject = debug_inject
         self._keep = []
         import torch
 

@@ -5,11 +5,10 @@ Criteria (FP32 path against the FP64 oracle):
   hits: bit-exact;
 * >= 99.9 % of oracle tracks reproduced with identical cluster sets;
 * on those tracks y and zeta within 1e-3 cm, sin(phi), tan(lambda) and q/pT
-  within 1e-4 relative, |d| <= 1e-4 * max(|v_oracle|, 1e-2).  For q/pT the
-  relative scale is the value itself only where the fit determines it
-  (sigma(q/pT) <= |q/pT|); on short stubs whose charge the fit leaves open
-  (sigma > |q/pT|) the scale is sigma(q/pT), i.e. 1e-4 of the parameter's
-  own uncertainty.
+  within 1e-4 relative, |d| <= 1e-4 * max(|v_oracle|, 1e-2), the same
+  tolerance for every track; at most 0.1 % of the matched tracks may miss
+  it.  The report gives, per parameter, the largest error and the 99.9th
+  percentile against the FP64 oracle, and the out-of-tolerance count.
 """
 from __future__ import annotations
 
@@ -55,7 +54,7 @@ def compare_tracks(res: dict, o: dict, zunit: float, check: bool = True) -> dict
     frac = len(matched) / max(1, len(oo))
     err = np.zeros((len(matched), 5))
     bad = 0
-    undetermined = 0
+    bad_param = np.zeros(5, np.int64)
     for k, (i, j) in enumerate(matched):
         po = o["trk_par"][i].copy()
         pg = res["par"][j].astype(np.float64)
@@ -65,18 +64,16 @@ def compare_tracks(res: dict, o: dict, zunit: float, check: bool = True) -> dict
         d = np.abs(pg - po)
         err[k, :2] = d[:2]
         scale = np.maximum(np.abs(po[2:]), REL_FLOOR)
-        sq = float(np.sqrt(max(o["trk_cov"][i][14], 0.0)))
-        if sq > abs(po[4]):
-            scale[2] = max(sq, REL_FLOOR)
-            undetermined += 1
         err[k, 2:] = d[2:] / scale
         same_x = abs(float(res["x"][j]) - o["trk_x"][i]) < 1e-4
-        if not same_x or np.any(err[k, :2] > TOL_POS) or np.any(err[k, 2:] > TOL_REL):
+        over = np.concatenate([err[k, :2] > TOL_POS, err[k, 2:] > TOL_REL])
+        bad_param += over
+        if not same_x or np.any(over):
             bad += 1
     rep = dict(n_oracle=len(oo), n_gpu=len(go), matched=len(matched), frac=frac, bad_params=bad,
-               charge_undetermined=undetermined,
+               bad_per_param=bad_param.tolist(),
                max_err=err.max(axis=0).tolist() if len(err) else [0] * 5,
-               p999_err=np.quantile(err, 0.999, axis=0).tolist() if len(err) else [0] * 5)
+               p999_err=np.quantile(err, 0.999, axis=0).tolist() if len(err) else [0] * 5, _err=err)
     if check:
         assert_criteria(rep)
     return rep
@@ -84,14 +81,22 @@ def compare_tracks(res: dict, o: dict, zunit: float, check: bool = True) -> dict
 
 def assert_criteria(rep: dict) -> None:
     """>= 99.9 % of oracle tracks reproduced with identical cluster sets, and
-    >= 99.9 % of them with every parameter within tolerance."""
+    >= 99.9 % of those with every parameter within tolerance."""
     assert rep["frac"] >= TRACK_MATCH, rep
-    assert rep["bad_params"] <= (1 - TRACK_MATCH) * max(1, rep["n_oracle"]), rep
+    assert rep["bad_params"] <= (1 - TRACK_MATCH) * max(1, rep["matched"]), rep
 
 
 def pool(reps: list) -> dict:
     out = dict(n_oracle=sum(r["n_oracle"] for r in reps), matched=sum(r["matched"] for r in reps),
                bad_params=sum(r["bad_params"] for r in reps),
+               bad_per_param=np.sum([r["bad_per_param"] for r in reps], axis=0).tolist(),
                max_err=np.max([r["max_err"] for r in reps], axis=0).tolist())
+    err = np.concatenate([r["_err"] for r in reps])
+    out["p999_err"] = np.quantile(err, 0.999, axis=0).tolist() if len(err) else [0] * 5
     out["frac"] = out["matched"] / max(1, out["n_oracle"])
     return out
+
+
+def brief(rep: dict) -> dict:
+    """The report without the per-track error array (for printing)."""
+    return {k: v for k, v in rep.items() if not k.startswith("_")}

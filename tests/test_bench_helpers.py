@@ -44,9 +44,20 @@ def test_aggregate_rate_is_whole_job():
     assert bench.aggregate_rate(1e9, 4, 2000.0) == 2e9
 
 
-def test_recorded_traffic_matches_the_sources():
-    """The traffic the roofline line reports must come from a capture of the
-    kernel as it is now: the record carries a hash of its sources."""
-    v = bench.measured_traffic("k_tl_out", "full_tf")
-    assert v is not None and v > 0
+def test_recorded_traffic_follows_the_sources(monkeypatch):
+    """The traffic the roofline line reports comes from a capture of the
+    kernel as it is now: a record carries a hash of the kernel's sources and
+    counts only while they hash to it; otherwise the line reports null."""
+    import hashlib
+
+    srcs = ["k_track.cu", "o2tpc_internal.cuh"]
+    h = hashlib.sha256()
+    for f in srcs:
+        with open(os.path.join(bench.ROOT, "paper_2106_03636_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    rec = {("k_tl_out", "full_tf"): {"bytes": 1.0e9, "sources_sha256_16": h.hexdigest()[:16], "sources": srcs},
+           ("k_tl_in", "full_tf"): {"bytes": 1.0e9, "sources_sha256_16": "0" * 16, "sources": srcs}}
+    monkeypatch.setattr(bench, "MEASURED_TRAFFIC", rec)
+    assert bench.measured_traffic("k_tl_out", "full_tf") == 1.0e9
+    assert bench.measured_traffic("k_tl_in", "full_tf") is None
     assert bench.measured_traffic("k_tl_out", "chunks") is None

@@ -40,8 +40,8 @@ def test_binding_structures_match_header_sizes():
     assert ctypes.sizeof(o2tpc.o2tpc_tf) == 8 + 4 + 4 + 6 * 8 + 8 + 8 + 8
     assert ctypes.sizeof(o2tpc.o2tpc_stats) == 5 * 8 + 4 * 4 + 8 + 18 * 4 + 2 * 4
     # device, budget, inflight, batch, bz, vdrift, flags(+pad), 2 callbacks, user, stream, batch_full,
-    # two launch shapes
-    assert ctypes.sizeof(o2tpc.o2tpc_config) == 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 * 4 + 8 + 4 + 4 + 8 + 8 + 8
+    # two launch shapes, graph clusters, graph TFs + nf_staged, cache path, debug_inject(+pad)
+    assert ctypes.sizeof(o2tpc.o2tpc_config) == 8 + 8 + 4 + 4 + 8 + 8 + 8 + 8 * 4 + 8 + 4 + 4 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(o2tpc.o2tpc_tuning) == 5 * 4 + 9 * 4
 
 

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import compare_tracks
+from parity import brief, compare_tracks
 from paper_2106_03636_gb300 import o2tpc, synth
 
 pytestmark = pytest.mark.gpu
@@ -87,11 +87,4 @@ def test_raw_digits_to_tracks():
     with o2tpc.Tracker() as t:
         res = t.track(tf2, location=o2tpc.O2TPC_LOC_DEVICE, arrays={"packed": rec_dev.contiguous()})
     assert res["status"] == 0
-    rep = compare_tracks(res, oracle.run(tf2), ZUNIT, check=False)
-    print(rep)
-    # the same tracks; on clusterized input (merged deposits) a few more
-    # tracks than on generated clusters sit at a precision edge of the final
-    # refit (a sector-boundary rotation that succeeds in one precision only),
-    # so the parameter check is pooled over this one frame at 0.2 %
-    assert rep["frac"] >= 0.999
-    assert rep["bad_params"] <= 0.002 * rep["n_oracle"]
+    print(brief(compare_tracks(res, oracle.run(tf2), ZUNIT)))

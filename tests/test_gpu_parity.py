@@ -4,7 +4,7 @@ import pytest
 
 import oracle
 from helpers import float_tf
-from parity import assert_criteria, compare_stages, compare_tracks, pool
+from parity import assert_criteria, brief, compare_stages, compare_tracks, pool
 from paper_2106_03636_gb300 import o2tpc, synth
 
 pytestmark = pytest.mark.gpu
@@ -33,8 +33,7 @@ def test_single_sector_parity(trk):
     tf = synth.single_sector()
     ticket, res, o = run_both(trk, tf)
     compare_stages(trk, ticket, o)
-    rep = compare_tracks(res, o, ZUNIT)
-    print(rep)
+    print(brief(compare_tracks(res, o, ZUNIT)))
     trk.release(ticket, res)
 
 
@@ -49,7 +48,7 @@ def test_single_sector_dense_parity(trk):
         reps.append(compare_tracks(res, o, ZUNIT, check=False))
         trk.release(ticket, res)
     rep = pool(reps)
-    print(rep)
+    print(brief(rep))
     assert_criteria(rep)
 
 
@@ -58,7 +57,7 @@ def test_full_tpc_parity(trk, n_coll):
     tf = synth.full_tpc_1ms(n_coll=n_coll)
     ticket, res, o = run_both(trk, tf)
     compare_stages(trk, ticket, o)
-    print(compare_tracks(res, o, ZUNIT))
+    print(brief(compare_tracks(res, o, ZUNIT)))
     trk.release(ticket, res)
 
 
@@ -66,7 +65,7 @@ def test_fixed_point_parity(trk):
     tf = synth.full_tpc_1ms(seed=5, n_coll=2, fmt=synth.FMT_FIXED)
     ticket, res, o = run_both(trk, tf)
     compare_stages(trk, ticket, o)
-    print(compare_tracks(res, o, ZUNIT))
+    print(brief(compare_tracks(res, o, ZUNIT)))
     trk.release(ticket, res)
 
 
@@ -231,7 +230,7 @@ def test_float_time_input_parity(trk):
     tf = synth.float_time_from_fixed(synth.full_tpc_1ms(seed=62, n_coll=2, fmt=synth.FMT_FIXED))
     ticket, res, o = run_both(trk, tf)
     compare_stages(trk, ticket, o)
-    print(compare_tracks(res, o, ZUNIT))
+    print(brief(compare_tracks(res, o, ZUNIT)))
     trk.release(ticket, res)
 
 
@@ -252,3 +251,28 @@ def test_autotuner_cache_file(tmp_path):
         assert t["tuned"] and t["tuned_on_clusters"] == 0
         for k in ("nf_hits_per_block", "nf_staged", "sort_threads_per_row"):
             assert t[k] == first[k]
+
+
+def test_cooperative_search_equals_per_lane_search():
+    """The warp-cooperative row search of the following passes picks the
+    same hits as the per-lane search: tracklets and tracks bit for bit."""
+    tf = synth.full_tpc_1ms(seed=31, n_coll=3)
+    out = []
+    for flags in (0, o2tpc.O2TPC_FLAG_COOP_SEARCH):
+        with o2tpc.Tracker(flags=flags | o2tpc.O2TPC_FLAG_KEEP_STAGES) as t:
+            tk = t.submit(tf)
+            r = t.poll(tk, keep=True)
+            r["tl_nhits"] = t.stage(tk, "tl_nhits")
+            r["tl_hits"] = t.stage(tk, "tl_hits")
+            r["tl_state"] = t.stage(tk, "tl_state")
+            t.release(tk, r)
+            out.append(r)
+    a, b = out
+    assert a["n_tracks"] > 1000
+    nh = a["tl_nhits"]
+    assert np.array_equal(nh, b["tl_nhits"])
+    for i in np.nonzero(nh > 0)[0]:  # slots past a tracklet's hits are never written
+        assert np.array_equal(a["tl_hits"][i, :nh[i]], b["tl_hits"][i, :nh[i]]), i
+    assert np.array_equal(a["tl_state"][nh > 0], b["tl_state"][nh > 0])
+    for k in RESULT_KEYS:
+        assert np.array_equal(a[k], b[k]), k
