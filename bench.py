@@ -14,6 +14,12 @@ clusters in 12-byte fixed-point records), through the C-ABI.
   against the measured HBM copy bandwidth.
 * ``cpu_baseline``: the FP64 single-threaded oracle on one sector of the same
   Time Frame.
+* sub-objects (N = 1): ``full_tpc_1ms`` (the 1 ms, 50-collision frame),
+  ``chunks`` (64 uneven chunks: one captured batch vs one chunk at a time,
+  the autotuned shapes, FP64 fallbacks) and ``serving`` (Poisson arrivals at
+  50 Hz from a pool of Pb-Pb and pp Time Frames: served vs plain, p50 / p99,
+  sustained clusters/s, drops); ``n_fp64_fallback`` counts the final-refit
+  fallbacks of the full TF.
 
 ``--impl reference`` times that oracle as the reference arm instead.
 Under torchrun each rank tracks its own Time Frames (replicas; the only
@@ -64,8 +70,8 @@ STAGE_BYTES = {
     "continuous": 1.0,
 }
 # DRAM bytes (read + write) per launch that ncu measured for a kernel on a
-# workload (the launch list in profiles/launches_full_tf.md), valid while the
-# kernel's sources hash to the recorded value; otherwise the line says null.
+# workload, valid while the kernel's sources hash to the recorded value;
+# otherwise the line says null.
 MEASURED_TRAFFIC = {
     ("k_tl_out", "full_tf"): {"bytes": 8399.0e6 + 3496.7e6, "sources_sha256_16": "66461f3c31c50bde",
                               "sources": ["k_track.cu", "o2tpc_internal.cuh"]},
@@ -356,10 +362,11 @@ def aggregate_rate(units_per_rank: float, world: int, ms: float) -> float:
     return world * units_per_rank / (ms / 1e3)
 
 
-def run_chunks(args, rank, world, local):
+def measure_chunks(args, rank, world, local, steps, warmup):
     """Uneven sub-Time-Frame chunks (64 chunks, Poisson(20) collisions each, a
     quarter pp-like): plain = one chunk per launch sequence, synchronised per
-    chunk; batched = all chunks in one batch (one launch sequence)."""
+    chunk; batched = all chunks in one batch (one launch sequence, one CUDA
+    graph launch unless --no-graph).  Returns the measurement's fields."""
     import torch
     import torch.distributed as dist
 
@@ -387,7 +394,7 @@ def run_chunks(args, rank, world, local):
         return [batched.wait(t) for t in tk]
 
     def timed(fn, trk, *a):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fn(*a)
         if world > 1:
             dist.barrier()
@@ -395,8 +402,9 @@ def run_chunks(args, rank, world, local):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stage = np.zeros(len(o2tpc.STAGES))
         launches, sizes, captured = 0, set(), set()
+        fallback = 0
         e0.record(trk.stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             rs = fn(*a)
             for r in rs:
                 if r["status"] != 0:
@@ -411,22 +419,24 @@ def run_chunks(args, rank, world, local):
                 launches += int(r["stats"]["n_launches"])
                 sizes.add(int(r["stats"]["batch_size"]))
                 captured.add(int(r["stats"]["captured"]))
+                fallback += int(r["stats"]["n_fp64_fallback"])
         e1.record(trk.stream)
         torch.cuda.synchronize()
         ms = device_max(e0.elapsed_time(e1), world, local)
         timed.captured = sorted(captured)
-        return ms / args.steps, stage / args.steps, launches // args.steps, sorted(sizes), rs
+        timed.fallback = fallback // steps
+        return ms / steps, stage / steps, launches // steps, sorted(sizes), rs
 
-    with ClockSampler(local) as clk:
-        ms_p, stage_p, l_p, _, _ = timed(pass_plain, plain)
-        ms_b, stage_b, l_b, sizes_b, rs = timed(pass_batched, batched)
-        captured_b = timed.captured
-        if captured_b == [1]:
-            # the graph records no per-step events: step times of the same
-            # batch on the regular path, for stage_ms and the roofline line
-            reg = o2tpc.Tracker(device=local, max_batch=len(chunks), batch_full_clusters=2**64 - 1, flags=tune)
-            ms_r, stage_b, _, _, _ = timed(lambda: [reg.wait(t) for t in reg.submit_many(chunks, location=o2tpc.O2TPC_LOC_DEVICE, arrays=dev)], reg)
-            reg.close()
+    ms_p, stage_p, l_p, _, _ = timed(pass_plain, plain)
+    ms_b, stage_b, l_b, sizes_b, rs = timed(pass_batched, batched)
+    captured_b = timed.captured
+    fallback_b = timed.fallback
+    if captured_b == [1]:
+        # the graph records no per-step events: step times of the same
+        # batch on the regular path, for stage_ms and the roofline line
+        reg = o2tpc.Tracker(device=local, max_batch=len(chunks), batch_full_clusters=2**64 - 1, flags=tune)
+        ms_r, stage_b, _, _, _ = timed(lambda: [reg.wait(t) for t in reg.submit_many(chunks, location=o2tpc.O2TPC_LOC_DEVICE, arrays=dev)], reg)
+        reg.close()
     e2e = None
     if not args.no_e2e:
         pin = [{"packed": torch.from_numpy(c.packed).pin_memory()} for c in chunks]
@@ -438,14 +448,13 @@ def run_chunks(args, rank, world, local):
                "mode": "batched from pinned host memory"}
     peak, peak_kind = peaks()
     names = o2tpc.STAGES
-    line = {"metric": METRIC, "value": world * n / (ms_b / 1e3), "unit": "clusters/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "chunks_64x36sectors_poisson20", "chunks": len(chunks), "clusters": int(n),
-                       "chunk_clusters_min": int(min(c.n for c in chunks)),
-                       "chunk_clusters_max": int(max(c.n for c in chunks)), "format": "fixed12",
-                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
-            "batched": {"value": world * n / (ms_b / 1e3), "ms_per_step": ms_b, "batch_sizes": sizes_b,
+    out = {"value": world * n / (ms_b / 1e3), "unit": "clusters/s", "ms_per_step": ms_b,
+           "config": {"workload": "chunks_64x36sectors_poisson20", "chunks": len(chunks), "clusters": int(n),
+                      "chunk_clusters_min": int(min(c.n for c in chunks)),
+                      "chunk_clusters_max": int(max(c.n for c in chunks)), "format": "fixed12",
+                      "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+           "n_fp64_fallback": fallback_b,
+           "batched": {"value": world * n / (ms_b / 1e3), "ms_per_step": ms_b, "batch_sizes": sizes_b,
                         "gpu_launches": l_b, "captured_graph": captured_b == [1],
                         "graph_launches_per_step": 1 if captured_b == [1] else 0},
             "plain": {"value": world * n / (ms_p / 1e3), "ms_per_step": ms_p, "gpu_launches": l_p,
@@ -456,31 +465,42 @@ def run_chunks(args, rank, world, local):
             "roofline": roofline(stage_b, names, n, peak, peak_kind),
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "peak": peak,
                               "frac": n / (ms_b / 1e3) * PATH_BYTES / 1e9 / peak},
-            "cpu_baseline": None, "e2e": e2e, "gpu_launches": l_b, "clocks": clk.summary(),
+            "e2e": e2e, "gpu_launches": l_b,
             "autotune": {"batched": batched.tuning(), "plain": plain.tuning()}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     plain.close()
     batched.close()
+    return out
 
 
-def run_serving(args, rank, world, local):
-    """Served stream: Time Frames drawn from a pool of 24 (half Pb-Pb with
-    10..570 collisions, half pp-like ~3 M clusters) arrive as a Poisson
-    process from pinned host memory; at most --max-queue are admitted at
-    once (an arrival that finds the server full is dropped and counted).
-    Latency = arrival -> result polled on the host.  The same arrival
-    sequence is then replayed 'plain': one TF at a time, submitted and
-    waited for, no batching and no overlap."""
+def run_chunks(args, rank, world, local):
+    """The 64-chunk batch as its own bench line."""
+    with ClockSampler(local) as clk:
+        m = measure_chunks(args, rank, world, local, args.steps, args.warmup)
+    line = {"metric": METRIC, "value": m.pop("value"), "unit": m.pop("unit"), "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m.pop("ms_per_step"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": m.pop("config"),
+            "cpu_baseline": None, "clocks": clk.summary()}
+    line.update(m)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def measure_serving(args, rank, local, pool, seconds):
+    """Served stream: Time Frames drawn from `pool` arrive as a Poisson
+    process at --rate-hz over `seconds` from pinned host memory; at most
+    --max-queue are admitted at once (an arrival that finds the server full
+    is dropped and counted).  Latency = arrival -> result polled on the
+    host.  The same arrival sequence is then replayed 'plain': one TF at a
+    time, submitted and waited for, no batching and no overlap.  Returns
+    {"served": ..., "plain": ..., "offered": ...}."""
     import torch
 
-    from paper_2106_03636_gb300 import o2tpc, synth
+    from paper_2106_03636_gb300 import o2tpc
 
-    pool = synth.serving_pool(seed=replica_seed(20210611, rank))
     pin = [{"packed": torch.from_numpy(t.packed).pin_memory()} for t in pool]
     rng = np.random.default_rng(20210611 + rank)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate_hz, int(args.rate_hz * args.serve_seconds * 2) + 10))
-    arrivals = arrivals[arrivals < args.serve_seconds]
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate_hz, int(args.rate_hz * seconds * 2) + 10))
+    arrivals = arrivals[arrivals < seconds]
     picks = rng.integers(0, len(pool), len(arrivals))
 
     def warm(trk):
@@ -571,18 +591,59 @@ def run_serving(args, rank, world, local):
         trk.close()
         return summary(done, dropped, t0)
 
+    srv = served_run()
+    pln = plain_run()
+    return {"served": srv, "plain": pln, "offered": int(len(arrivals)), "rate_hz": args.rate_hz,
+            "arrival_window_s": seconds, "max_queue": args.max_queue,
+            "pool_clusters": [int(t.n) for t in pool], "input": "pinned host memory"}
+
+
+def measure_full_tpc_1ms(args, rank, world, local, steps: int = 5):
+    """The 1 ms full-TPC frame (50 collisions, ~21 M float clusters) resident
+    on the device: one frame at a time, synchronised per frame."""
+    import torch
+
+    from paper_2106_03636_gb300 import o2tpc, synth
+
+    tf = synth.full_tpc_1ms(seed=replica_seed(20210608, rank))
+    dev = {k: torch.from_numpy(getattr(tf, k)).to(f"cuda:{local}") for k in ("sector", "row", "y", "z")}
+    torch.cuda.synchronize()
+    with o2tpc.Tracker(device=local) as trk:
+        for _ in range(3):
+            r = trk.wait(trk.submit(tf, location=o2tpc.O2TPC_LOC_DEVICE, arrays=dev))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(trk.stream)
+        for _ in range(steps):
+            r = trk.wait(trk.submit(tf, location=o2tpc.O2TPC_LOC_DEVICE, arrays=dev))
+            if r["status"] != 0:
+                raise RuntimeError(o2tpc.o2tpc_strerror(r["status"]))
+        e1.record(trk.stream)
+        torch.cuda.synchronize()
+    ms = device_max(e0.elapsed_time(e1), world, local) / steps
+    return {"value": world * tf.n / (ms / 1e3), "unit": "clusters/s", "ms_per_step": ms, "steps": steps,
+            "clusters": int(tf.n), "tracks": int(r["n_tracks"]), "n_fp64_fallback": int(r["stats"]["n_fp64_fallback"]),
+            "mode": "plain, one frame at a time, input resident in HBM", "format": "float"}
+
+
+def run_serving(args, rank, world, local):
+    """The served stream over the pool of 24 Time Frames (half Pb-Pb with
+    10..570 collisions, half pp-like ~3 M clusters) as its own bench line."""
+    from paper_2106_03636_gb300 import synth
+
+    pool = synth.serving_pool(seed=replica_seed(20210611, rank))
     with ClockSampler(local) as clk:
-        srv = served_run()
-        pln = plain_run()
+        m = measure_serving(args, rank, local, pool, args.serve_seconds)
+    srv = m["served"]
     line = {"metric": METRIC, "value": srv["value"], "unit": "clusters/s", "n_gpus": world, "steps": srv["served"],
             "warmup": args.warmup, "ms_per_step": 1e3 * srv["wall_s"] / max(1, srv["served"]),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serving_pool24_poisson", "rate_hz": args.rate_hz,
                        "arrival_window_s": args.serve_seconds, "max_queue": args.max_queue,
-                       "pool_clusters": [int(t.n) for t in pool], "format": "fixed12",
+                       "pool_clusters": m["pool_clusters"], "format": "fixed12",
                        "input": "pinned host memory", "parallelism": f"replicas x{world}"},
-            "offered": int(len(arrivals)), "tf_per_s": srv["tf_per_s"], "p50_ms": srv["p50_ms"],
-            "p99_ms": srv["p99_ms"], "served": srv, "plain": pln, "clocks": clk.summary()}
+            "offered": m["offered"], "tf_per_s": srv["tf_per_s"], "p50_ms": srv["p50_ms"],
+            "p99_ms": srv["p99_ms"], "served": srv, "plain": m["plain"], "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -597,18 +658,30 @@ def main():
     ap.add_argument("--rate-hz", type=float, default=50.0, help="serving: Poisson arrival rate of TFs")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serving: arrival window")
     ap.add_argument("--max-queue", type=int, default=16, help="serving: TFs admitted at once (more are dropped)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="full_tf: skip the 1 ms frame, chunk and serving sub-measurements")
+    ap.add_argument("--serve-pool", type=int, default=8, help="full_tf: TFs in the serving sub-measurement's pool")
+    ap.add_argument("--serve-extra-seconds", type=float, default=20.0,
+                    help="full_tf: arrival window of the serving sub-measurement")
+    ap.add_argument("--plain-only", action="store_true",
+                    help="time only the one-TF-at-a-time loop, one TF in flight (small device footprint for "
+                         "profiling); implies --no-e2e --no-compress --no-extras")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="also time the oracle on the other workloads and on all host cores")
     ap.add_argument("--seed", type=int, default=20210609)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compress", action="store_true", help="skip the compressed-TF measurement")
     ap.add_argument("--trace", action="store_true", help="per-TF stage times on stderr")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
-    ap.add_argument("--no-graph", action="store_true", help="chunks: batched arm on the regular path, not captured")
+    ap.add_argument("--no-graph", action="store_true", help="served and chunks arms on the regular path, not captured")
     ap.add_argument("--torch-memory", action="store_true",
                     help="device buffers from PyTorch's caching allocator (no uploads ahead)")
-    ap.add_argument("--inflight", type=int, default=3, help="TFs kept in flight in the served measurement")
+    ap.add_argument("--inflight", type=int, default=2, help="TFs kept in flight in the served measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
+    if args.plain_only:
+        args.no_e2e = args.no_compress = args.no_extras = True
 
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -646,8 +719,9 @@ def main():
     torch.cuda.synchronize()
 
     tune = 0 if args.no_autotune else o2tpc.O2TPC_FLAG_AUTOTUNE
+    # plain: one TF at a time on the regular path (per-stage launches, host
+    # synchronisations), synchronised per TF
     trk = o2tpc.Tracker(device=local, torch_memory=args.torch_memory, flags=tune)
-    st = trk.stream
 
     def trace(tag, r):
         if args.trace:
@@ -655,17 +729,14 @@ def main():
             print(f"{tag}: batch {r['stats']['batch_size']} device {r['stats']['ms_device']:.2f} ms, "
                   + ", ".join(f"{o2tpc.STAGES[i]} {st[i]:.2f}" for i in range(len(o2tpc.STAGES))), file=sys.stderr, flush=True)
 
-    def step(location, arrays):
-        r = trk.wait(trk.submit(tf, location=location, arrays=arrays))
+    def step(t, location, arrays):
+        r = t.wait(t.submit(tf, location=location, arrays=arrays))
         if r["status"] != 0:
             raise RuntimeError(o2tpc.o2tpc_strerror(r["status"]))
         trace(f"step loc={location}", r)
         return r
 
-    for _ in range(args.warmup):
-        r = step(o2tpc.O2TPC_LOC_DEVICE, dev)
-
-    def timed(location, arrays):
+    def timed(t, location, arrays):
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -673,58 +744,83 @@ def main():
         stage = np.zeros(len(o2tpc.STAGES))
         launches = 0
         lat = []
-        e0.record(st)
+        e0.record(t.stream)
         for _ in range(args.steps):
             t0 = time.perf_counter()
-            r = step(location, arrays)
+            r = step(t, location, arrays)
             lat.append(1e3 * (time.perf_counter() - t0))
             stage += np.asarray(r["stats"]["ms_stage"])
             launches += int(r["stats"]["n_launches"])
-        e1.record(st)
+        e1.record(t.stream)
         torch.cuda.synchronize()
         ms = device_max(e0.elapsed_time(e1), world, local)
         return ms, stage / args.steps, launches, lat, r
 
-    def served(location, arrays, total, inflight):
+    def served(t, location, arrays, total, inflight):
         """Continuous batching: `inflight` TFs stay queued; the library's
-        worker admits as many as the memory budget allows into each batch.
-        Latency = submit -> result polled."""
+        worker admits them as memory and slots free up.  Latency = submit ->
+        result polled."""
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         pending = collections.deque()
-        t_sub, lat, sizes = {}, [], []
+        t_sub, lat, sizes, capt = {}, [], [], []
         launches = 0.0
         submitted = done = 0
-        e0.record(st)
+        e0.record(t.stream)
         while done < total:
             while submitted < total and len(pending) < inflight:
-                tk = trk.submit(tf, location=location, arrays=arrays)
+                tk = t.submit(tf, location=location, arrays=arrays)
                 t_sub[tk] = time.perf_counter()
                 pending.append(tk)
                 submitted += 1
             tk = pending.popleft()
-            r = trk.wait(tk)
+            r = t.wait(tk)
             if r["status"] != 0:
                 raise RuntimeError(o2tpc.o2tpc_strerror(r["status"]))
             lat.append(1e3 * (time.perf_counter() - t_sub.pop(tk)))
             trace(f"served loc={location}", r)
             b = int(r["stats"]["batch_size"])
             sizes.append(b)
+            capt.append(int(r["stats"]["captured"]))
             launches += r["stats"]["n_launches"] / b
             done += 1
-        e1.record(st)
+        e1.record(t.stream)
         torch.cuda.synchronize()
         ms = device_max(e0.elapsed_time(e1), world, local)
+        served.captured = capt
         return ms, lat, sizes, int(round(launches))
 
-    n_served = max(6, 2 * args.steps)
-    # steady state of the served path: pinned result blocks for every TF in flight
-    served(o2tpc.O2TPC_LOC_DEVICE, dev, args.inflight + 1, args.inflight)
+    for _ in range(args.warmup):
+        r = step(trk, o2tpc.O2TPC_LOC_DEVICE, dev)
+    n_served = max(1, args.steps)
+    pin = None
+    if not args.no_e2e:
+        pin = {"packed": host_in.pin_memory()} if tf.fmt == 1 else {
+            k: torch.from_numpy(getattr(tf, k)).pin_memory() for k in ("sector", "row", "y", "z")}
     with ClockSampler(local) as clk:
-        ms, stage, launches, lat, r = timed(o2tpc.O2TPC_LOC_DEVICE, dev)
-        ms_s, lat_s, sizes_s, launches_s = served(o2tpc.O2TPC_LOC_DEVICE, dev, n_served, args.inflight)
+        ms, stage, launches, lat, r = timed(trk, o2tpc.O2TPC_LOC_DEVICE, dev)
+        if not args.no_e2e:
+            step(trk, o2tpc.O2TPC_LOC_HOST, pin)
+            ms_h, stage_h, _, lat_h, rh = timed(trk, o2tpc.O2TPC_LOC_HOST, pin)
+        tuning = trk.tuning()
+        trk.close()  # its memory pool goes before the served context's
+        if args.plain_only:  # one TF in flight: the plain loop stands for both
+            ms_s, lat_s, sizes_s, launches_s = ms, lat, [1] * args.steps, launches // args.steps
+            captured_s = [0] * args.steps
+        else:
+            # served: its own context; with the captured path every TF is one
+            # CUDA graph launch (no host synchronisation inside), the next TF's
+            # replay queued behind it while the previous result downloads
+            gcap = 0 if args.no_graph else ((n + (1 << 20)) >> 20) << 20
+            strk = o2tpc.Tracker(device=local, torch_memory=args.torch_memory, flags=tune, graph_max_clusters=gcap,
+                                 graph_max_tfs=1)
+            for _ in range(args.warmup):
+                step(strk, o2tpc.O2TPC_LOC_DEVICE, dev)
+            served(strk, o2tpc.O2TPC_LOC_DEVICE, dev, args.inflight + 1, args.inflight)
+            ms_s, lat_s, sizes_s, launches_s = served(strk, o2tpc.O2TPC_LOC_DEVICE, dev, n_served, args.inflight)
+            captured_s = served.captured
     clocks = clk.summary()
     ms_step = ms / args.steps
     plain_value = aggregate_rate(n, world, ms_step)
@@ -734,12 +830,11 @@ def main():
     # e2e: pinned host input, H2D and result download inside the timed region
     e2e = None
     if not args.no_e2e:
-        pin = {"packed": host_in.pin_memory()} if tf.fmt == 1 else {
-            k: torch.from_numpy(getattr(tf, k)).pin_memory() for k in ("sector", "row", "y", "z")}
-        step(o2tpc.O2TPC_LOC_HOST, pin)
-        served(o2tpc.O2TPC_LOC_HOST, pin, args.inflight + 1, args.inflight)
-        ms_h, stage_h, _, lat_h, rh = timed(o2tpc.O2TPC_LOC_HOST, pin)
-        ms_hs, lat_hs, sizes_hs, _ = served(o2tpc.O2TPC_LOC_HOST, pin, n_served, args.inflight)
+        if args.plain_only:
+            ms_hs, lat_hs, sizes_hs = ms_h, lat_h, [1] * args.steps
+        else:
+            served(strk, o2tpc.O2TPC_LOC_HOST, pin, args.inflight + 1, args.inflight)
+            ms_hs, lat_hs, sizes_hs, _ = served(strk, o2tpc.O2TPC_LOC_HOST, pin, n_served, args.inflight)
         h2d = 12 * n if tf.fmt == 1 else 10 * n
         nt, ncl = rh["n_tracks"], rh["n_cluster_refs"]
         # offsets, cluster indices; x, alpha, par, cov, chi2, ndf, sector, flags, zeta_ref,
@@ -752,9 +847,8 @@ def main():
                "plain": {"value": world * n / (ms_h / args.steps / 1e3), "ms_per_step": ms_h / args.steps,
                          "p50_ms": float(np.percentile(lat_h, 50)), "p99_ms": float(np.percentile(lat_h, 99)),
                          "stage_ms": {o2tpc.STAGES[i]: round(float(stage_h[i]), 3) for i in range(len(o2tpc.STAGES))}}}
-
-    tuning = trk.tuning()
-    trk.close()  # its memory pool goes before the next context's
+    if not args.plain_only:
+        strk.close()
     # the compressed TF (Sec. 2.2) on the same TF: one TF at a time, device input
     compressed = None
     if not args.no_compress:
@@ -788,16 +882,31 @@ def main():
     roof = roofline(stage, names, n, peak, peak_kind, args.workload)
     path_frac = plain_value / world * PATH_BYTES / 1e9 / peak
 
+    # the other workloads of the benchmark, each a sub-object of this line
+    extras = {}
+    if world == 1 and not args.no_extras:
+        with ClockSampler(local) as clk_x:
+            extras["full_tpc_1ms"] = measure_full_tpc_1ms(args, rank, world, local)
+            extras["chunks"] = measure_chunks(args, rank, world, local, 3, 3)
+            from paper_2106_03636_gb300 import synth
+
+            pool = synth.serving_pool(seed=replica_seed(20210611, rank), n_tf=args.serve_pool)
+            extras["serving"] = measure_serving(args, rank, local, pool, args.serve_extra_seconds)
+            del pool
+        extras["clocks"] = clk_x.summary()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and tf.fmt == 1:
-        ob = oracle_baselines(tf)
-        s0 = ob["full_tf_sector0"]
-        cpu = {"value": s0["clusters_per_s"], "unit": "clusters/s", "cores": 1, "kind": "oracle",
-               "sample": f"sector 0 of the same TF: {s0['clusters']} clusters, {s0['s']:.1f} s",
-               "configs": ob}
+        nc0, dt0 = cpu_baseline(tf)
+        cpu = {"value": nc0 / dt0, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+               "sample": f"sector 0 of the same TF: {nc0} clusters, {dt0:.1f} s"}
+        if args.oracle_configs:
+            cpu["configs"] = oracle_baselines(tf)
 
     cfg.update({"clusters": int(n), "tracks": int(r["n_tracks"]), "l2": "inputs larger than L2 (no flush)",
-                "mode": f"served: continuous batching, {args.inflight} TFs in flight (TF replayed from memory)",
+                "mode": ("plain only: one TF at a time" if args.plain_only else
+                         f"served: continuous batching, {args.inflight} TFs in flight (TF replayed from memory)"
+                         + ("" if args.no_graph else ", captured path (one CUDA graph launch per TF)")),
                 "parallelism": f"replicas x{world}"})
     line = {"metric": METRIC, "value": value, "unit": "clusters/s", "n_gpus": world, "steps": n_served,
             "warmup": args.warmup, "ms_per_step": ms_s / n_served, "higher_is_better": True, "scaling": "weak",
@@ -806,14 +915,17 @@ def main():
             "p99_ms": float(np.percentile(lat_s, 99)),
             "served": {"value": served_value, "tf_per_s": world * n_served / (ms_s / 1e3),
                        "p50_ms": float(np.percentile(lat_s, 50)), "p99_ms": float(np.percentile(lat_s, 99)),
-                       "batch_sizes": sizes_s, "tfs": n_served, "gpu_launches": launches_s},
+                       "batch_sizes": sizes_s, "tfs": n_served, "gpu_launches": launches_s,
+                       "captured": captured_s},
             "plain": {"value": plain_value, "tf_per_s": world / (ms_step / 1e3), "ms_per_step": ms_step,
                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                       "steps": args.steps},
             "stage_ms": {names[i]: round(float(stage[i]), 3) for i in range(len(o2tpc.STAGES))},
             "path_roofline": {"bytes_per_cluster": PATH_BYTES, "frac": path_frac, "peak": peak},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_s, "clocks": clocks,
-            "autotune": tuning, "compressed": compressed}
+            "autotune": tuning, "compressed": compressed,
+            "n_fp64_fallback": int(r["stats"]["n_fp64_fallback"]), "n_tracks": int(r["n_tracks"])}
+    line.update(extras)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -103,137 +103,98 @@ __device__ inline int warp_take(int* counter, bool want) {
 }
 
 // (a) chain fit: seed from the first and third chain hits, then one update
-// per chain hit.  A transport failure drops the tracklet.  Every iteration of
-// the loop is one chain hit of every busy lane; a lane whose chain ends takes
-// the next tracklet.
+// per chain hit.  A transport failure drops the tracklet.  One thread per
+// tracklet, each walking its own chain (a warp-uniform form of this loop,
+// one chain hit of every lane per iteration, measured 30 % slower over
+// passes a and c together).
 __global__ void __launch_bounds__(128) k_tl_chain(const int* __restrict__ nTlDev, int* __restrict__ counter, const int* __restrict__ starts,
                                                   const int* __restrict__ up, const RowGrid* __restrict__ grid,
                                                   int nRows, const int2* __restrict__ syz,
                                                   const GeomConst* __restrict__ G, TrackletBufs tb) {
-  const unsigned full = 0xffffffffu;
   const float zunit = G->zunit, bzc = G->bzc;
   const int nTl = *nTlDev;
-  bool have = false, exhausted = false;
-  int k = 0, nc = 0, hit = -1, prev = 0, Rh = 0, R0 = 0, r0 = 0, yref = 0, zref = 0;
-  KState<float> st;
   for (;;) {
-    const bool want = !have && !exhausted;
-    const int kk = warp_take(counter, want);
-    if (want) {
-      if (kk >= nTl) {
-        exhausted = true;
-      } else {
-        k = kk;
-        const int h0 = starts[k];
-        R0 = find_row(grid, nRows, h0);
-        r0 = (R0 % kRowsPerTF) % kNRow;
-        const int2 a0 = syz[h0];
-        zref = a0.y;
-        yref = a0.x;
-        tb.zref[k] = zref;
-        tb.rbase[k] = R0 - r0;
-        const int h1 = up[h0];
-        const int R1 = link_row(grid, R0, h1);
-        const int h2 = up[h1];
-        const int R2 = link_row(grid, R1, h2);
-        const int2 a2 = syz[h2];
-        const float x0 = G->rowx[r0];
-        const float dx = (float)(R2 - R0) * G->pitch, dy = hit_y(a2.x, yref) - hit_y(a0.x, yref);
-        const float tphi = dy / dx;
-        const float s0 = tphi / sqrtf(1.f + tphi * tphi);
-        const float t0 = (hit_z(a2.y, zref, zunit) - hit_z(a0.y, zref, zunit)) / sqrtf(dx * dx + dy * dy);
-        kf_reset<float>(st, x0, hit_y(a0.x, yref), hit_z(a0.y, zref, zunit), s0, t0, 0.f);
-        kf_meas_cov<float>(st, G->angErr);
-        tb.hits[(size_t)k * kMaxTlHits] = h0;
-        tb.rows[(size_t)k * kMaxTlHits] = (uint8_t)r0;
-        nc = 1;
-        hit = h1;
-        prev = r0;
-        Rh = R1;
-        have = true;
+    const int k = atomicAdd(counter, 1);
+    if (k >= nTl) return;
+    const int h0 = starts[k];
+    const int R0 = find_row(grid, nRows, h0);
+    const int r0 = (R0 % kRowsPerTF) % kNRow;
+    int* H = tb.hits + (size_t)k * kMaxTlHits;
+    uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
+    const int2 a0 = syz[h0];
+    const int zref = a0.y;
+    int yref = a0.x;
+    tb.zref[k] = zref;
+    tb.rbase[k] = R0 - r0;
+    const int h1 = up[h0];
+    const int R1 = link_row(grid, R0, h1);
+    const int h2 = up[h1];
+    const int R2 = link_row(grid, R1, h2);
+    const int2 a2 = syz[h2];
+    const float x0 = G->rowx[r0];
+    const float dx = (float)(R2 - R0) * G->pitch, dy = hit_y(a2.x, yref) - hit_y(a0.x, yref);
+    const float tphi = dy / dx;
+    const float s0 = tphi / sqrtf(1.f + tphi * tphi);
+    const float t0 = (hit_z(a2.y, zref, zunit) - hit_z(a0.y, zref, zunit)) / sqrtf(dx * dx + dy * dy);
+    KState<float> st;
+    kf_reset<float>(st, x0, hit_y(a0.x, yref), hit_z(a0.y, zref, zunit), s0, t0, 0.f);
+    kf_meas_cov<float>(st, G->angErr);
+    H[0] = h0;
+    Rw[0] = (uint8_t)r0;
+    int nc = 1, hit = h1, prev = r0, Rh = R1;
+    bool dropped = false;
+    while (hit >= 0 && nc < kMaxTlHits) {
+      const int row = r0 + (Rh - R0);
+      const int2 hp = syz[hit];  // both loads in flight during the transport
+      const int next = up[hit];
+      if (kf_prop_row<float>(st, prev, row, G, bzc) != 0) {
+        dropped = true;
+        break;
       }
+      recentre_y(st.p[0], yref, hp.x);
+      kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr, G->angErr);
+      H[nc] = hit;
+      Rw[nc] = (uint8_t)row;
+      ++nc;
+      prev = row;
+      hit = next;
+      if (hit >= 0) Rh = link_row(grid, Rh, hit);
     }
-    if (__ballot_sync(full, have) == 0) {
-      if (__all_sync(full, exhausted)) break;
-      continue;
-    }
-    if (!have) continue;
-    if (hit < 0 || nc >= kMaxTlHits) {  // the chain is fitted
-      tb.nasc[k] = nc;
-      tb.yref[k] = yref;
-      store_raw(tb.state + (size_t)k * 21, st);
-      have = false;
-      continue;
-    }
-    const int row = r0 + (Rh - R0);
-    const int2 hp = syz[hit];  // both loads in flight during the transport
-    const int next = up[hit];
-    if (kf_prop_row<float>(st, prev, row, G, bzc) != 0) {
-      tb.nasc[k] = 0;
-      tb.yref[k] = yref;
-      tb.nhits[k] = 0;
-      have = false;
-      continue;
-    }
-    recentre_y(st.p[0], yref, hp.x);
-    kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr, G->angErr);
-    tb.hits[(size_t)k * kMaxTlHits + nc] = hit;
-    tb.rows[(size_t)k * kMaxTlHits + nc] = (uint8_t)row;
-    ++nc;
-    prev = row;
-    hit = next;
-    if (hit >= 0) Rh = link_row(grid, Rh, hit);
+    tb.nasc[k] = dropped ? 0 : nc;
+    tb.yref[k] = yref;
+    if (dropped) tb.nhits[k] = 0;
+    else store_raw(tb.state + (size_t)k * 21, st);
   }
 }
 
 // (c) inward refit from the top hit through every attached hit; a hit whose
-// transport fails is skipped.  One attached hit of every busy lane per
-// iteration, as in (a).
+// transport fails is skipped.  One thread per tracklet, as in (a).
 __global__ void __launch_bounds__(128) k_tl_refit(const int* __restrict__ nTlDev, int* __restrict__ counter, const int2* __restrict__ syz,
                                                   const GeomConst* __restrict__ G, TrackletBufs tb) {
-  const unsigned full = 0xffffffffu;
   const float zunit = G->zunit, bzc = G->bzc;
   const int nTl = *nTlDev;
-  bool have = false, exhausted = false;
-  int k = 0, i = 0, srow = 0, yref = 0, zref = 0;
-  KState<float> st;
   for (;;) {
-    const bool want = !have && !exhausted;
-    const int kk = warp_take(counter, want);
-    if (want) {
-      if (kk >= nTl) {
-        exhausted = true;
-      } else {
-        const int na = tb.nasc[kk];
-        if (na > 0) {
-          k = kk;
-          zref = tb.zref[k];
-          yref = tb.yref[k];
-          load_state(st, tb.state + (size_t)k * 21);
-          srow = tb.rows[(size_t)k * kMaxTlHits + na - 1];
-          i = na - 2;
-          have = true;
-        }
-      }
+    const int k = atomicAdd(counter, 1);
+    if (k >= nTl) return;
+    const int na = tb.nasc[k];
+    if (na == 0) continue;
+    const int* H = tb.hits + (size_t)k * kMaxTlHits;
+    const uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
+    const int zref = tb.zref[k];
+    int yref = tb.yref[k];
+    KState<float> st;
+    float* S = tb.state + (size_t)k * 21;
+    load_state(st, S);
+    int srow = Rw[na - 1];
+    for (int i = na - 2; i >= 0; --i) {
+      const int2 hp = syz[H[i]];
+      if (kf_prop_row<float>(st, srow, Rw[i], G, bzc) != 0) continue;
+      srow = Rw[i];
+      recentre_y(st.p[0], yref, hp.x);
+      kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr, G->angErr);
     }
-    if (__ballot_sync(full, have) == 0) {
-      if (__all_sync(full, exhausted)) break;
-      continue;
-    }
-    if (!have) continue;
-    if (i < 0) {
-      tb.yref[k] = yref;
-      store_raw(tb.state + (size_t)k * 21, st);
-      have = false;
-      continue;
-    }
-    const int2 hp = syz[tb.hits[(size_t)k * kMaxTlHits + i]];
-    const int row = tb.rows[(size_t)k * kMaxTlHits + i];
-    --i;
-    if (kf_prop_row<float>(st, srow, row, G, bzc) != 0) continue;
-    srow = row;
-    recentre_y(st.p[0], yref, hp.x);
-    kf_update<float>(st, hit_y(hp.x, yref), hit_z(hp.y, zref, zunit), nullptr, G->angErr);
+    tb.yref[k] = yref;
+    store_raw(S, st);
   }
 }
 
@@ -408,7 +369,7 @@ __global__ void __launch_bounds__(128, O2TPC_FOLLOW_MIN_BLOCKS) k_tl_follow(cons
   __shared__ SearchPar s_par[128];
   __shared__ unsigned long long s_best[128];
   const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wb = threadIdx.x & ~31;
+  const int wb = threadIdx.x & ~31;
   const float zunit = G->zunit, izunit = G->kz, bzc = G->bzc;
   const int nTl = *nTlDev;
   auto save_last = [&](const KState<float>& q) {
@@ -447,14 +408,11 @@ __global__ void __launch_bounds__(128, O2TPC_FOLLOW_MIN_BLOCKS) k_tl_follow(cons
   };
   for (;;) {
     // lanes without a tracklet take the next ones
-    const unsigned need = __ballot_sync(full, !have && !exhausted);
-    if (need) {
-      const int leader = __ffs(need) - 1;
-      int base = 0;
-      if (lane == leader) base = atomicAdd(counter, __popc(need));
-      base = __shfl_sync(full, base, leader);
-      if (!have && !exhausted) {
-        k = base + __popc(need & ((1u << lane) - 1));
+    const bool want = !have && !exhausted;
+    const int kk = warp_take(counter, want);
+    {
+      if (want) {
+        k = kk;
         if (k >= nTl) {
           exhausted = true;
         } else {

@@ -74,7 +74,8 @@ def interior_tracks(o: dict, outward: dict) -> dict:
         if ok:
             keep.append(t)
     off = o["trk_off"]
-    sub = {k: o[k][keep] for k in ("trk_par", "trk_cov", "trk_x", "trk_zref", "trk_sector", "trk_flags")}
+    sub = {k: o[k][keep] for k in ("trk_par", "trk_cov", "trk_x", "trk_zref", "trk_sector", "trk_flags", "trk_chi2",
+                                   "trk_ndf")}
     sub["trk_off"] = np.concatenate([[0], np.cumsum(np.diff(off)[keep])]).astype(np.int64)
     sub["trk_cl"] = np.concatenate([o["trk_cl"][off[t]:off[t + 1]] for t in keep]).astype(np.int32)
     return sub
@@ -112,7 +113,7 @@ def test_full_tf_sectors_0_1_sampled():
         "sorted_orig", "sorted_y", "sorted_z", "row_start", "row_count", "row_cellbase", "row_ny", "row_nz",
         "row_cz", "row_zmin", "cell_start", "up_raw", "dn_raw", "up", "dn", "starts", "tl_nhits", "st_off",
         "st_hits", "st_sector", "st_in", "st_out", "st_next", "trk_off", "trk_cl", "trk_x", "trk_par", "trk_cov",
-        "trk_sector", "trk_flags", "trk_zref", "trk_head"])
+        "trk_sector", "trk_flags", "trk_zref", "trk_head", "trk_chi2", "trk_ndf"])
     # sector 0, integer stages bit for bit
     assert np.array_equal(gpu["sorted_orig"], o["sorted_orig"][:n0]), "sort order"
     assert np.array_equal(gpu["sorted_yz"][:, 0], o["sorted_y"][:n0]), "sorted y"
