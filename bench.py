@@ -73,8 +73,12 @@ STAGE_BYTES = {
 # workload, valid while the kernel's sources hash to the recorded value;
 # otherwise the line says null.
 MEASURED_TRAFFIC = {
-    ("k_tl_out", "full_tf"): {"bytes": 8399.0e6 + 3496.7e6, "sources_sha256_16": "66461f3c31c50bde",
-                              "sources": ["k_track.cu", "o2tpc_internal.cuh"]},
+    # k_tl_follow<1> on the 1 ms frame (21.2 M clusters at the same 50 kHz
+    # density): 1.265 GB read + 0.319 GB written, scaled by 242.0 / 21.2 to
+    # the 128-orbit TF (profiles/k_tl_follow_full_tpc_1ms.md)
+    ("k_tl_follow<1>", "full_tf"): {"bytes": (1265.5e6 + 319.1e6) * 241.96 / 21.21,
+                                    "sources_sha256_16": "10140008fb4f8075",
+                                    "sources": ["k_track.cu", "o2tpc_internal.cuh"]},
 }
 
 
@@ -92,7 +96,7 @@ def measured_traffic(kernel: str, workload: str):
 
 
 # kernels (or single-kernel steps) the roofline line can name
-ROOF_KERNELS = {"tl_out": "k_tl_out", "tl_in": "k_tl_in", "neighbours": "k_neighbours",
+ROOF_KERNELS = {"tl_out": "k_tl_follow<1>", "tl_in": "k_tl_follow<-1>", "neighbours": "k_neighbours",
                 "refit": "k_final_refit", "sort": "k_row_scatter+k_cell_sort", "selection": "k_ownership+k_segments",
                 "sector_fit": "k_sector_fit", "merge": "k_merge_*"}
 PATH_BYTES = 65.0

@@ -34,7 +34,7 @@ def test_dominant_kernel_and_roofline():
     k, ms = bench.dominant_kernel(stage, names)
     assert (k, ms) == ("tl_out", 30.0)
     r = bench.roofline(stage, names, 242_000_000, 6800.0, "measured")
-    assert r["kernel"] == "k_tl_out" and r["bound"] == "hbm"
+    assert r["kernel"] == "k_tl_follow<1>" and r["bound"] == "hbm"
     assert abs(r["achieved"] - 12.0 * 242e6 / 0.030 / 1e9) < 1e-6
     assert abs(r["frac"] - r["achieved"] / 6800.0) < 1e-12
 
@@ -55,9 +55,9 @@ def test_recorded_traffic_follows_the_sources(monkeypatch):
     for f in srcs:
         with open(os.path.join(bench.ROOT, "paper_2106_03636_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    rec = {("k_tl_out", "full_tf"): {"bytes": 1.0e9, "sources_sha256_16": h.hexdigest()[:16], "sources": srcs},
-           ("k_tl_in", "full_tf"): {"bytes": 1.0e9, "sources_sha256_16": "0" * 16, "sources": srcs}}
+    rec = {("k_tl_follow<1>", "full_tf"): {"bytes": 1.0e9, "sources_sha256_16": h.hexdigest()[:16], "sources": srcs},
+           ("k_tl_follow<-1>", "full_tf"): {"bytes": 1.0e9, "sources_sha256_16": "0" * 16, "sources": srcs}}
     monkeypatch.setattr(bench, "MEASURED_TRAFFIC", rec)
-    assert bench.measured_traffic("k_tl_out", "full_tf") == 1.0e9
-    assert bench.measured_traffic("k_tl_in", "full_tf") is None
-    assert bench.measured_traffic("k_tl_out", "chunks") is None
+    assert bench.measured_traffic("k_tl_follow<1>", "full_tf") == 1.0e9
+    assert bench.measured_traffic("k_tl_follow<-1>", "full_tf") is None
+    assert bench.measured_traffic("k_tl_follow<1>", "chunks") is None
