@@ -136,7 +136,10 @@ typedef struct {
    * owns (freed memory is kept for the next batch until o2tpc_destroy), and
    * host-resident inputs still waiting in the queue are uploaded ahead on a
    * second (copy) stream while earlier batches compute; these copies use up
-   * to mem_budget / 8 device bytes beyond mem_budget. */
+   * to mem_budget / 8 device bytes beyond mem_budget.  dev_alloc must
+   * return blocks aligned to 256 bytes, as cudaMalloc does; a block that
+   * is not 16-byte aligned is handed back to dev_free and the call fails
+   * with O2TPC_ENOMEM. */
   void* (*dev_alloc)(size_t bytes, void* user);
   void (*dev_free)(void* ptr, void* user);
   void* alloc_user;

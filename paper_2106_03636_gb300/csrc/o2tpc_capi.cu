@@ -220,6 +220,10 @@ struct Ctx {
     void* p = nullptr;
     if (cfg.dev_alloc) {
       p = cfg.dev_alloc(bytes, cfg.alloc_user);
+      if (p && (reinterpret_cast<uintptr_t>(p) & 15)) {  // vector and bulk copies need 16 B
+        if (cfg.dev_free) cfg.dev_free(p, cfg.alloc_user);
+        p = nullptr;
+      }
     } else {
       if (cudaMallocFromPoolAsync(&p, bytes, pool, s) != cudaSuccess) {
         cudaGetLastError();
