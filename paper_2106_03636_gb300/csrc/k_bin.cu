@@ -194,28 +194,53 @@ __global__ void k_cell_sentinel(int* __restrict__ cellStart, const int* __restri
 
 // K3a: scatter each tile's clusters into its row bucket at
 // rowStart + (tile offset within the row) + (unordered rank inside the tile).
-// Records: {y_u, zeta_u, batch input index, cell}.
-__global__ void __launch_bounds__(512) k_row_scatter(const TFDesc* __restrict__ tfs, const int2* __restrict__ tiles,
-                                                     int tileSize, const GeomConst* __restrict__ G,
-                                                     const int* __restrict__ tileStats,
-                                                     const RowGrid* __restrict__ grid, int4* __restrict__ bucket) {
+// Records: {y_u, zeta_u, batch input index, cell}.  Persistent: one CTA per
+// SM takes the tiles in turn, so that only one tile per SM is open at a time
+// and the partly written 32-byte sectors of its 5472 row segments stay in L2
+// until they fill (with one CTA per tile the whole grid's open sectors
+// outgrew L2 on a 128-orbit TF).  Each thread decodes kU clusters before the
+// first of their scattered stores, which keeps kU input loads in flight.
+#ifndef O2TPC_SCATTER_THREADS
+#define O2TPC_SCATTER_THREADS 1024
+#endif
+#ifndef O2TPC_SCATTER_UNROLL
+#define O2TPC_SCATTER_UNROLL 4
+#endif
+constexpr int kScatterT = O2TPC_SCATTER_THREADS, kScatterU = O2TPC_SCATTER_UNROLL;
+__global__ void __launch_bounds__(kScatterT) k_row_scatter(const TFDesc* __restrict__ tfs, const int2* __restrict__ tiles,
+                                                           int nTiles, int tileSize, const GeomConst* __restrict__ G,
+                                                           const int* __restrict__ tileStats,
+                                                           const RowGrid* __restrict__ grid, int4* __restrict__ bucket) {
   __shared__ int s_cur[kRowsPerTF];
-  const int tile = blockIdx.x;
-  const int2 td = tiles[tile];
-  const TFDesc t = tfs[td.x];
-  const int Rbase = td.x * kRowsPerTF;
-  const int* ts = tileStats + (size_t)tile * 3 * kRowsPerTF;
-  for (int i = threadIdx.x; i < kRowsPerTF; i += blockDim.x) s_cur[i] = grid[Rbase + i].start + ts[i];
-  __syncthreads();
-  const int b = td.y, e = min(t.n, td.y + tileSize);
-  for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-    int lr, yu, zu;
-    decode(t, i, G, lr, yu, zu);
-    const RowGrid g = grid[Rbase + lr];
-    int iy = cell_iy(g, G->npads[lr % kNRow], yu);
-    int iz = cell_iz_floor(zu, g);  // zu >= zmin of its row: 0..nz-1
-    int slot = atomicAdd(&s_cur[lr], 1);
-    bucket[slot] = make_int4(yu, zu, t.inBase + i, iz * g.ny + iy);
+  for (int tile = blockIdx.x; tile < nTiles; tile += gridDim.x) {
+    const int2 td = tiles[tile];
+    const TFDesc t = tfs[td.x];
+    const int b = td.y, e = min(t.n, td.y + tileSize);
+    if (b >= e) continue;  // an unused tile slot (block-uniform)
+    const int Rbase = td.x * kRowsPerTF;
+    const int* ts = tileStats + (size_t)tile * 3 * kRowsPerTF;
+    __syncthreads();  // the previous tile's slot counters are no longer in use
+    for (int i = threadIdx.x; i < kRowsPerTF; i += kScatterT) s_cur[i] = grid[Rbase + i].start + ts[i];
+    __syncthreads();
+    for (int i0 = b + threadIdx.x; i0 < e; i0 += kScatterT * kScatterU) {
+      int lr[kScatterU], yu[kScatterU], zu[kScatterU];
+#pragma unroll
+      for (int u = 0; u < kScatterU; ++u) {
+        const int i = i0 + u * kScatterT;
+        if (i < e) decode(t, i, G, lr[u], yu[u], zu[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kScatterU; ++u) {
+        const int i = i0 + u * kScatterT;
+        if (i < e) {
+          const RowGrid g = grid[Rbase + lr[u]];
+          const int iy = cell_iy(g, G->npads[lr[u] % kNRow], yu[u]);
+          const int iz = cell_iz_floor(zu[u], g);  // zu >= zmin of its row: 0..nz-1
+          const int slot = atomicAdd(&s_cur[lr[u]], 1);
+          bucket[slot] = make_int4(yu[u], zu[u], t.inBase + i, iz * g.ny + iy);
+        }
+      }
+    }
   }
 }
 
@@ -224,6 +249,10 @@ __global__ void __launch_bounds__(512) k_row_scatter(const TFDesc* __restrict__ 
 // by input index).  Cell counters live in shared memory when the row has at
 // most kSmemCells cells, else in the global scratch (cellStart itself).
 constexpr int kSmemCells = 12288;
+#ifndef O2TPC_CELL_REGSORT
+#define O2TPC_CELL_REGSORT 1
+#endif
+constexpr int kRegSort = 8;
 
 template <int kT>
 __global__ void __launch_bounds__(kT) k_cell_sort(const RowGrid* __restrict__ grid, const int4* __restrict__ bucket,
@@ -279,10 +308,47 @@ __global__ void __launch_bounds__(kT) k_cell_sort(const RowGrid* __restrict__ gr
     sorig[pos] = rec.z;
   }
   __syncthreads();
-  // restore input order inside each cell
+  // restore input order inside each cell: a cell of at most kRegSort hits is
+  // loaded at once and sorted in registers (odd-even transposition network);
+  // a larger one by insertion in place
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {
     int b = cellStart[g.cellBase + c];
     int e = (c + 1 < nc) ? cellStart[g.cellBase + c + 1] : g.start + g.count;
+#if O2TPC_CELL_REGSORT
+    const int m = e - b;
+    if (m <= 1) continue;
+    if (m <= kRegSort) {
+      int ko[kRegSort];
+      int2 kv[kRegSort];
+#pragma unroll
+      for (int j = 0; j < kRegSort; ++j) {
+        ko[j] = (j < m) ? sorig[b + j] : INT_MAX;  // input indices are unique and < INT_MAX
+        kv[j] = (j < m) ? syz[b + j] : make_int2(0, 0);
+      }
+#pragma unroll
+      for (int rd = 0; rd < kRegSort; ++rd) {
+#pragma unroll
+        for (int j = rd & 1; j + 1 < kRegSort; j += 2) {
+          if (ko[j] > ko[j + 1]) {
+            const int tk = ko[j];
+            ko[j] = ko[j + 1];
+            ko[j + 1] = tk;
+            const int2 tv = kv[j];
+            kv[j] = kv[j + 1];
+            kv[j + 1] = tv;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kRegSort; ++j) {
+        if (j < m) {
+          sorig[b + j] = ko[j];
+          syz[b + j] = kv[j];
+        }
+      }
+      continue;
+    }
+#endif
     for (int i = b + 1; i < e; ++i) {
       int ko = sorig[i];
       int2 kv = syz[i];
@@ -322,10 +388,19 @@ void launch_grid(int nRows, const int* rowCnt, const int* rowMin, const int* row
   ++g_launch_count;
 }
 
+// CTAs per SM of the persistent row scatter
+#ifndef O2TPC_SCATTER_CTAS_PER_SM
+#define O2TPC_SCATTER_CTAS_PER_SM 1
+#endif
+
 void launch_row_scatter(const TFDesc* tfs, const int2* tiles, int nTiles, int tileSize, const GeomConst* G,
                         const int* tileStats, const RowGrid* grid, int4* bucket, cudaStream_t st) {
   if (nTiles > 0) {
-    k_row_scatter<<<nTiles, 512, 0, st>>>(tfs, tiles, tileSize, G, tileStats, grid, bucket);
+    int dev = 0, nSM = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nSM, cudaDevAttrMultiProcessorCount, dev);
+    const int nb = nSM > 0 ? std::min(nTiles, nSM * O2TPC_SCATTER_CTAS_PER_SM) : nTiles;
+    k_row_scatter<<<nb, kScatterT, 0, st>>>(tfs, tiles, nTiles, tileSize, G, tileStats, grid, bucket);
     ++g_launch_count;
   }
 }

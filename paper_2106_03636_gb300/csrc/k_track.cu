@@ -543,6 +543,33 @@ __device__ inline TlKey tl_key(const OwnCtx& o, const TrackletBufs& tb, int k, i
   return t;
 }
 
+// Slots [0, 8) of a tracklet's hit list from a 16-byte aligned address (a
+// tracklet's 152 slots start on 608-byte boundaries).  Slots past the
+// tracklet's hits hold stale values that the callers mask.
+__device__ inline void load_hits8(const int* H, int (&hh)[8]) {
+  const int4 a = reinterpret_cast<const int4*>(H)[0], b = reinterpret_cast<const int4*>(H)[1];
+  hh[0] = a.x; hh[1] = a.y; hh[2] = a.z; hh[3] = a.w;
+  hh[4] = b.x; hh[5] = b.y; hh[6] = b.z; hh[7] = b.w;
+}
+
+// Ownership bits of slots [0, nh) of a tracklet into this thread's column of
+// own[5][128] (bit i % 32 of word i / 32 set: slot i's hit is owned by it).
+__device__ inline void owned_bits(const OwnCtx& o, const TlKey& key, const int* H, int nh, unsigned (*own)[128]) {
+  for (int i = 0; i < nh; i += 8) {
+    int hh[8];
+    load_hits8(H + i, hh);
+    bool ok[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) ok[u] = (i + u < nh) && key.owns(o, hh[u]);
+    unsigned bits = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) bits |= (unsigned)ok[u] << u;
+    if ((i & 31) == 0) own[i >> 5][threadIdx.x] = bits;
+    else own[i >> 5][threadIdx.x] |= bits << (i & 31);
+  }
+}
+__device__ inline bool is_owned(const unsigned (*own)[128], int i) { return (own[i >> 5][threadIdx.x] >> (i & 31)) & 1u; }
+
 // K8a: hit ownership (atomicMax of the key; a hit already holding a larger
 // key is skipped without an atomic).
 __global__ void k_ownership(const int* __restrict__ nTlDev, OwnCtx o, TrackletBufs tb) {
@@ -552,17 +579,27 @@ __global__ void k_ownership(const int* __restrict__ nTlDev, OwnCtx o, TrackletBu
   if (nh < kMinHits) return;
   const TlKey key = tl_key(o, tb, k, nh);
   const int* H = tb.hits + (size_t)k * kMaxTlHits;
-  if (key.wide) {
-    auto* w = static_cast<unsigned long long*>(o.w);
-    for (int i = 0; i < nh; ++i) {
-      const int h = H[i];
-      if (w[h] < key.k64) atomicMax(&w[h], key.k64);
-    }
-  } else {
-    auto* w = static_cast<unsigned*>(o.w);
-    for (int i = 0; i < nh; ++i) {
-      const int h = H[i];
-      if (w[h] < key.k32) atomicMax(&w[h], key.k32);
+  // 8 hits per step (two 16-byte loads; the 152 slots are a multiple of 8),
+  // their 8 ownership words loaded before the first atomic
+  for (int i = 0; i < nh; i += 8) {
+    int hh[8];
+    load_hits8(H + i, hh);
+    if (key.wide) {
+      auto* w = static_cast<unsigned long long*>(o.w);
+      unsigned long long v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (i + u < nh) ? w[hh[u]] : ~0ull;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (v[u] < key.k64) atomicMax(&w[hh[u]], key.k64);
+    } else {
+      auto* w = static_cast<unsigned*>(o.w);
+      unsigned v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = (i + u < nh) ? w[hh[u]] : ~0u;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (v[u] < key.k32) atomicMax(&w[hh[u]], key.k32);
     }
   }
 }
@@ -573,6 +610,7 @@ __global__ void __launch_bounds__(128) k_segments_count(const int* __restrict__ 
                                                         int* __restrict__ nSeg, int* __restrict__ nSegHits) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= *nTlDev) return;
+  __shared__ unsigned s_own[(kMaxTlHits + 31) / 32][128];
   const int nh = tb.nhits[k];
   int cs = 0, ch = 0;
   if (nh >= kMinHits) {
@@ -580,10 +618,11 @@ __global__ void __launch_bounds__(128) k_segments_count(const int* __restrict__ 
     const int nasc = tb.nasc[k], nd = nh - nasc;
     const int* H = tb.hits + (size_t)k * kMaxTlHits;
     const uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
+    owned_bits(o, key, H, nh, s_own);
     int m = 0, prev = -1000;
     for (int j = 0; j < nh; ++j) {
       const int i = (j < nd) ? (nh - 1 - j) : (j - nd);
-      if (!key.owns(o, H[i])) continue;
+      if (!is_owned(s_own, i)) continue;
       const int row = Rw[i];
       if (m > 0 && row - prev - 1 > kMaxMiss) {
         if (m >= kMinHits) { ++cs; ch += m; }
@@ -612,10 +651,12 @@ __global__ void __launch_bounds__(128) k_segments_write(const int* __restrict__ 
   if (k >= *nTlDev) return;
   const int nh = tb.nhits[k];
   if (nh < kMinHits || segPos[k + 1] == segPos[k]) return;
+  __shared__ unsigned s_own[(kMaxTlHits + 31) / 32][128];
   const TlKey key = tl_key(o, tb, k, nh);
   const int nasc = tb.nasc[k], nd = nh - nasc;
   const int* H = tb.hits + (size_t)k * kMaxTlHits;
   const uint8_t* Rw = tb.rows + (size_t)k * kMaxTlHits;
+  owned_bits(o, key, H, nh, s_own);
   const int ts = tb.rbase[k] / kNRow;
   const int tf = ts / kNSec, sector = ts % kNSec;
   // the slots end at the tracklet's last kept hit, and at the capacity
@@ -638,8 +679,8 @@ __global__ void __launch_bounds__(128) k_segments_write(const int* __restrict__ 
   };
   for (int j = 0; j < nh; ++j) {
     const int i = (j < nd) ? (nh - 1 - j) : (j - nd);
+    if (!is_owned(s_own, i)) continue;
     const int h = H[i];
-    if (!key.owns(o, h)) continue;
     const int row = Rw[i];
     if (m > 0 && row - prev - 1 > kMaxMiss) flush();
     if (m == 0) first = h;
