@@ -73,12 +73,21 @@ STAGE_BYTES = {
 # workload, valid while the kernel's sources hash to the recorded value;
 # otherwise the line says null.
 MEASURED_TRAFFIC = {
-    # k_tl_follow<1> on the 1 ms frame (21.2 M clusters at the same 50 kHz
-    # density): 1.265 GB read + 0.319 GB written, scaled by 242.0 / 21.2 to
-    # the 128-orbit TF (profiles/k_tl_follow_full_tpc_1ms.md)
-    ("k_tl_follow<1>", "full_tf"): {"bytes": (1265.5e6 + 319.1e6) * 241.96 / 21.21,
-                                    "sources_sha256_16": "10140008fb4f8075",
+    # measured at full size: one ncu pass over every launch of the plain-only
+    # bench on the 128-orbit TF (gpu__time_duration.sum, dram__bytes_read.sum,
+    # dram__bytes_write.sum), the last TF's launches (profiles/launches_full_tf.md)
+    ("k_tl_follow<1>", "full_tf"): {"bytes": 11453599488 + 4863723520,
+                                    "sources_sha256_16": "58c898f3f3c41a05",
                                     "sources": ["k_track.cu", "o2tpc_internal.cuh"]},
+    ("k_tl_follow<-1>", "full_tf"): {"bytes": 25006988544 + 4140118528,
+                                     "sources_sha256_16": "58c898f3f3c41a05",
+                                     "sources": ["k_track.cu", "o2tpc_internal.cuh"]},
+    ("k_neighbours", "full_tf"): {"bytes": 2181558272 + 1895681280,
+                                  "sources_sha256_16": "d45000136ebb10df",
+                                  "sources": ["k_ca.cu", "o2tpc_internal.cuh"]},
+    ("k_row_scatter+k_cell_sort", "full_tf"): {"bytes": 6347177472 + 6376546560 + 12438317568 + 7191981312,
+                                               "sources_sha256_16": "b5dd6a9e05f5fc61",
+                                               "sources": ["k_bin.cu", "o2tpc_internal.cuh"]},
 }
 
 
