@@ -183,15 +183,18 @@ struct Ctx {
   cudaEvent_t evTl[4] = {};  // ends of the four tracklet passes
   cudaEvent_t evCtf[2] = {};  // the compression step
   o2tpc_tuning tune{};       // launch shapes in use (autotuner results)
-  // captured path: arena, graph, and the event after the last replay's
-  // result copies (the next replay overwrites the result arrays)
+  // captured path: arena and two graphs, identical but for the set of result
+  // arrays they write (replays alternate between them, so a replay never
+  // waits for the previous replay's results to download), and per set the
+  // event after the result copies of its last replay
   std::unique_ptr<GraphArena> graph;
   void* graphMem = nullptr;
-  cudaGraphExec_t graphExec = nullptr;
+  cudaGraphExec_t graphExec[2] = {nullptr, nullptr};
   long long graphKernels = 0;
   int graphNf = 0, graphSort = 0;
-  cudaEvent_t graphDl = nullptr;
-  bool graphDlRecorded = false;
+  cudaEvent_t graphDl[2] = {nullptr, nullptr};
+  bool graphDlRecorded[2] = {false, false};
+  int graphSlot = 0;  // the set the next replay writes
   // copy stream, its thread and the bytes uploaded ahead of their batch
   cudaStream_t upStream = nullptr;
   std::thread uploader;
@@ -415,6 +418,7 @@ struct Pipe {
   OutBufs ob{};
   const int *trkTfBegin = nullptr, *stTfBegin = nullptr, *tlTfBegin = nullptr;
   const unsigned* dErr = nullptr;
+  int graphSlot = 0;                 // captured path: the set of result arrays written
   std::shared_ptr<BatchMem> outMem;  // result arrays freed after the download (regular path)
   uint8_t* ctf = nullptr;            // compressed TFs of the batch, at ctfOff[i]
   std::vector<long long> ctfOff;
@@ -507,36 +511,48 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
     CK(cudaMemcpyAsync(A.cnt, h + b1 + b2, b3, cudaMemcpyHostToDevice, st));
     if (nColl) CK(cudaMemcpyAsync(A.coll, h + b1 + b2 + b3, b4, cudaMemcpyHostToDevice, st));
   }
-  if (c->graphDlRecorded) CK(cudaStreamWaitEvent(st, c->graphDl, 0));
-  if (c->graphExec && (c->graphNf != c->tune.nf_hits_per_block * 2 + c->tune.nf_staged ||
-                       c->graphSort != c->tune.sort_threads_per_row)) {
-    cudaGraphExecDestroy(c->graphExec);
-    c->graphExec = nullptr;
-  }
-  if (!c->graphExec) {
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-    const long long before = g_launch_count;
-    graph_enqueue(A, c->dGeom, c->tune.nf_hits_per_block, c->tune.nf_staged != 0, c->tune.sort_threads_per_row,
-                  (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, st, (c->cfg.flags & O2TPC_FLAG_COOP_SEARCH) != 0,
-                  (c->cfg.flags & O2TPC_FLAG_ROW_STEP2) != 0);
-    const cudaError_t ce = cudaStreamEndCapture(st, &g);
-    c->graphKernels = g_launch_count - before;
-    if (ce != cudaSuccess || !g || cudaGraphInstantiate(&c->graphExec, g, 0) != cudaSuccess) {
-      cudaGetLastError();
-      if (g) cudaGraphDestroy(g);
-      c->graphExec = nullptr;
-      std::fprintf(stderr, "o2tpc: graph capture failed; batches run on the regular path\n");
-      c->graph.reset();
-      return false;
+  // this replay writes result set `slot`, whose last results (two replays
+  // back) must have reached the host first
+  const int slot = c->graphSlot;
+  if (c->graphDlRecorded[slot]) CK(cudaStreamWaitEvent(st, c->graphDl[slot], 0));
+  if (c->graphExec[0] && (c->graphNf != c->tune.nf_hits_per_block * 2 + c->tune.nf_staged ||
+                          c->graphSort != c->tune.sort_threads_per_row)) {
+    for (auto& e : c->graphExec) {
+      if (e) cudaGraphExecDestroy(e);
+      e = nullptr;
     }
-    cudaGraphDestroy(g);
+  }
+  if (!c->graphExec[0]) {
+    for (int s = 0; s < 2; ++s) {
+      GraphArena As = A;
+      if (s == 1) As.ob = A.ob2;
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+      const long long before = g_launch_count;
+      graph_enqueue(As, c->dGeom, c->tune.nf_hits_per_block, c->tune.nf_staged != 0, c->tune.sort_threads_per_row,
+                    (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, st,
+                    (c->cfg.flags & O2TPC_FLAG_COOP_SEARCH) != 0, (c->cfg.flags & O2TPC_FLAG_ROW_STEP2) != 0);
+      const cudaError_t ce = cudaStreamEndCapture(st, &g);
+      c->graphKernels = g_launch_count - before;
+      if (ce != cudaSuccess || !g || cudaGraphInstantiate(&c->graphExec[s], g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        for (auto& e : c->graphExec) {
+          if (e) cudaGraphExecDestroy(e);
+          e = nullptr;
+        }
+        std::fprintf(stderr, "o2tpc: graph capture failed; batches run on the regular path\n");
+        c->graph.reset();
+        return false;
+      }
+      cudaGraphDestroy(g);
+    }
     c->graphNf = c->tune.nf_hits_per_block * 2 + c->tune.nf_staged;
     c->graphSort = c->tune.sort_threads_per_row;
   }
   g_launch_count = c->graphKernels;
   CK(cudaEventRecord(c->evs[0], st));
-  CK(cudaGraphLaunch(c->graphExec, st));
+  CK(cudaGraphLaunch(c->graphExec[slot], st));
   CK(cudaEventRecord(c->ev1, st));
   int hv[10];
   CK(cudaMemcpyAsync(hv, A.cnt, sizeof(Counts), cudaMemcpyDeviceToHost, st));
@@ -551,7 +567,9 @@ bool run_captured(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, 
   pp.n = (int)N;
   pp.tfd = tfd;
   pp.grid = A.grid;
-  pp.ob = A.ob;
+  pp.ob = slot ? A.ob2 : A.ob;
+  pp.graphSlot = slot;
+  c->graphSlot = slot ^ 1;
   pp.nHeads = hc.nHeads;
   pp.trkTfBegin = A.trkTfBegin;
   pp.stTfBegin = A.stTfBegin;
@@ -1170,7 +1188,10 @@ void run_batch(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs) {
     J.tfIndex = i;
   }
   CK(cudaEventRecord(P->dl1, dl));
-  if (captured) CK(cudaEventRecord(c->graphDl, dl));  // the next replay reuses the result arrays
+  if (captured) {  // the replay after next writes these result arrays again
+    CK(cudaEventRecord(c->graphDl[pp.graphSlot], dl));
+    c->graphDlRecorded[pp.graphSlot] = true;
+  }
   P->hostPrepMs = now_ms() - tPrep;
   P->hD = now_ms() - c->hostRef;
 
@@ -1523,7 +1544,7 @@ int o2tpc_create(const o2tpc_config* cfg, o2tpc_ctx** out) {
   }
   if (c.graph_max_clusters > 0) {
     try {
-      CK(cudaEventCreateWithFlags(&x->graphDl, cudaEventDisableTiming));
+      for (auto& e : x->graphDl) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       x->graph.reset(new GraphArena());
       x->graph->caps = graph_caps((long long)std::min<uint64_t>(c.graph_max_clusters, kMaxBatchHits / 2),
                                   c.graph_max_tfs > 0 ? c.graph_max_tfs : 64,
@@ -1681,10 +1702,12 @@ int o2tpc_destroy(o2tpc_ctx* ctx) {
   c->pinnedFree.clear();
   c->dev_free(c->dGeom);
   c->dev_free(c->dCounts);
-  if (c->graphExec) cudaGraphExecDestroy(c->graphExec);
+  for (auto& e : c->graphExec)
+    if (e) cudaGraphExecDestroy(e);
   if (c->graphMem) c->dev_free(c->graphMem);
   cudaStreamSynchronize(c->stream);
-  if (c->graphDl) cudaEventDestroy(c->graphDl);
+  for (auto& e : c->graphDl)
+    if (e) cudaEventDestroy(e);
   if (c->hStage) cudaFreeHost(c->hStage);
   for (auto& e : c->evs)
     if (e) cudaEventDestroy(e);

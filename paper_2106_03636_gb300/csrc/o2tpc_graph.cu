@@ -126,27 +126,29 @@ size_t graph_carve(GraphArena& A, char* base) {
   take(A.headFlag, k.stCap + 1);
   take(A.heads, k.headCap);
   take(A.trkNcl, k.headCap + 1);
-  take(A.ob.off, k.headCap + 1);
-  take(A.ob.cl, k.stHitsCap);
-  take(A.ob.x, k.headCap);
-  take(A.ob.alpha, k.headCap);
-  take(A.ob.par, (size_t)k.headCap * 5);
-  take(A.ob.cov, (size_t)k.headCap * 15);
-  take(A.ob.chi2, k.headCap);
-  take(A.ob.ndf, k.headCap);
-  take(A.ob.sector, k.headCap);
-  take(A.ob.flags, k.headCap);
-  take(A.ob.zref, k.headCap);
-  take(A.ob.nFallback, 1);
-  take(A.ob.fallback, k.headCap);
-  take(A.ob.ends, k.headCap);
-  take(A.ob.endsR, k.headCap);
-  take(A.ob.t0, k.headCap);
-  take(A.ob.t0err, k.headCap);
-  take(A.ob.t0lo, k.headCap);
-  take(A.ob.t0hi, k.headCap);
-  take(A.ob.mate, k.headCap);
-  take(A.ob.coll, k.headCap);
+  for (OutBufs* o : {&A.ob, &A.ob2}) {
+    take(o->off, k.headCap + 1);
+    take(o->cl, k.stHitsCap);
+    take(o->x, k.headCap);
+    take(o->alpha, k.headCap);
+    take(o->par, (size_t)k.headCap * 5);
+    take(o->cov, (size_t)k.headCap * 15);
+    take(o->chi2, k.headCap);
+    take(o->ndf, k.headCap);
+    take(o->sector, k.headCap);
+    take(o->flags, k.headCap);
+    take(o->zref, k.headCap);
+    take(o->nFallback, 1);
+    take(o->fallback, k.headCap);
+    take(o->ends, k.headCap);
+    take(o->endsR, k.headCap);
+    take(o->t0, k.headCap);
+    take(o->t0err, k.headCap);
+    take(o->t0lo, k.headCap);
+    take(o->t0hi, k.headCap);
+    take(o->mate, k.headCap);
+    take(o->coll, k.headCap);
+  }
   take(A.trkTfBegin, k.BCap + 1);
   take(A.coll, k.collCap);
   take(A.memNext, k.headCap);

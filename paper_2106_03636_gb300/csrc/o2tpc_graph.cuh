@@ -45,6 +45,7 @@ struct GraphArena {
   MergeBufs mb;
   int *headFlag, *heads, *trkNcl;
   OutBufs ob;
+  OutBufs ob2;  // a second set of result arrays: replays alternate between the two
   int* trkTfBegin;
   double* coll;                       // interaction times of the batch
   int *memNext, *memPrev, *memPairs;  // membrane links and their pair count

@@ -206,12 +206,13 @@ def test_launch_shapes_and_autotuner_leave_results_unchanged():
 
 def test_captured_path_equals_regular_path():
     """Batches run as one CUDA graph launch (the captured path) give the same
-    results as the regular path, on two different batches in a row (the
-    second a replay of the graph); with token capacities every batch
-    overflows and reruns on the regular path, again with the same results."""
+    results as the regular path, on three different batches in a row (the
+    replays alternate between two sets of result arrays, so the third reuses
+    the first one's); with token capacities every batch overflows and reruns
+    on the regular path, again with the same results."""
     keys = RESULT_KEYS
     sets = [synth.chunk_mix(seed=41, n_chunks=5) + [synth.single_sector(seed=42)],
-            synth.chunk_mix(seed=43, n_chunks=7)]
+            synth.chunk_mix(seed=43, n_chunks=7), synth.chunk_mix(seed=44, n_chunks=3)]
     with o2tpc.Tracker() as r:
         ref = [[r.poll(t) for t in r.submit_many(s)] for s in sets]
     for flags, captured in ((0, 1), (o2tpc.O2TPC_FLAG_GRAPH_TIGHT, 0)):
