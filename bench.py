@@ -75,7 +75,7 @@ STAGE_BYTES = {
 MEASURED_TRAFFIC = {
     # measured at full size: one ncu pass over every launch of the plain-only
     # bench on the 128-orbit TF (gpu__time_duration.sum, dram__bytes_read.sum,
-    # dram__bytes_write.sum), the last TF's launches (profiles/launches_full_tf.md)
+    # dram__bytes_write.sum), the launches of the last of the four TFs it runs
     ("k_tl_follow<1>", "full_tf"): {"bytes": 11453599488 + 4863723520,
                                     "sources_sha256_16": "58c898f3f3c41a05",
                                     "sources": ["k_track.cu", "o2tpc_internal.cuh"]},
