@@ -85,9 +85,64 @@ struct KeyLess {
   __device__ bool operator()(const int2& x, const int2& y) const { return x.x < y.x || (x.x == y.x && x.y < y.y); }
 };
 
+// The same bitonic network for n2 > kListSmem items in global memory g: the
+// stages up to kListSmem, and at every later stage the steps of distance <
+// kListSmem, run on one kListSmem chunk at a time staged in shared memory
+// sm; only the steps of distance >= kListSmem make passes over g.  The
+// direction of a compare-exchange is taken from the global index.
+__device__ void list_bitonic_big(int2* g, int n2, int2* sm) {
+  constexpr int S = kListSmem;
+  const KeyLess less;
+  auto cx = [&](int2* buf, int i, int l, int gi, int k) {
+    const int2 x = buf[i], y = buf[l];
+    if (((gi & k) == 0) ? less(y, x) : less(x, y)) {
+      buf[i] = y;
+      buf[l] = x;
+    }
+  };
+  // stages k <= S: each chunk sorted on its own (its direction from the chunk's index)
+  for (int c = 0; c < n2; c += S) {
+    for (int i = threadIdx.x; i < S; i += blockDim.x) sm[i] = g[c + i];
+    __syncthreads();
+    for (int k = 2; k <= S; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < S; i += blockDim.x) {
+          const int l = i ^ j;
+          if (l > i) cx(sm, i, l, c + i, k);
+        }
+        __syncthreads();
+      }
+    for (int i = threadIdx.x; i < S; i += blockDim.x) g[c + i] = sm[i];
+    __syncthreads();
+  }
+  for (int k = 2 * S; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j >= S; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) cx(g, i, l, i, k);
+      }
+      __syncthreads();
+    }
+    for (int c = 0; c < n2; c += S) {
+      for (int i = threadIdx.x; i < S; i += blockDim.x) sm[i] = g[c + i];
+      __syncthreads();
+      for (int j = S >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < S; i += blockDim.x) {
+          const int l = i ^ j;
+          if (l > i) cx(sm, i, l, c + i, k);
+        }
+        __syncthreads();
+      }
+      for (int i = threadIdx.x; i < S; i += blockDim.x) g[c + i] = sm[i];
+      __syncthreads();
+    }
+  }
+}
+
 // One CTA per B list: sort it by drift coordinate (bitonic, in shared memory
 // up to kListSmem items, else in the global scratch at 2 * listStart, which
-// has room for the padded power of two).
+// has room for the padded power of two, with the short-distance steps staged
+// through shared memory chunk by chunk).
 __global__ void __launch_bounds__(512) k_merge_list_sort(MergeBufs mb, int2* __restrict__ scratch) {
   __shared__ int2 sk[kListSmem];
   const int b = mb.listStart[blockIdx.x], n = mb.listStart[blockIdx.x + 1] - b;
@@ -98,7 +153,8 @@ __global__ void __launch_bounds__(512) k_merge_list_sort(MergeBufs mb, int2* __r
   for (int i = threadIdx.x; i < n2; i += blockDim.x)
     buf[i] = (i < n) ? make_int2(mb.listKey[b + i], mb.listItems[b + i]) : make_int2(INT_MAX, INT_MAX);
   __syncthreads();
-  cta_bitonic(buf, n2, KeyLess());
+  if (n2 <= kListSmem) cta_bitonic(buf, n2, KeyLess());
+  else list_bitonic_big(buf, n2, sk);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     mb.listKey[b + i] = buf[i].x;
     mb.listItems[b + i] = buf[i].y;
@@ -205,6 +261,7 @@ __global__ void __launch_bounds__(128) k_merge_pairs(SectorTrackBufs sb, const G
     else atomicOr(err, kErrOverflow);
   }
 }
+
 
 __global__ void k_pair_hist(MergeBufs mb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
