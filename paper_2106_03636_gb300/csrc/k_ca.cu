@@ -448,6 +448,53 @@ void scan_exclusive(const int* in, int* out, int n, const int* nDev, int* scratc
   ++g_launch_count;
 }
 
+// ---- processing order by length (longest first)
+__device__ inline int len_bin(const int* __restrict__ off, int i) {
+  return kLenBins - 1 - min(off[i + 1] - off[i], kLenBins - 1);
+}
+
+__global__ void __launch_bounds__(256) k_len_hist(const int* __restrict__ nDev, const int* __restrict__ off,
+                                                  int* __restrict__ hist) {
+  __shared__ int sh[kLenBins];
+  for (int b = threadIdx.x; b < kLenBins; b += blockDim.x) sh[b] = 0;
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < *nDev) atomicAdd(&sh[len_bin(off, i)], 1);
+  __syncthreads();
+  for (int b = threadIdx.x; b < kLenBins; b += blockDim.x)
+    if (sh[b]) atomicAdd(&hist[b], sh[b]);
+}
+
+// hist[0, kLenBins) -> exclusive offsets (one CTA of kLenBins threads)
+__global__ void __launch_bounds__(kLenBins) k_len_scan(int* __restrict__ hist) {
+  __shared__ int sh[kLenBins];
+  const int v = hist[threadIdx.x];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int d = 1; d < kLenBins; d <<= 1) {
+    const int t = threadIdx.x >= d ? sh[threadIdx.x - d] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  hist[threadIdx.x] = sh[threadIdx.x] - v;
+}
+
+__global__ void __launch_bounds__(256) k_len_place(const int* __restrict__ nDev, const int* __restrict__ off,
+                                                   int* __restrict__ hist, int* __restrict__ perm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < *nDev) perm[atomicAdd(&hist[len_bin(off, i)], 1)] = i;
+}
+
+void launch_len_order(int n, const int* nDev, const int* off, int* hist, int* perm, cudaStream_t st) {
+  if (n <= 0) return;
+  cudaMemsetAsync(hist, 0, sizeof(int) * kLenBins, st);
+  k_len_hist<<<(n + 255) / 256, 256, 0, st>>>(nDev, off, hist);
+  k_len_scan<<<1, kLenBins, 0, st>>>(hist);
+  k_len_place<<<(n + 255) / 256, 256, 0, st>>>(nDev, off, hist, perm);
+  g_launch_count += 3;
+}
+
 // *dst = min(arr[*idx], cap) (a count read off the end of a scan), flagging
 // an overflow; optionally also writes the count at base[*dst] (CSR end).
 __global__ void k_count_at(const int* __restrict__ arr, const int* __restrict__ idx, int* __restrict__ dst, int cap,

@@ -707,9 +707,10 @@ __global__ void k_st_gather(const int* __restrict__ nHitsDev, SectorTrackBufs sb
 
 __global__ void __launch_bounds__(128) k_sector_fit(const int* __restrict__ nStDev, TrackletBufs tb,
                                                     const int2* __restrict__ syz, const GeomConst* __restrict__ G,
-                                                    SectorTrackBufs sb) {
-  const int id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= *nStDev) return;
+                                                    SectorTrackBufs sb, const int* __restrict__ order) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= *nStDev) return;
+  const int id = order[j];
   const float zunit = G->zunit, bzc = G->bzc;
   const int b = sb.off[id], m = sb.off[id + 1] - b;
   const int2* P = sb.yz + b;
@@ -842,9 +843,9 @@ void launch_st_gather(int nHits, const int* nHitsDev, SectorTrackBufs sb, const 
 }
 
 void launch_sector_fit(int nSt, const int* nStDev, const TrackletBufs tb, const int2* syz, const GeomConst* G,
-                       SectorTrackBufs sb, cudaStream_t st) {
+                       SectorTrackBufs sb, const int* order, cudaStream_t st) {
   if (nSt > 0) {
-    k_sector_fit<<<(nSt + 127) / 128, 128, 0, st>>>(nStDev, tb, syz, G, sb);
+    k_sector_fit<<<(nSt + 127) / 128, 128, 0, st>>>(nStDev, tb, syz, G, sb, order);
     ++g_launch_count;
   }
 }

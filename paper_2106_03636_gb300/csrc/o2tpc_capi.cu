@@ -780,7 +780,10 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   launch_st_gather(nStHits, &C->nStHits, sb, syz, sorig, st);
   CKL();
   CK(cudaEventRecord(c->evs[6], st));
-  launch_sector_fit(nSt, &C->nSt, tb, syz, G, sb, st);
+  int* lenHist = dalloc<int>(M, kLenBins);
+  int* stOrder = dalloc<int>(M, nSt);
+  launch_len_order(nSt, &C->nSt, sb.off, lenHist, stOrder, st);
+  launch_sector_fit(nSt, &C->nSt, tb, syz, G, sb, stOrder, st);
   CKL();
   int* stTfBegin = dalloc<int>(M, B + 1);
   int* tfKeys = dalloc<int>(M, B + 1);
@@ -871,8 +874,7 @@ void run_regular(Ctx* c, std::vector<std::shared_ptr<Job>>& jobs, BatchMem& M, P
   scan_exclusive(trkNcl, ob.off, nHeads, &C->nHeads, scratch, st);
   CKL();
   launch_final_refit(nHeads, &C->nHeads, heads, sb, mb, syz, sorig, dTF, G,
-                     (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, ob,
-                     st);
+                     (c->cfg.flags & O2TPC_FLAG_FORCE_FP64) ? 1 : 0, ob, st);
   CKL();
   int* trkTfBegin = dalloc<int>(M, B + 1);
   launch_lower_bounds(heads, &C->nHeads, stTfBegin, B + 1, trkTfBegin, st);

@@ -150,6 +150,8 @@ size_t graph_carve(GraphArena& A, char* base) {
     take(o->coll, k.headCap);
   }
   take(A.trkTfBegin, k.BCap + 1);
+  take(A.lenHist, kLenBins);
+  take(A.stOrder, k.stCap);
   take(A.coll, k.collCap);
   take(A.memNext, k.headCap);
   take(A.memPrev, k.headCap);
@@ -197,7 +199,8 @@ void graph_enqueue(const GraphArena& A, const GeomConst* G, int nfBlock, bool nf
   launch_count_at(A.segPos, &C->nTl, &C->nSt, k.stCap, &C->overflow, st, A.segHitPos, &C->nStHits, k.stHitsCap,
                   A.sb.off);
   launch_st_gather(k.stHitsCap, &C->nStHits, A.sb, A.syz, A.sorig, st);
-  launch_sector_fit(k.stCap, &C->nSt, A.tb, A.syz, G, A.sb, st);
+  launch_len_order(k.stCap, &C->nSt, A.sb.off, A.lenHist, A.stOrder, st);
+  launch_sector_fit(k.stCap, &C->nSt, A.tb, A.syz, G, A.sb, A.stOrder, st);
   launch_iota(A.tfKeys, k.BCap + 1, st);
   launch_lower_bounds(A.sb.tf, &C->nSt, A.tfKeys, k.BCap + 1, A.stTfBegin, st);
   // A10

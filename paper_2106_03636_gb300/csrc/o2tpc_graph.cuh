@@ -46,6 +46,7 @@ struct GraphArena {
   int *headFlag, *heads, *trkNcl;
   OutBufs ob;
   OutBufs ob2;  // a second set of result arrays: replays alternate between the two
+  int *lenHist, *stOrder;  // the sector fits' longest-first processing order
   int* trkTfBegin;
   double* coll;                       // interaction times of the batch
   int *memNext, *memPrev, *memPairs;  // membrane links and their pair count

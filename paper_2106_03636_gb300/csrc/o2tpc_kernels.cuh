@@ -55,6 +55,12 @@ void launch_clean(int n, const int* nDev, const int* upRaw, const int* dnRaw, in
                   cudaStream_t st);
 int scan_scratch_ints(long long n);
 void scan_exclusive(const int* in, int* out, int n, const int* nDev, int* scratch, cudaStream_t st);
+// perm[0, m) = 0..m-1 (m = *nDev <= n) ordered by descending length
+// off[i + 1] - off[i] (lengths clamped to kLenBins - 1; any order among equal
+// lengths), so that a kernel walking perm with one thread per item gives the
+// 32 lanes of a warp items of about equal length.  hist: kLenBins ints.
+constexpr int kLenBins = 512;
+void launch_len_order(int n, const int* nDev, const int* off, int* hist, int* perm, cudaStream_t st);
 // Ordered compaction with warp ballots: the indices i < *nDev with flag[i]
 // set, ascending, into out (at most cap; more raise *overflow).
 // launch_ballot_count: tile counts, their scan into tileOff and *count;
@@ -123,8 +129,9 @@ void launch_segments_write(int nTl, const int* nTlDev, const int* secBegin, cons
 // sb.yz / sb.orig of every sector-track hit (after the CSR end is written)
 void launch_st_gather(int nHits, const int* nHitsDev, SectorTrackBufs sb, const int2* syz, const int* sorig,
                       cudaStream_t st);
+// order: the sector tracks in the order the fits take them (launch_len_order of sb.off)
 void launch_sector_fit(int nSt, const int* nStDev, const TrackletBufs tb, const int2* syz, const GeomConst* G,
-                       SectorTrackBufs sb, cudaStream_t st);
+                       SectorTrackBufs sb, const int* order, cudaStream_t st);
 
 // k_merge.cu
 struct MergeBufs {
