@@ -12,7 +12,10 @@
 
 namespace o2tpc {
 
-constexpr int kNFCand = 4;  // candidates per side held in registers by the NeighboursFinder
+#ifndef O2TPC_NF_CAND
+#define O2TPC_NF_CAND 6
+#endif
+constexpr int kNFCand = O2TPC_NF_CAND;  // candidates per side held in registers by the NeighboursFinder
 
 // Candidate residuals of one side, packed: (y_h - y_c + 1024) << 16 |
 // (z_h - z_c + 1024).  Inside the windows both halves stay in [776, 1272], so
