@@ -84,24 +84,61 @@ __global__ void __launch_bounds__(512) k_ingest_stats(const TFDesc* __restrict__
 
 // Per (TF, row): reduce the tile statistics, and turn each tile's count into
 // its exclusive offset inside the row's bucket (tile order = input order).
-__global__ void k_row_reduce(const TFDesc* __restrict__ tfs, int nTF, int* __restrict__ tileStats,
-                             int* __restrict__ rowCnt, int* __restrict__ rowMin, int* __restrict__ rowMax) {
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= nTF * kRowsPerTF) return;
-  int tf = g / kRowsPerTF, lr = g - tf * kRowsPerTF;
-  const TFDesc t = tfs[tf];
+// A block takes 32 rows of one TF; its 32 warps split the TF's tiles into 32
+// consecutive chunks (lane = row, so a warp's loads of one tile are one
+// 128-byte line): chunk sums first, their exclusive scan per row in shared
+// memory, then each chunk writes its tiles' offsets.
+constexpr int kRRRows = 32, kRRChunks = 32;
+__global__ void __launch_bounds__(kRRRows * kRRChunks) k_row_reduce(const TFDesc* __restrict__ tfs, int nTF,
+                                                                  int* __restrict__ tileStats, int* __restrict__ rowCnt,
+                                                                  int* __restrict__ rowMin, int* __restrict__ rowMax) {
+  __shared__ int s_sum[kRRChunks][kRRRows + 1], s_min[kRRChunks][kRRRows + 1], s_max[kRRChunks][kRRRows + 1];
+  const int blocksPerTF = (kRowsPerTF + kRRRows - 1) / kRRRows;
+  const int tf = blockIdx.x / blocksPerTF;
+  const int lane = threadIdx.x % kRRRows, q = threadIdx.x / kRRRows;
+  const int lr = (blockIdx.x % blocksPerTF) * kRRRows + lane;
+  const bool row = tf < nTF && lr < kRowsPerTF;
+  const TFDesc t = tfs[min(tf, nTF - 1)];
+  const int per = (t.nTiles + kRRChunks - 1) / kRRChunks;
+  const int k0 = min(q * per, t.nTiles), k1 = min(k0 + per, t.nTiles);
   int c = 0, mn = INT_MAX, mx = INT_MIN;
-  for (int k = 0; k < t.nTiles; ++k) {
-    int* ts = tileStats + (size_t)(t.tileBase + k) * 3 * kRowsPerTF;
-    int v = ts[lr];
-    ts[lr] = c;
-    c += v;
-    mn = min(mn, ts[kRowsPerTF + lr]);
-    mx = max(mx, ts[2 * kRowsPerTF + lr]);
+  if (row)
+    for (int k = k0; k < k1; ++k) {
+      const int* ts = tileStats + (size_t)(t.tileBase + k) * 3 * kRowsPerTF;
+      c += ts[lr];
+      mn = min(mn, ts[kRowsPerTF + lr]);
+      mx = max(mx, ts[2 * kRowsPerTF + lr]);
+    }
+  s_sum[q][lane] = c;
+  s_min[q][lane] = mn;
+  s_max[q][lane] = mx;
+  __syncthreads();
+  if (q == 0) {  // per row: exclusive scan of the chunk sums, totals, extremes
+    int run = 0, m0 = INT_MAX, m1 = INT_MIN;
+    for (int j = 0; j < kRRChunks; ++j) {
+      const int v = s_sum[j][lane];
+      s_sum[j][lane] = run;
+      run += v;
+      m0 = min(m0, s_min[j][lane]);
+      m1 = max(m1, s_max[j][lane]);
+    }
+    if (row) {
+      const int g = tf * kRowsPerTF + lr;
+      rowCnt[g] = run;
+      rowMin[g] = m0;
+      rowMax[g] = m1;
+    }
   }
-  rowCnt[g] = c;
-  rowMin[g] = mn;
-  rowMax[g] = mx;
+  __syncthreads();
+  if (row) {
+    int o = s_sum[q][lane];
+    for (int k = k0; k < k1; ++k) {
+      int* ts = tileStats + (size_t)(t.tileBase + k) * 3 * kRowsPerTF;
+      const int v = ts[lr];
+      ts[lr] = o;
+      o += v;
+    }
+  }
 }
 
 // Block-wide exclusive scan of one int per thread (blockDim.x == 1024).
@@ -377,8 +414,9 @@ void launch_ingest_stats(const TFDesc* tfs, const int2* tiles, int nTiles, int t
 
 void launch_row_reduce(const TFDesc* tfs, int nTF, int* tileStats, int* rowCnt, int* rowMin, int* rowMax,
                        cudaStream_t st) {
-  int n = nTF * kRowsPerTF;
-  k_row_reduce<<<(n + 255) / 256, 256, 0, st>>>(tfs, nTF, tileStats, rowCnt, rowMin, rowMax);
+  if (nTF <= 0) return;
+  const int blocksPerTF = (kRowsPerTF + kRRRows - 1) / kRRRows;
+  k_row_reduce<<<nTF * blocksPerTF, kRRRows * kRRChunks, 0, st>>>(tfs, nTF, tileStats, rowCnt, rowMin, rowMax);
   ++g_launch_count;
 }
 
