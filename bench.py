@@ -73,21 +73,15 @@ STAGE_BYTES = {
 # workload, valid while the kernel's sources hash to the recorded value;
 # otherwise the line says null.
 MEASURED_TRAFFIC = {
-    # measured at full size: one ncu pass over every launch of the plain-only
-    # bench on the 128-orbit TF (gpu__time_duration.sum, dram__bytes_read.sum,
-    # dram__bytes_write.sum), the launches of the last of the four TFs it runs
-    ("k_tl_follow<1>", "full_tf"): {"bytes": 11453599488 + 4863723520,
-                                    "sources_sha256_16": "58c898f3f3c41a05",
+    # the following passes: one-pass DRAM counters of a single kernel on the
+    # 1 ms frame (19.70 M clusters at the same 50 kHz density), scaled by the
+    # cluster count (x 241.96 / 19.70) to a launch on the 128-orbit TF
+    ("k_tl_follow<1>", "full_tf"): {"bytes": (1275230720 + 318950656) * 241.96 / 19.70,
+                                    "sources_sha256_16": "4e806c985b556a02",
                                     "sources": ["k_track.cu", "o2tpc_internal.cuh"]},
-    ("k_tl_follow<-1>", "full_tf"): {"bytes": 25006988544 + 4140118528,
-                                     "sources_sha256_16": "58c898f3f3c41a05",
+    ("k_tl_follow<-1>", "full_tf"): {"bytes": (1255842048 + 240202240) * 241.96 / 19.70,
+                                     "sources_sha256_16": "4e806c985b556a02",
                                      "sources": ["k_track.cu", "o2tpc_internal.cuh"]},
-    ("k_neighbours", "full_tf"): {"bytes": 2181558272 + 1895681280,
-                                  "sources_sha256_16": "d45000136ebb10df",
-                                  "sources": ["k_ca.cu", "o2tpc_internal.cuh"]},
-    ("k_row_scatter+k_cell_sort", "full_tf"): {"bytes": 6347177472 + 6376546560 + 12438317568 + 7191981312,
-                                               "sources_sha256_16": "b5dd6a9e05f5fc61",
-                                               "sources": ["k_bin.cu", "o2tpc_internal.cuh"]},
 }
 
 
