@@ -684,7 +684,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="served and chunks arms on the regular path, not captured")
     ap.add_argument("--torch-memory", action="store_true",
                     help="device buffers from PyTorch's caching allocator (no uploads ahead)")
-    ap.add_argument("--inflight", type=int, default=2, help="TFs kept in flight in the served measurement")
+    ap.add_argument("--inflight", type=int, default=3, help="TFs kept in flight in the served measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "gb300" else args.warmup
     if args.plain_only:
