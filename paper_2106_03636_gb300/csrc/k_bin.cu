@@ -286,9 +286,6 @@ __global__ void __launch_bounds__(kScatterT) k_row_scatter(const TFDesc* __restr
 // by input index).  Cell counters live in shared memory when the row has at
 // most kSmemCells cells, else in the global scratch (cellStart itself).
 constexpr int kSmemCells = 12288;
-#ifndef O2TPC_CELL_REGSORT
-#define O2TPC_CELL_REGSORT 1
-#endif
 constexpr int kRegSort = 8;
 
 template <int kT>
@@ -351,7 +348,6 @@ __global__ void __launch_bounds__(kT) k_cell_sort(const RowGrid* __restrict__ gr
   for (int c = threadIdx.x; c < nc; c += blockDim.x) {
     int b = cellStart[g.cellBase + c];
     int e = (c + 1 < nc) ? cellStart[g.cellBase + c + 1] : g.start + g.count;
-#if O2TPC_CELL_REGSORT
     const int m = e - b;
     if (m <= 1) continue;
     if (m <= kRegSort) {
@@ -385,7 +381,6 @@ __global__ void __launch_bounds__(kT) k_cell_sort(const RowGrid* __restrict__ gr
       }
       continue;
     }
-#endif
     for (int i = b + 1; i < e; ++i) {
       int ko = sorig[i];
       int2 kv = syz[i];
