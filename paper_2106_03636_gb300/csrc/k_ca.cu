@@ -193,13 +193,15 @@ __global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ g
       const int nd = nu > 0 ? nf_collect(gd, dy0, dy1, dz0, dz1, cellStart, sd, bd0, hh, di, dr) : 0;
       // bestD starts one above the cut, so "D < bestD" also applies the cut
       int bestD = kMaxMetric + 1;
-      if (nu <= kNFCand && nd <= kNFCand) {
-        // pairs in ascending (u, d): a strict "<" keeps the first minimum,
-        // which is the lexicographic minimum of (D, u, d)
+      // pairs in ascending (u, d): a strict "<" keeps the first minimum,
+      // which is the lexicographic minimum of (D, u, d).  Slots [a0, kNFCand)
+      // of both sides: the last four when both sides fit there (the common
+      // case), else all of them.
+      auto pair_scan = [&](const int a0) {
 #pragma unroll
-        for (int a = 0; a < kNFCand; ++a)
+        for (int a = a0; a < kNFCand; ++a)
 #pragma unroll
-          for (int b = 0; b < kNFCand; ++b) {
+          for (int b = a0; b < kNFCand; ++b) {
             const unsigned sres = ur[a] + dr[b];
             const int ey = (int)(sres >> 16) - 2048, ez = (int)(sres & 0xFFFFu) - 2048;
             const int D = kWeightY * ey * ey + kWeightZ * ez * ez;
@@ -209,6 +211,12 @@ __global__ void __launch_bounds__(kB) k_neighbours(const RowGrid* __restrict__ g
               bd = di[b];
             }
           }
+      };
+      constexpr int kNFSmall = kNFCand < 4 ? kNFCand : 4;
+      if (nu <= kNFSmall && nd <= kNFSmall) {
+        pair_scan(kNFCand - kNFSmall);
+      } else if (nu <= kNFCand && nd <= kNFCand) {
+        pair_scan(0);
       } else {
         const int y2 = 2 * yh, z2 = 2 * zh;
         for (int izu = uz0; izu <= uz1; ++izu) {
