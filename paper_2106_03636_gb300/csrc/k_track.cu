@@ -33,8 +33,9 @@ __device__ inline int find_row(const RowGrid* __restrict__ grid, int nRows, int 
 }
 
 // Row of hit h linked up from a hit on row R: R + 1, or R + 2 when the link
-// crosses a missing row (row step 2).
-__device__ inline int link_row(const RowGrid* __restrict__ grid, int R, int h) {
+// crosses a missing row (only with row step 2; without it no row is read).
+__device__ inline int link_row(const RowGrid* __restrict__ grid, int R, int h, int rowStep2) {
+  if (!rowStep2) return R + 1;
   const RowGrid g = grid[R + 1];
   return h < g.start + g.count ? R + 1 : R + 2;
 }
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(128) k_tl_chain(const int* __restrict__ nTlDev
                                                   int nRows, const int2* __restrict__ syz,
                                                   const GeomConst* __restrict__ G, TrackletBufs tb) {
   const float zunit = G->zunit, bzc = G->bzc;
+  const int rs2 = G->rowStep2;
   const int nTl = *nTlDev;
   for (;;) {
     const int k = atomicAdd(counter, 1);
@@ -127,9 +129,9 @@ __global__ void __launch_bounds__(128) k_tl_chain(const int* __restrict__ nTlDev
     tb.zref[k] = zref;
     tb.rbase[k] = R0 - r0;
     const int h1 = up[h0];
-    const int R1 = link_row(grid, R0, h1);
+    const int R1 = link_row(grid, R0, h1, rs2);
     const int h2 = up[h1];
-    const int R2 = link_row(grid, R1, h2);
+    const int R2 = link_row(grid, R1, h2, rs2);
     const int2 a2 = syz[h2];
     const float x0 = G->rowx[r0];
     const float dx = (float)(R2 - R0) * G->pitch, dy = hit_y(a2.x, yref) - hit_y(a0.x, yref);
@@ -158,7 +160,7 @@ __global__ void __launch_bounds__(128) k_tl_chain(const int* __restrict__ nTlDev
       ++nc;
       prev = row;
       hit = next;
-      if (hit >= 0) Rh = link_row(grid, Rh, hit);
+      if (hit >= 0) Rh = link_row(grid, Rh, hit, rs2);
     }
     tb.nasc[k] = dropped ? 0 : nc;
     tb.yref[k] = yref;
