@@ -76,11 +76,11 @@ MEASURED_TRAFFIC = {
     # the following passes: one-pass DRAM counters of a single kernel on the
     # 1 ms frame (19.70 M clusters at the same 50 kHz density), scaled by the
     # cluster count (x 241.96 / 19.70) to a launch on the 128-orbit TF
-    ("k_tl_follow<1>", "full_tf"): {"bytes": (1275230720 + 318950656) * 241.96 / 19.70,
-                                    "sources_sha256_16": "4e806c985b556a02",
+    ("k_tl_follow<1>", "full_tf"): {"bytes": (1256651008 + 318376704) * 241.96 / 19.70,
+                                    "sources_sha256_16": "c51eb7e4024de7bf",
                                     "sources": ["k_track.cu", "o2tpc_internal.cuh"]},
-    ("k_tl_follow<-1>", "full_tf"): {"bytes": (1255842048 + 240202240) * 241.96 / 19.70,
-                                     "sources_sha256_16": "4e806c985b556a02",
+    ("k_tl_follow<-1>", "full_tf"): {"bytes": (1249804288 + 240405760) * 241.96 / 19.70,
+                                     "sources_sha256_16": "c51eb7e4024de7bf",
                                      "sources": ["k_track.cu", "o2tpc_internal.cuh"]},
 }
 

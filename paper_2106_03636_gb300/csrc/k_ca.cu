@@ -491,10 +491,21 @@ __global__ void __launch_bounds__(kLenBins) k_len_scan(int* __restrict__ hist) {
   hist[threadIdx.x] = sh[threadIdx.x] - v;
 }
 
-__global__ void __launch_bounds__(256) k_len_place(const int* __restrict__ nDev, const int* __restrict__ off,
-                                                   int* __restrict__ hist, int* __restrict__ perm) {
+// Each block ranks its items per bin in shared memory, then reserves its
+// range in each bin with one global atomic per (block, bin).
+__global__ void __launch_bounds__(1024) k_len_place(const int* __restrict__ nDev, const int* __restrict__ off,
+                                                    int* __restrict__ hist, int* __restrict__ perm) {
+  __shared__ int sh[kLenBins];
+  for (int b = threadIdx.x; b < kLenBins; b += blockDim.x) sh[b] = 0;
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < *nDev) perm[atomicAdd(&hist[len_bin(off, i)], 1)] = i;
+  const int bin = (i < *nDev) ? len_bin(off, i) : -1;
+  const int rank = (bin >= 0) ? atomicAdd(&sh[bin], 1) : 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < kLenBins; b += blockDim.x)
+    if (sh[b]) sh[b] = atomicAdd(&hist[b], sh[b]);
+  __syncthreads();
+  if (bin >= 0) perm[sh[bin] + rank] = i;
 }
 
 void launch_len_order(int n, const int* nDev, const int* off, int* hist, int* perm, cudaStream_t st) {
@@ -502,7 +513,7 @@ void launch_len_order(int n, const int* nDev, const int* off, int* hist, int* pe
   cudaMemsetAsync(hist, 0, sizeof(int) * kLenBins, st);
   k_len_hist<<<(n + 255) / 256, 256, 0, st>>>(nDev, off, hist);
   k_len_scan<<<1, kLenBins, 0, st>>>(hist);
-  k_len_place<<<(n + 255) / 256, 256, 0, st>>>(nDev, off, hist, perm);
+  k_len_place<<<(n + 1023) / 1024, 1024, 0, st>>>(nDev, off, hist, perm);
   g_launch_count += 3;
 }
 
