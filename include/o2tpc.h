@@ -157,7 +157,7 @@ typedef struct {
   /* Captured path (0: off): batches of at most graph_max_tfs TFs (0: 64) and
    * graph_max_clusters clusters run as ONE CUDA graph launch - the whole
    * pipeline captured once and replayed, no host synchronisation inside -
-   * from a device arena allocated at o2tpc_create (about 200 bytes per
+   * from a device arena allocated at o2tpc_create (about 220 bytes per
    * cluster of graph_max_clusters, on top of mem_budget).  A batch whose
    * data exceed the arena's capacities (e.g. far more tracklets than usual)
    * is run again on the regular path; results are the same either way.
