@@ -225,6 +225,27 @@ def test_captured_path_equals_regular_path():
                         assert np.array_equal(x[k], y[k]), k
 
 
+def test_tf_submitted_while_another_is_in_flight():
+    """TFs submitted while another TF is on the device (the serving pattern:
+    the later ones queue, share batches and run behind it) give the same
+    results as each run alone, on the regular and on the captured path."""
+    big = synth.full_tpc_1ms(seed=51, n_coll=10)
+    later = [synth.single_sector(seed=52), synth.full_tpc_1ms(seed=53, n_coll=1), synth.single_sector(seed=54)]
+    with o2tpc.Tracker(flags=o2tpc.O2TPC_FLAG_NO_BATCHING) as a:
+        alone = [a.track(tf) for tf in [big] + later]
+    for kw in ({}, {"graph_max_clusters": 32 << 20, "graph_max_tfs": 8}):
+        with o2tpc.Tracker(max_batch=8, **kw) as t:
+            first = t.submit(big)
+            in_flight = t.poll(first, timeout_ms=0) is None
+            tickets = [t.submit(tf) for tf in later]
+            got = [t.poll(first)] + [t.poll(k) for k in tickets]
+        assert in_flight, "the first TF had finished before the others were submitted"
+        for x, y in zip(alone, got):
+            assert y["status"] == 0
+            for k in RESULT_KEYS:
+                assert np.array_equal(x[k], y[k]), k
+
+
 def test_float_time_input_parity(trk):
     """Float input with drift time instead of z: bit-exact integer stages and
     the track criteria against the oracle on the same input."""
